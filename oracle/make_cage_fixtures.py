@@ -1,0 +1,87 @@
+"""Draws the seeded Panda-cage fixtures that need the method's arithmetic.
+
+Writes ``tests/golden/cage_fixtures.npz`` with
+  self_pairs     (k, 2) int32   self-collision sphere pairs of the Panda-like
+                                model: spheres on bodies at least two apart in
+                                the chain, at least 0.02 m apart in the
+                                mid-range configuration, and colliding in at
+                                most 5% of 256 uniformly drawn configurations
+                                (pairs that overlap across a joint in most
+                                poses are geometry artefacts, not checks);
+  endpoint_pool  (4, 1024, 7)   per cage arm, configurations uniform in the
+                 float32        joint limits that are env+self valid with at
+                                least 1 mm clearance (the paper samples motions
+                                with valid endpoints, Sec. IV-A1).
+Only the FP64 oracle evaluates geometry here.  Seeds: 301 (pair screening),
+302 (endpoint pools).  Usage: python oracle/make_cage_fixtures.py
+"""
+from __future__ import annotations
+
+import os
+import sys
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parents[1]
+sys.path.insert(0, str(ROOT))
+
+from oracle import oracle as O  # noqa: E402
+from paper_2604_23960_gb300 import workloads as W  # noqa: E402
+
+OUT = ROOT / "tests" / "golden" / "cage_fixtures.npz"
+POOL = 1024
+
+
+def screen_self_pairs(seed: int = 301, n_cfg: int = 256, max_rate: float = 0.05, min_mid: float = 0.02):
+    m = W.panda_like(W._identity34(), None)
+    body = m.sphere_link
+    r = m.sphere_xyzr[:, 3].astype(np.float64)
+    cand = [(a, b) for a in range(m.n_spheres) for b in range(a + 1, m.n_spheres)
+            if abs(int(body[a]) - int(body[b])) >= 2]
+    cand = np.array(cand, np.int64)
+    qmid = (W.PANDA_LO.astype(np.float64) + W.PANDA_HI) / 2
+    c = O.fk(m, qmid)
+    d = np.linalg.norm(c[cand[:, 0]] - c[cand[:, 1]], axis=1) - r[cand[:, 0]] - r[cand[:, 1]]
+    keep = d > min_mid
+    rng = np.random.default_rng(seed)
+    hits = np.zeros(len(cand))
+    for _ in range(n_cfg):
+        q = rng.uniform(W.PANDA_LO, W.PANDA_HI)
+        c = O.fk(m, q)
+        d = np.linalg.norm(c[cand[:, 0]] - c[cand[:, 1]], axis=1) - r[cand[:, 0]] - r[cand[:, 1]]
+        hits += d < 0
+    keep &= hits / n_cfg <= max_rate
+    return cand[keep].astype(np.int32)
+
+
+def endpoint_pools(self_pairs, seed: int = 302, pool: int = POOL, chunk: int = 4096):
+    fx = {"self_pairs": self_pairs}
+    arms = W.cage_arms(fx)
+    env = W.cage_env()
+    rng = np.random.default_rng(seed)
+    pools = []
+    threads = os.cpu_count() or 1
+    for k in range(4):
+        got = []
+        while sum(len(g) for g in got) < pool:
+            cfg = rng.uniform(W.PANDA_LO, W.PANDA_HI, (chunk, 7)).astype(np.float32)
+            wps = np.repeat(cfg, 2, axis=0)       # start = goal: a single state
+            b = W._fast_batch(chunk, 1, np.full(chunk, k, np.int32), wps, None, 1.0 / 32, W.KIND_MV, 0)
+            wl = W.Workload("pool", arms, [env], b, env=0, check_env=True)
+            m = O.Oracle(wl).mv_min_clearance(stop_below=-1.0, threads=threads)
+            got.append(cfg[m > 1e-3])
+        pools.append(np.concatenate(got)[:pool])
+    return np.stack(pools).astype(np.float32)
+
+
+def main():
+    sp = screen_self_pairs()
+    pools = endpoint_pools(sp)
+    OUT.parent.mkdir(parents=True, exist_ok=True)
+    np.savez_compressed(OUT, self_pairs=sp, endpoint_pool=pools)
+    print(f"wrote {OUT}: {len(sp)} self pairs, endpoint pools {pools.shape}")
+
+
+if __name__ == "__main__":
+    main()

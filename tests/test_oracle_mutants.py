@@ -1,0 +1,67 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each case copies the oracle's C source, plants one plausible mistake (a sign,
+a dropped term, a transposed product, an off-by-one, a wrong padding or tie
+order), builds it on the CPU and runs the pin suite against that build in a
+child process; the pins must fail.  The unmodified source must pass.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
+
+from oracle import oracle as O
+
+ROOT = Path(__file__).resolve().parents[1]
+
+MUTANTS = {
+    "rot_x_sign": ("r.m[1][2] = -sin(a);", "r.m[1][2] = sin(a);"),
+    "dh_order": ("mat4 t1 = mat_mul(&rx, &tx);\n  mat4 t2 = mat_mul(&t1, &rz);",
+                 "mat4 t1 = mat_mul(&rx, &rz);\n  mat4 t2 = mat_mul(&t1, &tx);"),
+    "flange_dropped": ("mat4 fl = r->flange ? mat_from34(r->flange) : mat_identity();",
+                       "mat4 fl = mat_identity();"),
+    "last_state_dropped": ("for (int64_t t = 0; t <= T && !found; ++t) {",
+                           "for (int64_t t = 0; t < T && !found; ++t) {"),
+    "mv_last_state_dropped": ("for (int64_t t = 0; t <= T && valid; ++t) {",
+                              "for (int64_t t = 0; t < T && valid; ++t) {"),
+    "ffc_pair_order": ("for (int i = 0; i < qs.n && !found; ++i)\n      for (int j = i + 1; j < qs.n && !found; ++j)\n        if (pair_min(&qs, i, j) < 0.0) {",
+                       "for (int j = 1; j < qs.n && !found; ++j)\n      for (int i = 0; i < j && !found; ++i)\n        if (pair_min(&qs, i, j) < 0.0) {"),
+    "pad_first": ("const float *l = W + (size_t)(w1 - 1) * st;", "const float *l = W + (size_t)w0 * st;"),
+    "box_sign": ("else if (c[i] > hi) e = c[i] - hi;", "else if (c[i] > hi) e = hi - c[i] - 1.0;"),
+    "interp_offbyone": ("double f = (double)(t - tau) / (double)n;", "double f = (double)(t - tau) / (double)(n + 1);"),
+    "steps_floor": ("return (int64_t)ceil(dist / res);", "return (int64_t)floor(dist / res);"),
+    "self_dropped": ("for (int p = 0; p < r->n_self; ++p) {\n    int a = r->self_pairs[2 * p], c = r->self_pairs[2 * p + 1];\n    double v",
+                     "for (int p = 0; p < 0; ++p) {\n    int a = r->self_pairs[2 * p], c = r->self_pairs[2 * p + 1];\n    double v"),
+    "obstacle_radius_dropped": ("double v = orc_sphere_sphere(C + 3 * a, ra, co, e->spheres[4 * o + 3]);",
+                                "double v = orc_sphere_sphere(C + 3 * a, ra, co, 0.0);"),
+    "base_ignored": ("frame[0] = mat_from34(r->base);", "frame[0] = mat_identity();"),
+    "theta_offset_dropped": ("(double)row[3] + q[k - 1]", "q[k - 1]"),
+}
+
+PIN_ARGS = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+            str(ROOT / "tests" / "test_oracle_pins.py")]
+
+
+def _run_pins(lib: Path) -> int:
+    env = dict(os.environ, MRV_ORACLE_LIB=str(lib))
+    return subprocess.run(PIN_ARGS, cwd=ROOT, env=env, capture_output=True, timeout=600).returncode
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    src = O.SRC.read_text()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    lib = O.build(src=mut, out=tmp_path / "libmut.so")
+    assert _run_pins(lib) != 0, f"pins did not catch mutant {name}"
+
+
+def test_unmodified_passes(tmp_path):
+    lib = O.build(src=O.SRC, out=tmp_path / "liborig.so")
+    assert _run_pins(lib) == 0
