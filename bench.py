@@ -1,0 +1,376 @@
+"""Benchmark: MV motion-checks/s on 4 Panda-like arms in the cage (10k
+composite joint-space motions, resolution 1/32 rad), one GB300.
+
+A step is one MotionValidation pass over the whole 10k-motion batch with
+inputs resident in HBM: counter reset, preparation kernels, the persistent
+work-stealing kernel and the result kernel, replayed from one CUDA graph.
+L2 is flushed (a 512 MB write) before every timed step; each step is timed
+with CUDA events on the launching stream.  Rank 0 prints one JSON line.
+
+--impl reference times the FP64 oracle on the host cores instead (the
+reference arm for this workload: the paper ships no code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "MV/FFC motion-checks/s vs per-query launch; p50/p99 latency, 1 GB300"
+WORKLOAD = "cage_mv: MV, 4 Panda-like 7-DOF arms x 64 spheres, cage env 40 spheres + 12 boxes, " \
+           "10k start/goal joint-space motions, resolution 1/32 rad"
+FLOPS_PER_TEST = 10     # FP32 flops of one sphere-sphere test (3 sub, 1 mul + 2 fma, radius add + square)
+MAKERS = None
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text()), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def serving(ctx, duration_s=6.0, loads=(0.5, 0.8, 0.95), n_clients=64, seed=206):
+    """Poisson arrivals from 64 simulated planner clients; requests of
+    logU[1, 4096] motions from four families over four resident envs;
+    continuous batching over 4 streams.  Returns capacity, and throughput with
+    p50/p99 request latency (arrival -> result) at each load fraction."""
+    import threading
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import workloads as W
+    models, envs, fams = W.make_serving_families(20000, seed=seed)
+    rids = [ctx.upload_model(m) for m in models]
+    eids = [ctx.upload_env(e) for e in envs]
+    bas = [ctx.bind(f, rids, eids) for f in fams]
+    rng = np.random.default_rng(seed)
+    pool = []
+    for _ in range(600):
+        f = int(rng.integers(0, 4))
+        n = int(np.clip(round(math.exp(rng.uniform(0.0, math.log(4096)))), 1, 4096))
+        q0 = int(rng.integers(0, fams[f].batch.n_queries - n))
+        pool.append(mrv.slice_batch(bas[f], q0, q0 + n))
+    mean_size = float(np.mean([r.n_queries for r in pool]))
+    srv = mrv.Server(ctx, n_streams=4, device_budget_bytes=2 << 30, max_batch_queries=65536, max_pending=100000)
+    # capacity: the whole pool submitted at once (saturated server)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(r) for r in pool]
+    for t, r in zip(tickets, pool):
+        srv.wait(t, r.n_queries, timeout_ms=600000)
+    cap_qps = sum(r.n_queries for r in pool) / (time.perf_counter() - t0)
+    out = {"capacity": cap_qps, "unit": "motion-checks/s", "clients": n_clients, "mean_request": mean_size,
+           "streams": 4, "loads": []}
+    for frac in loads:
+        lam = frac * cap_qps / mean_size              # requests / s over all clients
+        lat, done_q = [], [0]
+        lock = threading.Lock()
+        t_start = time.perf_counter() + 0.2
+        t_end = t_start + duration_s
+
+        def client(cid):
+            r = np.random.default_rng(seed * 1000 + cid + int(frac * 100))
+            t = t_start + r.exponential(n_clients / lam)
+            while t < t_end:
+                now = time.perf_counter()
+                if t > now:
+                    time.sleep(t - now)
+                req = pool[int(r.integers(0, len(pool)))]
+                tk = srv.submit(req)
+                srv.wait(tk, req.n_queries, timeout_ms=600000)
+                fin = time.perf_counter()
+                with lock:
+                    lat.append(fin - t)
+                    done_q[0] += req.n_queries
+                t += r.exponential(n_clients / lam)
+
+        th = [threading.Thread(target=client, args=(c,)) for c in range(n_clients)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        span = max(time.perf_counter(), t_end) - t_start
+        la = np.array(lat) * 1e3
+        out["loads"].append({"load": frac, "offered_req_s": lam, "requests": len(lat),
+                             "throughput": done_q[0] / span, "p50_ms": float(np.percentile(la, 50)) if len(la) else None,
+                             "p99_ms": float(np.percentile(la, 99)) if len(la) else None})
+    st = srv.stats()
+    out["micro_batches"] = st["micro_batches"]
+    out["max_inflight"] = st["max_inflight"]
+    srv.close()
+    return out
+
+
+def cpu_baseline(w, seconds_hint: float = 20.0):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
+    from oracle import oracle as O
+    o = O.Oracle(w)
+    threads = os.cpu_count() or 1
+    n = w.batch.n_queries
+    idx = np.arange(min(n, 256))
+    t0 = time.perf_counter()
+    o.mv(idx, threads=threads)
+    dt = time.perf_counter() - t0
+    per_q = dt / len(idx)
+    k = int(min(n, max(len(idx), seconds_hint / max(per_q, 1e-9))))
+    idx = np.arange(k)
+    t0 = time.perf_counter()
+    o.mv(idx, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "motion-checks/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {k} of the {n} motions, FP64 scalar MV with early exit, {threads} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2604_23960_gb300 import workloads as W
+    w = W.make_cage_mv(10000)
+    o = O.Oracle(w)
+    threads = os.cpu_count() or 1
+    sample = args.ref_sample
+    rng_idx = [np.arange(s * sample, (s + 1) * sample) % w.batch.n_queries for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        o.mv(rng_idx[s], threads=threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        o.mv(rng_idx[args.warmup + s], threads=threads)
+    dt = time.perf_counter() - t0
+    v = sample * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "motion-checks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"{sample} motions of the 10k batch per step"},
+            "cpu_baseline": {"value": v, "unit": "motion-checks/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} motions per step"},
+            "e2e": {"value": v, "unit": "motion-checks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    ctx = mrv.Context(local, stream.cuda_stream)
+    w = W.make_cage_mv(args.queries)
+    ba_host = ctx.bind(w)
+    ba = ba_host.to("cuda")
+    nq = w.batch.n_queries
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    valid = torch.empty(nq, dtype=torch.uint8, device=dev)
+    conf = torch.empty((nq, 3), dtype=torch.int32, device=dev)
+    kind = torch.zeros(nq, dtype=torch.uint8, device=dev)       # every query is MV
+    ba.a["q_kind"] = kind
+    bs = ba.struct(mrv.MRV_CHECK_ENV, with_kind=True)
+    graph = mrv.mrv_graph_create(ctx.h, bs, valid, conf)
+
+    def step():
+        mrv.mrv_graph_launch(graph)
+
+    # warm-up (also validates the run)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+            ctx.sync()
+    stats = ctx.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+                ctx.sync()
+                kern_ms.append(ctx.stats()["device_ms"])
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_s = float(t.item())
+    value = nq * world * args.steps / total_s
+    nvalid = int(valid.sum().item())
+
+    # end to end through the public API with pinned host buffers
+    bh = ba_host.to("cpu", pin=True)
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        ctx.mv_validate(bh)
+        for i in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = ctx.mv_validate(bh)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    assert int(out.sum()) == nvalid
+    h2d = sum(v.numel() * v.element_size() for k, v in bh.a.items() if v is not None and k != "q_kind")
+    e2e_val = nq / (statistics.median(e2e_ms) / 1e3)
+
+    # one synchronous launch per query (the plain GPU path)
+    pq_n = min(nq, args.per_query_n)
+    sub = W.subset(w, np.arange(pq_n))
+    bsub = ctx.bind(sub, ctx.robot_ids, ctx.env_ids).to("cuda")
+    ctx.mv_validate(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pq_valid = ctx.mv_validate(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
+    torch.cuda.synchronize()
+    pq_rate = pq_n / (time.perf_counter() - t0)
+    assert torch.equal(pq_valid, valid[:pq_n])
+
+    # exhaustive pass (every check of every state): the roofline of the kernel
+    ctx.mv_validate(ba, exhaustive=True)
+    ex_ms = []
+    for _ in range(3):
+        flush.zero_()
+        ctx.mv_validate(ba, exhaustive=True)
+        ex_ms.append(ctx.stats()["device_ms"])
+    ex_stats = ctx.stats()
+
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    kms = statistics.mean(kern_ms)
+    achieved = stats["sphere_tests"] * FLOPS_PER_TEST / (kms / 1e3) / 1e12
+    ex_achieved = ex_stats["sphere_tests"] * FLOPS_PER_TEST / (statistics.median(ex_ms) / 1e3) / 1e12
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "motion-checks/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries_per_gpu": nq, "parallelism": f"replicas{world}",
+                   "l2": "flushed before every timed step (512 MB write)",
+                   "launch": "CUDA graph: reset + prepare + persistent work-stealing kernel + results",
+                   "tuning": mrv.mrv_get_tuning(ctx.h)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "k_main (persistent MV kernel), early exit",
+                     "peak_source": f"SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} sm_max_mhz)"},
+        "roofline_exhaustive": {"achieved": ex_achieved, "frac": ex_achieved / fp32_peak,
+                                "kernel_ms": statistics.median(ex_ms), "sphere_tests": ex_stats["sphere_tests"]},
+        "e2e": {"value": e2e_val, "unit": "motion-checks/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(nq),
+                "api": "mv_validate with pinned host buffers", "ms_median": statistics.median(e2e_ms)},
+        "per_query_launch": {"value": pq_rate, "unit": "motion-checks/s", "queries": pq_n,
+                             "speedup_batched": value / world / pq_rate},
+        "effort": {"states": stats["states_checked"] / max(1, stats["states_available"]),
+                   "sphere_tests": stats["sphere_tests"] / max(1, stats["sphere_tests_available"])},
+        "valid_total": f"{nvalid}/{nq}",
+        "kernel_ms_mean": kms,
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_serve:
+        line["serving"] = serving(ctx, args.serve_seconds)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    mrv.mrv_graph_destroy(graph)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mrv", choices=["mrv", "reference"])
+    ap.add_argument("--queries", type=int, default=10000)
+    ap.add_argument("--per-query-n", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-sample", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * mrv.h — multi-robot motion validation on GB300 (sm_103a): C ABI.
+ *
+ * Two primitives over synchronized multi-robot motions (paper Sec. III):
+ *   MotionValidation  (MV,  Alg. 1): boolean validity with early termination
+ *                     on any robot-obstacle, self or robot-robot collision;
+ *   FindFirstConflict (FFC, Alg. 2): the earliest robot-robot conflict
+ *                     (timestep, robot i, robot j).
+ * Robots are kinematic chains (modified DH) or point robots, approximated by
+ * spheres (Sec. II-B); obstacles are spheres and axis-aligned boxes ("simple
+ * geometries", Sec. III-A); motions are start/goal pairs discretised at a
+ * C-space resolution (Sec. IV-A3) or timed waypoint paths; shorter paths are
+ * padded with their last configuration (Sec. III-A).
+ *
+ * Conventions for every entry point:
+ *   - return value: MRV_OK (0) or a negative MRV_ERR_* code; no call aborts
+ *     the process.  mrv_last_error() returns a message for the calling thread.
+ *   - the caller owns every input and output buffer; uploads copy into
+ *     device memory owned by the context.
+ *   - pointers are host pointers unless the batch has MRV_PTRS_ON_DEVICE set,
+ *     in which case every input array of the batch and every output array of
+ *     the call are device pointers on the context's device.
+ *   - work runs on the context's CUDA stream; a call returns after its
+ *     outputs are written unless MRV_ASYNC is set (then mrv_sync() waits and
+ *     reports device-side errors).  MRV_ASYNC requires MRV_PTRS_ON_DEVICE.
+ *   - robot indices (i, j) in a conflict are 0-based slot positions inside
+ *     the query (the paper numbers robots from 1).
+ */
+#ifndef MRV_H
+#define MRV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MRV_OK 0
+#define MRV_ERR_ARG (-1)       /* malformed argument or batch               */
+#define MRV_ERR_OOM (-2)       /* device or host allocation failed          */
+#define MRV_ERR_NOT_FOUND (-3) /* unknown or released robot / env id        */
+#define MRV_ERR_CUDA (-4)      /* CUDA runtime error                        */
+#define MRV_ERR_TIMEOUT (-5)   /* a bounded device or host wait ran out     */
+#define MRV_ERR_BUSY (-6)      /* admission refused / queue full            */
+#define MRV_ERR_LIMIT (-7)     /* a size beyond a documented maximum        */
+
+/* ---- limits ------------------------------------------------------------ */
+#define MRV_MAX_ROBOTS 8          /* robots per query (28 pairs)            */
+#define MRV_MAX_DOF 8             /* joints per robot                       */
+#define MRV_MAX_SPHERES 256       /* spheres per robot model                */
+#define MRV_MAX_QUERY_SPHERES 512 /* spheres summed over a query's robots   */
+#define MRV_MAX_STEPS (1 << 24)   /* composite step count T of a query      */
+
+/* ---- robot kinds ------------------------------------------------------- */
+#define MRV_ROBOT_DH_CHAIN 0
+#define MRV_ROBOT_POINT 1
+
+/* ---- batch flags ------------------------------------------------------- */
+#define MRV_CHECK_ENV 0x1u        /* robot-obstacle + self checks (Alg. 1)  */
+#define MRV_HIERARCHICAL 0x2u     /* Alg. 1 hierarchical order (MV)         */
+#define MRV_EXHAUSTIVE 0x4u       /* no early termination (Sec. IV-A1)      */
+#define MRV_PTRS_ON_DEVICE 0x8u   /* inputs and outputs are device pointers */
+#define MRV_ASYNC 0x10u           /* return before completion (see above)   */
+#define MRV_PER_QUERY_LAUNCH 0x20u /* baseline: one synchronous kernel
+                                      launch per query                      */
+
+/* ---- query kinds (mrv_run) ---------------------------------------------- */
+#define MRV_KIND_MV 0
+#define MRV_KIND_FFC 1
+
+typedef struct mrv_ctx mrv_ctx;
+
+/* Creates a context on CUDA device `device`; work is issued on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out is owned by the
+ * caller and freed with mrv_destroy.  MRV_ERR_CUDA when the device is absent. */
+int mrv_create(mrv_ctx **out, int device, void *cuda_stream);
+int mrv_destroy(mrv_ctx *ctx);
+/* Message of the last failing call on this thread (never NULL; owned by the
+ * library, valid until the next call on this thread). */
+const char *mrv_last_error(mrv_ctx *ctx);
+/* Changes the stream later calls are issued on. */
+int mrv_set_stream(mrv_ctx *ctx, void *cuda_stream);
+
+/* ---- robot models (Sec. II-B: kinematic chain + spheres) ---------------- */
+typedef struct {
+  int32_t kind;             /* MRV_ROBOT_DH_CHAIN or MRV_ROBOT_POINT          */
+  int32_t dof;              /* DH: 1..MRV_MAX_DOF; POINT: 2 (x, y at point_z)
+                               or 3 (x, y, z)                                 */
+  const float *dh;          /* DH: dof x 4 row-major (a, alpha, d, theta_off);
+                               joint k maps frame k-1 to frame k by
+                               RotX(alpha) TransX(a) RotZ(theta_off+q_k)
+                               TransZ(d) (Craig's modified DH)                */
+  const float *flange;      /* DH: 3x4 fixed transform after the last joint
+                               (frame dof+1); NULL = identity                 */
+  const float *base;        /* 3x4 row-major world <- base transform; NULL =
+                               identity                                       */
+  float point_z;            /* POINT with dof 2: fixed z                      */
+  int32_t n_spheres;        /* 1..MRV_MAX_SPHERES                             */
+  const int32_t *sphere_link; /* n_spheres: 0 = base frame, k = frame after
+                               joint k, dof+1 = flange frame (DH); POINT: 0 =
+                               base, 1 = moving frame                         */
+  const float *sphere_xyzr; /* n_spheres x 4: link-local center, radius > 0   */
+  int32_t n_self_pairs;     /* self-collision pairs checked with the env      */
+  const int32_t *self_pairs; /* n_self_pairs x 2 sphere indices, or NULL      */
+} mrv_robot_desc;
+
+/* Copies a robot model (host pointers) to the device.  *robot_id_out is the
+ * handle used in batches.  MRV_ERR_ARG / MRV_ERR_LIMIT on malformed models. */
+int robot_model_upload(mrv_ctx *ctx, const mrv_robot_desc *desc, int32_t *robot_id_out);
+
+/* ---- environments (obstacle set E, Alg. 1) ------------------------------ */
+typedef struct {
+  int32_t n_spheres;
+  const float *spheres_xyzr;  /* n_spheres x 4, world frame                  */
+  int32_t n_aabbs;
+  const float *aabb_lohi;     /* n_aabbs x 6: lo x,y,z then hi x,y,z         */
+} mrv_env_desc;
+
+/* Copies an obstacle set (host pointers) to the device. */
+int env_upload(mrv_ctx *ctx, const mrv_env_desc *desc, int32_t *env_id_out);
+/* Drops the upload's reference (robots and envs share the id space); the
+ * device memory is freed once no call in flight uses it (the context's
+ * stream is synchronized first). */
+int mrv_release(mrv_ctx *ctx, int32_t id);
+
+/* ---- batches of queries --------------------------------------------------
+ * A ragged CSR batch.  Query q has slots q_robot_off[q] .. q_robot_off[q+1]-1
+ * (1..MRV_MAX_ROBOTS robots; slot order defines robot indices i, j).  Slot s
+ * uses robot model slot_robot_id[s] and waypoints slot_wp_off[s] ..
+ * slot_wp_off[s+1]-1; waypoint w is the row waypoints[w*wp_stride ..] whose
+ * first dof entries are the configuration.
+ *   - timed form (seg_steps != NULL): seg_steps[w] >= 1 interpolation steps
+ *     from waypoint w to the next one of its slot (ignored for a slot's last
+ *     waypoint); slot times start at 0; a slot past its end holds its last
+ *     configuration (padding, Sec. III-A).
+ *   - start/goal form (seg_steps == NULL): every slot has exactly 2
+ *     waypoints; each robot needs ceil(|g - s|_2 / resolution) steps (0 if it
+ *     does not move) and the composite motion takes the maximum T over its
+ *     robots, all robots time-scaled to start and finish together
+ *     (Sec. IV-A3).  T is computed in IEEE double, operations separately
+ *     rounded, summing squared joint differences in joint order.
+ * States t = 0..T (T+1 states) are checked; T <= MRV_MAX_STEPS. */
+typedef struct {
+  int32_t n_queries;
+  int32_t n_slots;           /* = q_robot_off[n_queries]                     */
+  int32_t n_waypoints;       /* = slot_wp_off[n_slots]                       */
+  int32_t env_id;            /* obstacle set of every query; -1 = none       */
+  const int32_t *q_robot_off;   /* n_queries + 1                             */
+  const int32_t *slot_robot_id; /* n_slots                                   */
+  const int32_t *slot_wp_off;   /* n_slots + 1                               */
+  const float *waypoints;       /* n_waypoints x wp_stride                   */
+  int32_t wp_stride;            /* >= the largest dof used                   */
+  const int32_t *seg_steps;     /* n_waypoints, or NULL (start/goal form)    */
+  float resolution;             /* start/goal form: C-space units per step   */
+  const int32_t *q_env_id;      /* n_queries env ids (-1 none) or NULL       */
+  const uint8_t *q_kind;        /* n_queries MRV_KIND_* (mrv_run) or NULL    */
+  uint32_t flags;               /* MRV_* batch flags                         */
+} mrv_batch;
+
+/* conflict record (Alg. 2): {-1,-1,-1} = none */
+typedef struct {
+  int32_t t, i, j;
+} mrv_conflict;
+
+/* MotionValidation (Alg. 1) of every query: valid_out[q] = 1 iff no state
+ * t in 0..T has a robot-robot collision or (MRV_CHECK_ENV) a robot-obstacle
+ * or self collision.  Early termination per query unless MRV_EXHAUSTIVE.
+ * min_clearance_out (nullable; requires MRV_EXHAUSTIVE): signed minimum
+ * clearance over every check of the query, +inf when no check applies. */
+int mv_validate(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out, float *min_clearance_out);
+
+/* FindFirstConflict (Alg. 2) of every query: the lexicographically smallest
+ * (t, i, j) with robots i < j overlapping at state t.  No obstacle or self
+ * checks (Sec. III-B). */
+int ffc_find(mrv_ctx *ctx, const mrv_batch *batch, mrv_conflict *out);
+
+/* Mixed batch in one persistent launch: query q is MV when q_kind[q] ==
+ * MRV_KIND_MV (valid_out[q] written) and FFC otherwise (conflict_out[q]
+ * written); entries of the other output are left untouched. */
+int mrv_run(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out, mrv_conflict *conflict_out);
+
+/* Diagnostic: per-sphere minimum clearance of query `q` of the batch at the
+ * listed timesteps (0 <= ts[k] <= T).  out: nt x M floats, M = spheres of the
+ * query's robots in slot order; each value is the minimum over the checks
+ * that involve the sphere (other robots' spheres; obstacles and self pairs
+ * when MRV_CHECK_ENV), +inf when none.  Pointer kinds follow the batch
+ * flag. */
+int mrv_clearance(mrv_ctx *ctx, const mrv_batch *batch, int32_t q, const int32_t *ts, int32_t nt,
+                  float *out);
+
+/* Waits for MRV_ASYNC work on the context's stream; returns its status. */
+int mrv_sync(mrv_ctx *ctx);
+
+/* ---- statistics of the last completed call -------------------------------- */
+typedef struct {
+  uint64_t states_available; /* sum over queries of (T+1)                    */
+  uint64_t states_checked;   /* states whose checks ran                      */
+  uint64_t sphere_tests;     /* sphere-sphere + sphere-box tests executed    */
+  uint64_t sphere_tests_available; /* tests of an exhaustive run             */
+  uint64_t work_items;       /* persistent-scheduler items                   */
+  int32_t n_valid, n_conflicts;
+  float device_ms;           /* kernel time of the last call (CUDA events)   */
+} mrv_stats;
+int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
+
+/* ---- scheduling knobs (persistent work-stealing kernel) ------------------ */
+typedef struct {
+  int32_t chunk_tiles;       /* 32-state tiles per work item (>= 1)          */
+  int32_t warps_per_block;   /* 1..12 (16 KB of shared memory per warp)      */
+  int32_t blocks_per_sm;     /* 0 = as many as fit                           */
+  int32_t fk_states;         /* states per FK round (<= 16 / robots)        */
+} mrv_tuning;
+int mrv_set_tuning(mrv_ctx *ctx, const mrv_tuning *t);
+int mrv_get_tuning(mrv_ctx *ctx, mrv_tuning *t);
+
+/* Times candidate tunings on `batch` (MRV_PTRS_ON_DEVICE, run through
+ * mrv_run semantics), keeps the fastest in the context, and caches it in the
+ * text file `cache_path` (nullable) keyed by device name and a batch class
+ * (robot count, sphere count and length buckets, query kinds).  A cached
+ * entry is reused without timing. */
+int mrv_autotune(mrv_ctx *ctx, const mrv_batch *batch, const char *cache_path, mrv_tuning *chosen);
+
+/* ---- CUDA-graph replay of one batch ----------------------------------------
+ * Captures the whole mixed run of a device-resident batch (counter reset,
+ * preparation kernels, persistent kernel, result kernel) into a CUDA graph
+ * bound to these exact pointers; mrv_graph_launch replays it on the
+ * context's stream (asynchronous; mrv_sync waits). */
+typedef struct mrv_graph mrv_graph;
+int mrv_graph_create(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out, mrv_conflict *conflict_out,
+                     mrv_graph **out);
+int mrv_graph_launch(mrv_graph *g);
+int mrv_graph_destroy(mrv_graph *g);
+
+/* ---- serving: continuous batching over streams ------------------------------
+ * A server owns `n_streams` CUDA streams and a scheduler thread.  Requests
+ * (host batches) are copied at submission; the scheduler admits waiting
+ * requests in arrival order whenever a stream is free and the request's
+ * device footprint fits in the free part of `device_budget_bytes`, packs
+ * every admitted request into one micro-batch, and runs it while other
+ * micro-batches are still on the device.  Robot and env ids refer to the
+ * context's resident uploads. */
+typedef struct mrv_server mrv_server;
+typedef struct {
+  int32_t n_streams;            /* concurrent micro-batches (1..16)          */
+  size_t device_budget_bytes;   /* admission limit on device footprint       */
+  int32_t max_batch_queries;    /* queries per micro-batch                   */
+  int32_t max_pending;          /* waiting requests before MRV_ERR_BUSY      */
+} mrv_server_opts;
+int mrv_server_create(mrv_ctx *ctx, const mrv_server_opts *opts, mrv_server **out);
+int mrv_server_destroy(mrv_server *s);
+/* Copies the host batch (flags: MRV_CHECK_ENV, MRV_EXHAUSTIVE only) and
+ * queues it; *ticket identifies the request. */
+int mrv_server_submit(mrv_server *s, const mrv_batch *batch, uint64_t *ticket);
+/* Waits up to timeout_ms for the request, then copies its results (host
+ * pointers, n_queries entries; either may be NULL) and forgets the ticket.
+ * MRV_ERR_TIMEOUT leaves the request pending. */
+int mrv_server_wait(mrv_server *s, uint64_t ticket, int32_t timeout_ms, uint8_t *valid_out,
+                    mrv_conflict *conflict_out);
+typedef struct {
+  uint64_t submitted, completed, rejected, micro_batches, queries;
+  uint64_t max_inflight;        /* largest number of micro-batches in flight */
+  double busy_ms;               /* device time summed over micro-batches     */
+} mrv_server_stats;
+int mrv_server_get_stats(mrv_server *s, mrv_server_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRV_H */

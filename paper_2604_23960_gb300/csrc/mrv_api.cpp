@@ -1,0 +1,798 @@
+// Host runtime of the C ABI declared in include/mrv.h: contexts, the
+// device-resident model / environment registry, batch staging, the launch
+// sequence (prepare -> persistent kernel -> results), CUDA-graph capture and
+// statistics.  Every entry point returns a status code; nothing aborts.
+#include "mrv_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+namespace mrv {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? MRV_ERR_OOM : MRV_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// scratch arena
+// ---------------------------------------------------------------------------
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+
+size_t Scratch::bytes_for(int64_t nq, int64_t ns, int64_t nw, int64_t stride) {
+  size_t b = 0;
+  auto add = [&](size_t n) { b = align_up(b, 256) + n; };
+  add(sizeof(int32_t) * nw);            // slot_tau
+  add(sizeof(QueryDev) * nq);           // q
+  add(sizeof(int32_t) * nq * 3);        // hit, best, minclr
+  add(sizeof(int32_t) * nq);            // sorted
+  add(sizeof(int32_t) * (kMaxLevels + 1) * 3);
+  add(sizeof(int32_t) * 8);             // counters
+  add(sizeof(uint32_t) * 2);            // err
+  add(sizeof(unsigned long long) * 8);  // stats
+  add(sizeof(int32_t) * 4);             // counts
+  // staged inputs
+  add(sizeof(int32_t) * (nq + 1));
+  add(sizeof(int32_t) * ns);
+  add(sizeof(int32_t) * (ns + 1));
+  add(sizeof(float) * nw * stride);
+  add(sizeof(int32_t) * nw);
+  add(sizeof(int32_t) * nq);            // q_env
+  add(sizeof(uint8_t) * nq);            // q_kind
+  // staged outputs
+  add(sizeof(uint8_t) * nq);
+  add(sizeof(float) * nq);
+  add(sizeof(mrv_conflict) * nq);
+  return align_up(b, 256) + 256;
+}
+
+int Scratch::ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStream_t st) {
+  const size_t need = bytes_for(nq, ns, nw, stride);
+  if (need > cap) {
+    if (base) {
+      cudaStreamSynchronize(st);
+      cudaFree(base);
+      base = nullptr;
+      cap = 0;
+    }
+    size_t want = need + need / 4;
+    cudaError_t e = cudaMalloc(&base, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      base = nullptr;
+      return cuda_fail(e, "scratch allocation");
+    }
+    cap = want;
+  }
+  char *p = static_cast<char *>(base);
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    o = align_up(o, 256);
+    void *r = p + o;
+    o += n;
+    return r;
+  };
+  slot_tau = (int32_t *)take(sizeof(int32_t) * nw);
+  q = (QueryDev *)take(sizeof(QueryDev) * nq);
+  q_hit = (int32_t *)take(sizeof(int32_t) * nq);
+  q_best = (int32_t *)take(sizeof(int32_t) * nq);
+  q_minclr = (float *)take(sizeof(float) * nq);
+  sorted = (int32_t *)take(sizeof(int32_t) * nq);
+  hist = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
+  level_start = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
+  cursor = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
+  counters = (int32_t *)take(sizeof(int32_t) * 8);
+  err = (uint32_t *)take(sizeof(uint32_t) * 2);
+  stats = (unsigned long long *)take(sizeof(unsigned long long) * 8);
+  counts = (int32_t *)take(sizeof(int32_t) * 4);
+  in_q_off = (int32_t *)take(sizeof(int32_t) * (nq + 1));
+  in_slot_robot = (int32_t *)take(sizeof(int32_t) * ns);
+  in_slot_wp = (int32_t *)take(sizeof(int32_t) * (ns + 1));
+  in_wp = (float *)take(sizeof(float) * nw * stride);
+  in_steps = (int32_t *)take(sizeof(int32_t) * nw);
+  in_q_env = (int32_t *)take(sizeof(int32_t) * nq);
+  in_q_kind = (uint8_t *)take(sizeof(uint8_t) * nq);
+  out_valid = (uint8_t *)take(sizeof(uint8_t) * nq);
+  out_minclr = (float *)take(sizeof(float) * nq);
+  out_conf = (mrv_conflict *)take(sizeof(mrv_conflict) * nq);
+  return MRV_OK;
+}
+
+void Scratch::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  cap = 0;
+}
+
+// ---------------------------------------------------------------------------
+// batch launch
+// ---------------------------------------------------------------------------
+
+int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
+  if (!b) return fail(MRV_ERR_ARG, "batch is NULL");
+  if (b->n_queries < 0 || b->n_slots < 0 || b->n_waypoints < 0)
+    return fail(MRV_ERR_ARG, "negative batch sizes");
+  if (b->n_queries == 0) return MRV_OK;
+  if (b->wp_stride < 1 || b->wp_stride > 64) return fail(MRV_ERR_ARG, "wp_stride %d outside 1..64", b->wp_stride);
+  if (!b->q_robot_off || !b->slot_robot_id || !b->slot_wp_off || !b->waypoints)
+    return fail(MRV_ERR_ARG, "missing batch array");
+  if (b->flags & ~(uint32_t)(MRV_CHECK_ENV | MRV_HIERARCHICAL | MRV_EXHAUSTIVE | MRV_PTRS_ON_DEVICE | MRV_ASYNC |
+                             MRV_PER_QUERY_LAUNCH))
+    return fail(MRV_ERR_ARG, "unknown flag bits 0x%x", b->flags);
+  if ((b->flags & MRV_ASYNC) && !(b->flags & MRV_PTRS_ON_DEVICE))
+    return fail(MRV_ERR_ARG, "MRV_ASYNC requires MRV_PTRS_ON_DEVICE");
+  if (!b->seg_steps && !(std::isfinite(b->resolution) && b->resolution > 0.f))
+    return fail(MRV_ERR_ARG, "start/goal form needs a positive finite resolution");
+  if (b->env_id != -1 && ctx->env_slot(b->env_id) < 0)
+    return fail(MRV_ERR_NOT_FOUND, "unknown env id %d", b->env_id);
+  if (!(b->flags & MRV_PTRS_ON_DEVICE)) {
+    if (b->q_robot_off[0] != 0 || b->q_robot_off[b->n_queries] != b->n_slots)
+      return fail(MRV_ERR_ARG, "q_robot_off must run from 0 to n_slots");
+    if (b->slot_wp_off[0] != 0 || b->slot_wp_off[b->n_slots] != b->n_waypoints)
+      return fail(MRV_ERR_ARG, "slot_wp_off must run from 0 to n_waypoints");
+    for (int q = 0; q < b->n_queries; ++q) {
+      const int n = b->q_robot_off[q + 1] - b->q_robot_off[q];
+      if (n < 1) return fail(MRV_ERR_ARG, "query %d has no robot", q);
+      if (n > MRV_MAX_ROBOTS) return fail(MRV_ERR_LIMIT, "query %d has %d robots (max %d)", q, n, MRV_MAX_ROBOTS);
+    }
+  }
+  return MRV_OK;
+}
+
+BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int chunk_tiles) {
+  BatchDev B;
+  std::memset(&B, 0, sizeof B);
+  B.n_queries = b->n_queries;
+  B.n_slots = b->n_slots;
+  B.n_waypoints = b->n_waypoints;
+  B.wp_stride = b->wp_stride;
+  B.flags = b->flags;
+  B.resolution = b->resolution;
+  B.default_env = b->env_id == -1 ? -1 : ctx->env_slot(b->env_id);
+  const bool dev = b->flags & MRV_PTRS_ON_DEVICE;
+  B.q_robot_off = dev ? b->q_robot_off : S.in_q_off;
+  B.slot_robot_id = dev ? b->slot_robot_id : S.in_slot_robot;
+  B.slot_wp_off = dev ? b->slot_wp_off : S.in_slot_wp;
+  B.waypoints = dev ? b->waypoints : S.in_wp;
+  B.seg_steps = b->seg_steps ? (dev ? b->seg_steps : S.in_steps) : nullptr;
+  B.q_env_id = b->q_env_id ? (dev ? b->q_env_id : S.in_q_env) : nullptr;
+  B.q_kind = b->q_kind ? (dev ? b->q_kind : S.in_q_kind) : nullptr;
+  B.forced_kind = forced_kind;
+  B.chunk_tiles = chunk_tiles;
+  B.slot_tau = S.slot_tau;
+  B.q = S.q;
+  B.q_hit = S.q_hit;
+  B.q_best = S.q_best;
+  B.q_minclr = S.q_minclr;
+  B.sorted = S.sorted;
+  B.hist = S.hist;
+  B.level_start = S.level_start;
+  B.cursor = S.cursor;
+  B.counters = S.counters;
+  B.err = S.err;
+  B.stats = S.stats;
+  B.models = ctx->d_models;
+  B.n_models = (int32_t)ctx->models.size();
+  B.envs = ctx->d_envs;
+  B.n_envs = (int32_t)ctx->envs.size();
+  B.clock_budget = ctx->clock_budget;
+  return B;
+}
+
+int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st) {
+  if (b->flags & MRV_PTRS_ON_DEVICE) return MRV_OK;
+  const int64_t nq = b->n_queries, ns = b->n_slots, nw = b->n_waypoints;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void *dst, const void *src, size_t n) {
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
+  };
+  cp(S.in_q_off, b->q_robot_off, sizeof(int32_t) * (nq + 1));
+  cp(S.in_slot_robot, b->slot_robot_id, sizeof(int32_t) * ns);
+  cp(S.in_slot_wp, b->slot_wp_off, sizeof(int32_t) * (ns + 1));
+  cp(S.in_wp, b->waypoints, sizeof(float) * nw * b->wp_stride);
+  if (b->seg_steps) cp(S.in_steps, b->seg_steps, sizeof(int32_t) * nw);
+  if (b->q_env_id) cp(S.in_q_env, b->q_env_id, sizeof(int32_t) * nq);
+  if (b->q_kind) cp(S.in_q_kind, b->q_kind, sizeof(uint8_t) * nq);
+  if (e != cudaSuccess) return cuda_fail(e, "input copy");
+  return MRV_OK;
+}
+
+int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm) {
+  int occ = 0;
+  if (max_blocks_per_sm(warps, clr, &occ) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+  return ctx->num_sms * occ;
+}
+
+// Issues the launch sequence on the context's stream (capturable).
+int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+                mrv_conflict *conf, bool timed) {
+  return enqueue_run_on(ctx, B, S, clr, valid, minclr, conf, ctx->stream, timed ? ctx->ev0 : nullptr,
+                        timed ? ctx->ev1 : nullptr);
+}
+
+int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+                   mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch reset");
+  if ((e = launch_prepare(B, st)) != cudaSuccess) return cuda_fail(e, "prepare launch");
+  const int warps = ctx->tuning.warps_per_block;
+  if ((e = set_main_attrs(warps)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  // external records become event nodes when the stream is being captured
+  if (ev0) cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal);
+  e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm), warps, clr, -1, st);
+  if (e != cudaSuccess) return cuda_fail(e, "main launch");
+  if (ev1) cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
+  if ((e = launch_finish(B, valid, minclr, conf, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish launch");
+  return MRV_OK;
+}
+
+int check_device_err(uint32_t err) {
+  if (!err) return MRV_OK;
+  if (err & kErrTimeout) return fail(MRV_ERR_TIMEOUT, "device work exceeded its clock budget");
+  if (err & kErrAbort) return fail(MRV_ERR_TIMEOUT, "device work aborted");
+  if (err & kErrRobotId) return fail(MRV_ERR_NOT_FOUND, "batch names an unknown robot id");
+  if (err & kErrEnvId) return fail(MRV_ERR_NOT_FOUND, "batch names an unknown env id");
+  if (err & kErrSpheres) return fail(MRV_ERR_LIMIT, "a query has more than %d spheres", MRV_MAX_QUERY_SPHERES);
+  if (err & kErrSteps) return fail(MRV_ERR_LIMIT, "a query has bad step counts or T > %d", MRV_MAX_STEPS);
+  if (err & kErrRobots) return fail(MRV_ERR_ARG, "a query has 0 or more than %d robots", MRV_MAX_ROBOTS);
+  if (err & kErrWaypoints) return fail(MRV_ERR_ARG, "a slot has bad waypoint offsets or counts");
+  if (err & kErrDof) return fail(MRV_ERR_ARG, "wp_stride is smaller than a robot's dof");
+  return fail(MRV_ERR_ARG, "device reported error bits 0x%x", err);
+}
+
+int finish_call(mrv_ctx *ctx, Scratch &S, bool async) {
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_stats, S.stats, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_counts, S.counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  ctx->pending = true;
+  if (async) return MRV_OK;
+  return ctx->sync();
+}
+
+}  // namespace mrv
+
+using mrv::cuda_fail;
+
+int mrv_ctx::sync() {
+  using namespace mrv;
+  cudaSetDevice(device);
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  if (!pending) return MRV_OK;
+  pending = false;
+  stats.sphere_tests = h_stats[1];
+  stats.states_checked = h_stats[0];
+  stats.states_available = h_stats[2];
+  stats.sphere_tests_available = h_stats[3];
+  stats.work_items = h_stats[4];
+  stats.n_valid = h_counts[0];
+  stats.n_conflicts = h_counts[1];
+  float ms = 0.f;
+  if (timed_pending && cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) stats.device_ms = ms;
+  cudaGetLastError();
+  timed_pending = false;
+  return check_device_err(h_status[0]);
+}
+
+namespace mrv {
+
+int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr,
+              mrv_conflict *conf) {
+  int rc = validate_batch(ctx, b);
+  if (rc) return rc;
+  if (b->n_queries == 0) {
+    ctx->stats = mrv_stats{};
+    return MRV_OK;
+  }
+  if (minclr && !(b->flags & MRV_EXHAUSTIVE))
+    return fail(MRV_ERR_ARG, "min_clearance_out requires MRV_EXHAUSTIVE");
+  if (ctx->pending && (rc = ctx->sync())) return rc;
+  cudaSetDevice(ctx->device);
+  Scratch &S = ctx->scratch;
+  if ((rc = S.ensure(b->n_queries, b->n_slots, b->n_waypoints, b->wp_stride, ctx->stream))) return rc;
+  if ((rc = stage_inputs(b, S, ctx->stream))) return rc;
+  const bool dev = b->flags & MRV_PTRS_ON_DEVICE;
+  const bool clr = minclr != nullptr;
+  const bool per_query = b->flags & MRV_PER_QUERY_LAUNCH;
+  BatchDev B = make_batchdev(ctx, b, S, forced_kind, per_query ? 1 : ctx->tuning.chunk_tiles);
+  uint8_t *v_dst = valid ? (dev ? valid : S.out_valid) : nullptr;
+  float *m_dst = minclr ? (dev ? minclr : S.out_minclr) : nullptr;
+  mrv_conflict *c_dst = conf ? (dev ? conf : S.out_conf) : nullptr;
+  cudaStream_t st = ctx->stream;
+  if (!per_query) {
+    if ((rc = enqueue_run(ctx, B, S, clr, v_dst, m_dst, c_dst, true))) return rc;
+  } else {
+    // baseline: one synchronous launch per query (grid = the query's chunks)
+    cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * 4, st);
+    if (e == cudaSuccess) e = launch_prepare(B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prepare");
+    std::vector<QueryDev> hq(b->n_queries);
+    e = cudaMemcpyAsync(hq.data(), S.q, sizeof(QueryDev) * b->n_queries, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "query table copy");
+    if ((e = set_main_attrs(1)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    cudaEventRecord(ctx->ev0, st);
+    for (int q = 0; q < b->n_queries; ++q) {
+      if (hq[q].bits & 4u || hq[q].nchunks == 0) continue;
+      if ((e = launch_main(B, hq[q].nchunks, 1, clr, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "query synchronize");
+    }
+    cudaEventRecord(ctx->ev1, st);
+    if ((e = launch_finish(B, v_dst, m_dst, c_dst, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish");
+  }
+  ctx->timed_pending = true;
+  if (!dev) {
+    cudaError_t e = cudaSuccess;
+    const size_t nq = b->n_queries;
+    if (valid) e = cudaMemcpyAsync(valid, S.out_valid, nq, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && minclr) e = cudaMemcpyAsync(minclr, S.out_minclr, nq * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && conf) e = cudaMemcpyAsync(conf, S.out_conf, nq * sizeof(mrv_conflict), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
+  }
+  return finish_call(ctx, S, (b->flags & MRV_ASYNC) != 0);
+}
+
+// ---------------------------------------------------------------------------
+// registry
+// ---------------------------------------------------------------------------
+
+}  // namespace mrv
+
+int mrv_ctx::env_slot(int32_t id) const {
+  using namespace mrv;
+  const int s = id - kEnvIdBase;
+  if (s < 0 || s >= (int)envs.size() || !envs[s].dev.live) return -1;
+  return s;
+}
+
+int mrv_ctx::push_tables() {
+  using namespace mrv;
+  // every stream of the device may read the tables (contexts, servers)
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize before table update");
+  auto grow = [&](void **dptr, size_t *cap, size_t need, size_t elem) -> cudaError_t {
+    if (need <= *cap && *dptr) return cudaSuccess;
+    size_t c = std::max<size_t>(16, need * 2);
+    void *p = nullptr;
+    cudaError_t r = cudaMalloc(&p, c * elem);
+    if (r != cudaSuccess) return r;
+    if (*dptr) cudaFree(*dptr);
+    *dptr = p;
+    *cap = c;
+    return cudaSuccess;
+  };
+  std::vector<ModelDev> hm(models.size());
+  for (size_t i = 0; i < models.size(); ++i) hm[i] = models[i].dev;
+  std::vector<EnvDev> he(envs.size());
+  for (size_t i = 0; i < envs.size(); ++i) he[i] = envs[i].dev;
+  if ((e = grow((void **)&d_models, &cap_models, hm.size(), sizeof(ModelDev))) != cudaSuccess)
+    return cuda_fail(e, "model table");
+  if ((e = grow((void **)&d_envs, &cap_envs, he.size(), sizeof(EnvDev))) != cudaSuccess) return cuda_fail(e, "env table");
+  if (!hm.empty() && (e = cudaMemcpy(d_models, hm.data(), hm.size() * sizeof(ModelDev), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "model table copy");
+  if (!he.empty() && (e = cudaMemcpy(d_envs, he.data(), he.size() * sizeof(EnvDev), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "env table copy");
+  return MRV_OK;
+}
+
+namespace mrv {
+
+static int upload(void **dst, const void *src, size_t n) {
+  *dst = nullptr;
+  if (n == 0) return MRV_OK;
+  cudaError_t e = cudaMalloc(dst, n);
+  if (e != cudaSuccess) {
+    *dst = nullptr;
+    return cuda_fail(e, "upload allocation");
+  }
+  e = cudaMemcpy(*dst, src, n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "upload copy");
+  return MRV_OK;
+}
+
+}  // namespace mrv
+
+using namespace mrv;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char *mrv_last_error(mrv_ctx *) { return g_err.c_str(); }
+
+int mrv_create(mrv_ctx **out, int device, void *cuda_stream) {
+  if (!out) return fail(MRV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(MRV_ERR_CUDA, "no CUDA device available");
+  }
+  if (device < 0 || device >= n) return fail(MRV_ERR_ARG, "device %d outside 0..%d", device, n - 1);
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  mrv_ctx *c = new (std::nothrow) mrv_ctx();
+  if (!c) return fail(MRV_ERR_OOM, "context allocation");
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->device_name = prop.name;
+  e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "context resources");
+  }
+  c->h_status = (uint32_t *)c->h_pinned;
+  c->h_stats = (unsigned long long *)((char *)c->h_pinned + 64);
+  c->h_counts = (int32_t *)((char *)c->h_pinned + 256);
+  *out = c;
+  return MRV_OK;
+}
+
+int mrv_destroy(mrv_ctx *c) {
+  if (!c) return MRV_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto &m : c->models) m.free_all();
+  for (auto &e : c->envs) e.free_all();
+  c->scratch.release();
+  if (c->d_models) cudaFree(c->d_models);
+  if (c->d_envs) cudaFree(c->d_envs);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+  return MRV_OK;
+}
+
+int mrv_set_stream(mrv_ctx *c, void *stream) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  int rc = c->sync();
+  c->stream = (cudaStream_t)stream;
+  return rc;
+}
+
+int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
+  if (!c || !d || !id_out) return fail(MRV_ERR_ARG, "NULL argument");
+  if (d->kind != MRV_ROBOT_DH_CHAIN && d->kind != MRV_ROBOT_POINT) return fail(MRV_ERR_ARG, "unknown robot kind");
+  if (d->kind == MRV_ROBOT_DH_CHAIN && (d->dof < 1 || d->dof > MRV_MAX_DOF))
+    return fail(MRV_ERR_LIMIT, "dof %d outside 1..%d", d->dof, MRV_MAX_DOF);
+  if (d->kind == MRV_ROBOT_POINT && d->dof != 2 && d->dof != 3) return fail(MRV_ERR_ARG, "point robots have dof 2 or 3");
+  if (d->kind == MRV_ROBOT_DH_CHAIN && !d->dh) return fail(MRV_ERR_ARG, "DH table missing");
+  if (d->n_spheres < 1 || d->n_spheres > MRV_MAX_SPHERES)
+    return fail(MRV_ERR_LIMIT, "n_spheres %d outside 1..%d", d->n_spheres, MRV_MAX_SPHERES);
+  if (!d->sphere_link || !d->sphere_xyzr) return fail(MRV_ERR_ARG, "sphere arrays missing");
+  if (d->n_self_pairs < 0 || (d->n_self_pairs > 0 && !d->self_pairs)) return fail(MRV_ERR_ARG, "self pairs missing");
+  const int n_frames = d->kind == MRV_ROBOT_POINT ? 2 : d->dof + 2;
+  for (int s = 0; s < d->n_spheres; ++s) {
+    if (d->sphere_link[s] < 0 || d->sphere_link[s] >= n_frames)
+      return fail(MRV_ERR_ARG, "sphere %d attached to frame %d (0..%d)", s, d->sphere_link[s], n_frames - 1);
+    const float *x = d->sphere_xyzr + 4 * s;
+    if (!(std::isfinite(x[0]) && std::isfinite(x[1]) && std::isfinite(x[2]) && x[3] > 0.f && std::isfinite(x[3])))
+      return fail(MRV_ERR_ARG, "sphere %d not finite or radius <= 0", s);
+  }
+  for (int p = 0; p < d->n_self_pairs; ++p) {
+    const int a = d->self_pairs[2 * p], b = d->self_pairs[2 * p + 1];
+    if (a < 0 || b < 0 || a >= d->n_spheres || b >= d->n_spheres || a == b)
+      return fail(MRV_ERR_ARG, "self pair %d (%d, %d) invalid", p, a, b);
+  }
+  cudaSetDevice(c->device);
+  HostModel m;
+  ModelDev &D = m.dev;
+  std::memset(&D, 0, sizeof D);
+  D.kind = d->kind;
+  D.dof = d->dof;
+  D.n_spheres = d->n_spheres;
+  D.n_self = d->n_self_pairs;
+  D.live = 1;
+  D.point_z = d->point_z;
+  static const float I34[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+  std::memcpy(D.base, d->base ? d->base : I34, sizeof D.base);
+  std::memcpy(D.flange, d->flange ? d->flange : I34, sizeof D.flange);
+  if (d->kind == MRV_ROBOT_DH_CHAIN)
+    for (int k = 0; k < d->dof; ++k) {
+      const float *r = d->dh + 4 * k;
+      D.dh[k][0] = std::cos(r[1]);
+      D.dh[k][1] = std::sin(r[1]);
+      D.dh[k][2] = r[0];
+      D.dh[k][3] = r[2];
+      D.dh[k][4] = r[3];
+    }
+  int rc;
+  if ((rc = upload(&m.d_spheres, d->sphere_xyzr, sizeof(float) * 4 * d->n_spheres))) return rc;
+  if ((rc = upload(&m.d_links, d->sphere_link, sizeof(int32_t) * d->n_spheres))) { m.free_all(); return rc; }
+  if ((rc = upload(&m.d_self, d->self_pairs, sizeof(int32_t) * 2 * d->n_self_pairs))) { m.free_all(); return rc; }
+  D.spheres = (const float4 *)m.d_spheres;
+  D.sphere_link = (const int32_t *)m.d_links;
+  D.self_pairs = (const int2 *)m.d_self;
+  m.refs = 1;
+  m.max_spheres = d->n_spheres;
+  c->models.push_back(m);
+  if ((rc = c->push_tables())) {
+    c->models.back().free_all();
+    c->models.pop_back();
+    return rc;
+  }
+  *id_out = (int32_t)c->models.size() - 1;
+  return MRV_OK;
+}
+
+int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
+  if (!c || !d || !id_out) return fail(MRV_ERR_ARG, "NULL argument");
+  if (d->n_spheres < 0 || d->n_aabbs < 0) return fail(MRV_ERR_ARG, "negative obstacle counts");
+  if ((d->n_spheres && !d->spheres_xyzr) || (d->n_aabbs && !d->aabb_lohi)) return fail(MRV_ERR_ARG, "obstacle arrays missing");
+  for (int i = 0; i < d->n_aabbs; ++i)
+    for (int k = 0; k < 3; ++k)
+      if (!(d->aabb_lohi[6 * i + k] <= d->aabb_lohi[6 * i + 3 + k]))
+        return fail(MRV_ERR_ARG, "box %d has lo > hi on axis %d", i, k);
+  cudaSetDevice(c->device);
+  HostEnv h;
+  std::memset(&h.dev, 0, sizeof h.dev);
+  int rc;
+  if ((rc = upload(&h.d_spheres, d->spheres_xyzr, sizeof(float) * 4 * d->n_spheres))) return rc;
+  if ((rc = upload(&h.d_aabbs, d->aabb_lohi, sizeof(float) * 6 * d->n_aabbs))) { h.free_all(); return rc; }
+  h.dev.n_spheres = d->n_spheres;
+  h.dev.n_aabbs = d->n_aabbs;
+  h.dev.live = 1;
+  h.dev.spheres = (const float4 *)h.d_spheres;
+  h.dev.aabbs = (const float *)h.d_aabbs;
+  h.refs = 1;
+  c->envs.push_back(h);
+  if ((rc = c->push_tables())) {
+    c->envs.back().free_all();
+    c->envs.pop_back();
+    return rc;
+  }
+  *id_out = kEnvIdBase + (int32_t)c->envs.size() - 1;
+  return MRV_OK;
+}
+
+int mrv_release(mrv_ctx *c, int32_t id) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  cudaSetDevice(c->device);
+  if (id >= kEnvIdBase) {
+    const int s = c->env_slot(id);
+    if (s < 0) return fail(MRV_ERR_NOT_FOUND, "unknown env id %d", id);
+    if (--c->envs[s].refs == 0) {
+      int rc = c->sync();
+      c->envs[s].free_all();
+      c->envs[s].dev.live = 0;
+      int rc2 = c->push_tables();
+      return rc ? rc : rc2;
+    }
+    return MRV_OK;
+  }
+  if (id < 0 || id >= (int)c->models.size() || !c->models[id].dev.live)
+    return fail(MRV_ERR_NOT_FOUND, "unknown robot id %d", id);
+  if (--c->models[id].refs == 0) {
+    int rc = c->sync();
+    c->models[id].free_all();
+    c->models[id].dev.live = 0;
+    int rc2 = c->push_tables();
+    return rc ? rc : rc2;
+  }
+  return MRV_OK;
+}
+
+int mv_validate(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, float *min_clearance_out) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  if (!valid_out && b && b->n_queries > 0) return fail(MRV_ERR_ARG, "valid_out is NULL");
+  return run_batch(c, b, MRV_KIND_MV, valid_out, min_clearance_out, nullptr);
+}
+
+int ffc_find(mrv_ctx *c, const mrv_batch *b, mrv_conflict *out) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  if (!out && b && b->n_queries > 0) return fail(MRV_ERR_ARG, "out is NULL");
+  return run_batch(c, b, MRV_KIND_FFC, nullptr, nullptr, out);
+}
+
+int mrv_run(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_conflict *conflict_out) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  if (b && b->n_queries > 0 && (!valid_out || !conflict_out)) return fail(MRV_ERR_ARG, "outputs are NULL");
+  if (b && b->n_queries > 0 && !b->q_kind) return fail(MRV_ERR_ARG, "mrv_run needs q_kind");
+  return run_batch(c, b, -1, valid_out, nullptr, conflict_out);
+}
+
+int mrv_sync(mrv_ctx *c) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  return c->sync();
+}
+
+int mrv_get_stats(mrv_ctx *c, mrv_stats *out) {
+  if (!c || !out) return fail(MRV_ERR_ARG, "NULL argument");
+  *out = c->stats;
+  return MRV_OK;
+}
+
+int mrv_set_tuning(mrv_ctx *c, const mrv_tuning *t) {
+  if (!c || !t) return fail(MRV_ERR_ARG, "NULL argument");
+  if (t->chunk_tiles < 1 || t->chunk_tiles > 4096) return fail(MRV_ERR_ARG, "chunk_tiles outside 1..4096");
+  if (t->warps_per_block < 1 || t->warps_per_block > 12) return fail(MRV_ERR_ARG, "warps_per_block outside 1..12");
+  if (t->blocks_per_sm < 0) return fail(MRV_ERR_ARG, "blocks_per_sm < 0");
+  c->tuning = *t;
+  return MRV_OK;
+}
+
+int mrv_get_tuning(mrv_ctx *c, mrv_tuning *t) {
+  if (!c || !t) return fail(MRV_ERR_ARG, "NULL argument");
+  *t = c->tuning;
+  return MRV_OK;
+}
+
+int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, int32_t nt, float *out) {
+  if (!c) return fail(MRV_ERR_ARG, "ctx is NULL");
+  int rc = validate_batch(c, b);
+  if (rc) return rc;
+  if (q < 0 || q >= b->n_queries) return fail(MRV_ERR_ARG, "query %d outside the batch", q);
+  if (nt < 0 || (nt > 0 && (!ts || !out))) return fail(MRV_ERR_ARG, "bad timestep list");
+  if (nt == 0) return MRV_OK;
+  if (c->pending && (rc = c->sync())) return rc;
+  cudaSetDevice(c->device);
+  Scratch &S = c->scratch;
+  if ((rc = S.ensure(b->n_queries, b->n_slots, b->n_waypoints, b->wp_stride, c->stream))) return rc;
+  if ((rc = stage_inputs(b, S, c->stream))) return rc;
+  const bool dev = b->flags & MRV_PTRS_ON_DEVICE;
+  BatchDev B = make_batchdev(c, b, S, MRV_KIND_MV, 1);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+  if (e == cudaSuccess) e = launch_prepare(B, st);
+  if (e != cudaSuccess) return cuda_fail(e, "prepare");
+  // the query's sphere count bounds the output; read it back
+  QueryDev hq;
+  if ((e = cudaMemcpyAsync(&hq, S.q + q, sizeof hq, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(e, "query record copy");
+  if (hq.bits & 4u) {
+    uint32_t err = 0;
+    cudaMemcpy(&err, S.err, sizeof err, cudaMemcpyDeviceToHost);
+    return check_device_err(err ? err : kErrRobots);
+  }
+  const int32_t *d_ts = ts;
+  float *d_out = out;
+  void *tmp = nullptr;
+  if (!dev) {
+    const size_t bytes = sizeof(int32_t) * nt + sizeof(float) * (size_t)nt * hq.M;
+    if ((e = cudaMalloc(&tmp, bytes)) != cudaSuccess) return cuda_fail(e, "clearance buffers");
+    d_ts = (const int32_t *)tmp;
+    d_out = (float *)((char *)tmp + sizeof(int32_t) * nt);
+    e = cudaMemcpyAsync((void *)d_ts, ts, sizeof(int32_t) * nt, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = launch_clearance(B, q, d_ts, nt, (b->flags & MRV_CHECK_ENV) ? 1 : 0, d_out, st);
+  if (e == cudaSuccess && !dev)
+    e = cudaMemcpyAsync(out, d_out, sizeof(float) * (size_t)nt * hq.M, cudaMemcpyDeviceToHost, st);
+  uint32_t err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "clearance");
+  err = c->h_status[0];
+  return check_device_err(err);
+}
+
+// ---- graphs -----------------------------------------------------------------
+
+int mrv_graph_create(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_conflict *conflict_out,
+                     mrv_graph **out) {
+  if (!c || !out) return fail(MRV_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  int rc = validate_batch(c, b);
+  if (rc) return rc;
+  if (!(b->flags & MRV_PTRS_ON_DEVICE)) return fail(MRV_ERR_ARG, "graphs need MRV_PTRS_ON_DEVICE");
+  if (b->flags & MRV_PER_QUERY_LAUNCH) return fail(MRV_ERR_ARG, "graphs replay the batched path only");
+  if (b->n_queries == 0) return fail(MRV_ERR_ARG, "empty batch");
+  if (!b->q_kind || !valid_out || !conflict_out) return fail(MRV_ERR_ARG, "graphs capture mrv_run: q_kind and both outputs needed");
+  if (c->pending && (rc = c->sync())) return rc;
+  cudaSetDevice(c->device);
+  mrv_graph *g = new (std::nothrow) mrv_graph();
+  if (!g) return fail(MRV_ERR_OOM, "graph allocation");
+  g->ctx = c;
+  if ((rc = g->scratch.ensure(b->n_queries, b->n_slots, b->n_waypoints, b->wp_stride, c->stream))) {
+    delete g;
+    return rc;
+  }
+  BatchDev B = make_batchdev(c, b, g->scratch, -1, c->tuning.chunk_tiles);
+  // attributes are set outside the capture
+  set_main_attrs(c->tuning.warps_per_block);
+  grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm);
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g->scratch.release();
+    delete g;
+    return cuda_fail(e, "capture stream");
+  }
+  cudaStream_t saved = c->stream;
+  c->stream = cap;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = enqueue_run(c, B, g->scratch, false, valid_out, nullptr, conflict_out, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (rc == MRV_OK && e2 == cudaSuccess) {
+      e2 = cudaGraphInstantiate(&g->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e2 != cudaSuccess) rc = cuda_fail(e2, "graph instantiate");
+    } else if (rc == MRV_OK) {
+      rc = cuda_fail(e2, "graph capture");
+    }
+  } else {
+    rc = cuda_fail(e, "begin capture");
+  }
+  c->stream = saved;
+  cudaStreamDestroy(cap);
+  if (rc) {
+    g->scratch.release();
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return MRV_OK;
+}
+
+int mrv_graph_launch(mrv_graph *g) {
+  if (!g || !g->exec) return fail(MRV_ERR_ARG, "graph is NULL");
+  mrv_ctx *c = g->ctx;
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaGraphLaunch(g->exec, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  // status of the replay is read by the next mrv_sync
+  e = cudaMemcpyAsync(c->h_status, g->scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_stats, g->scratch.stats, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_counts, g->scratch.counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph status copy");
+  c->pending = true;
+  c->timed_pending = true;   // the graph records the context's timing events
+  return MRV_OK;
+}
+
+int mrv_graph_destroy(mrv_graph *g) {
+  if (!g) return MRV_OK;
+  cudaSetDevice(g->ctx->device);
+  cudaStreamSynchronize(g->ctx->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->scratch.release();
+  delete g;
+  return MRV_OK;
+}
+
+}  // extern "C"

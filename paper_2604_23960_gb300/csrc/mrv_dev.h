@@ -1,0 +1,107 @@
+// Device-side data layout shared by the host runtime and the kernels.
+//
+// Everything the kernels read lives in device memory owned by the context:
+//   ModelDev  one entry per uploaded robot model (indexed by robot id); DH
+//             rows are pre-split into cos/sin of alpha so the per-state chain
+//             needs one sincosf per joint.
+//   EnvDev    one entry per uploaded obstacle set (indexed by env slot).
+//   BatchDev  the ragged CSR batch (caller arrays or staged copies) plus the
+//             per-query / per-slot arrays derived on the device.
+#pragma once
+#include <stdint.h>
+
+#include "../../include/mrv.h"
+
+namespace mrv {
+
+constexpr int kWarp = 32;             // lanes per tile (the GPU's batch width W)
+constexpr int kMaxLinks = MRV_MAX_DOF + 2;  // frames 0..dof+1
+constexpr int kMaxLevels = 64;        // work levels (chunks per query)
+constexpr int kEnvIdBase = 1 << 20;   // env ids = kEnvIdBase + env slot
+constexpr int kFkChains = 16;         // (state, robot) chains per FK round
+
+// device error bits (BatchDev::err)
+enum : uint32_t {
+  kErrRobotId = 1u << 0,
+  kErrEnvId = 1u << 1,
+  kErrRobots = 1u << 2,      // 0 or > MRV_MAX_ROBOTS robots, or bad offsets
+  kErrWaypoints = 1u << 3,   // bad waypoint offsets / counts
+  kErrSteps = 1u << 4,       // negative steps or T > MRV_MAX_STEPS
+  kErrSpheres = 1u << 5,     // > MRV_MAX_QUERY_SPHERES spheres in a query
+  kErrDof = 1u << 6,         // wp_stride < dof
+  kErrTimeout = 1u << 7,     // persistent kernel exceeded its clock budget
+  kErrAbort = 1u << 8,       // abort flag observed
+};
+
+struct ModelDev {
+  int32_t kind, dof, n_spheres, n_self;
+  int32_t live;
+  float point_z;
+  float base[12];
+  float flange[12];
+  float dh[MRV_MAX_DOF][5];      // cos(alpha), sin(alpha), a, d, theta_offset
+  const float4 *spheres;         // local xyz, radius
+  const int32_t *sphere_link;
+  const int2 *self_pairs;
+};
+
+struct EnvDev {
+  int32_t n_spheres, n_aabbs;
+  int32_t live, pad;
+  const float4 *spheres;         // world xyz, radius
+  const float *aabbs;            // n x 6
+};
+
+// per-query derived record (written by the preparation kernel)
+struct QueryDev {
+  int32_t T;          // composite step count (states 0..T)
+  int32_t n;          // robots
+  int32_t M;          // spheres summed over robots
+  int32_t ntiles;     // 32-state tiles
+  int32_t nchunks;    // work items of this query
+  int32_t cte;        // tiles per work item
+  int32_t env;        // env slot or -1
+  uint32_t bits;      // bit 0: FFC, bit 1: flavor A (lane = state), bit 2: invalid
+  long long pairtests;  // robot-robot sphere tests per state
+  long long envtests;   // robot-obstacle + self tests per state (MV with env)
+};
+
+struct BatchDev {
+  int32_t n_queries, n_slots, n_waypoints, wp_stride;
+  uint32_t flags;
+  float resolution;
+  int32_t default_env;               // env slot or -1
+  int32_t pad0;
+  const int32_t *q_robot_off;
+  const int32_t *slot_robot_id;
+  const int32_t *slot_wp_off;
+  const float *waypoints;
+  const int32_t *seg_steps;          // may be null (start/goal form)
+  const int32_t *q_env_id;           // may be null
+  const uint8_t *q_kind;             // may be null (all MV unless forced)
+  int32_t forced_kind;               // -1 = q_kind, else MRV_KIND_*
+  int32_t chunk_tiles;
+  // derived (device scratch)
+  int32_t *slot_tau;                 // n_waypoints: time of each waypoint
+  QueryDev *q;                       // n_queries
+  int32_t *q_hit;                    // MV: 1 once a collision is found
+  int32_t *q_best;                   // FFC: min key t*32 + pair index
+  float *q_minclr;                   // exhaustive MV: min clearance (as ordered int)
+  int32_t *sorted;                   // queries sorted by nchunks (desc)
+  int32_t *hist;                     // kMaxLevels + 1 bins
+  int32_t *level_start;              // kMaxLevels + 1
+  int32_t *cursor;                   // kMaxLevels + 1
+  int32_t *counters;                 // [0] work counter, [1] n_items, [2] abort flag
+  uint32_t *err;
+  unsigned long long *stats;         // [0] states checked, [1] sphere tests,
+                                     // [2] states available, [3] tests available,
+                                     // [4] items
+  // tables
+  const ModelDev *models;
+  int32_t n_models;
+  const EnvDev *envs;
+  int32_t n_envs;
+  long long clock_budget;            // persistent kernel: clock64 ticks (0 = none)
+};
+
+}  // namespace mrv

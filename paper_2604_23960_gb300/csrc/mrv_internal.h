@@ -1,0 +1,124 @@
+// Host-side types of the runtime (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mrv_dev.h"
+
+namespace mrv {
+
+extern thread_local std::string g_err;
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// device scratch of one run: derived per-query arrays, counters, staged
+// inputs and outputs; one arena, grown on demand, carved at 256-byte offsets
+struct Scratch {
+  void *base = nullptr;
+  size_t cap = 0;
+  int32_t *slot_tau = nullptr;
+  QueryDev *q = nullptr;
+  int32_t *q_hit = nullptr, *q_best = nullptr;
+  float *q_minclr = nullptr;
+  int32_t *sorted = nullptr, *hist = nullptr, *level_start = nullptr, *cursor = nullptr;
+  int32_t *counters = nullptr;
+  uint32_t *err = nullptr;
+  unsigned long long *stats = nullptr;
+  int32_t *counts = nullptr;
+  int32_t *in_q_off = nullptr, *in_slot_robot = nullptr, *in_slot_wp = nullptr, *in_steps = nullptr,
+          *in_q_env = nullptr;
+  float *in_wp = nullptr;
+  uint8_t *in_q_kind = nullptr;
+  uint8_t *out_valid = nullptr;
+  float *out_minclr = nullptr;
+  mrv_conflict *out_conf = nullptr;
+
+  static size_t bytes_for(int64_t nq, int64_t ns, int64_t nw, int64_t stride);
+  int ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStream_t st);
+  void release();
+};
+
+struct HostModel {
+  ModelDev dev{};
+  void *d_spheres = nullptr, *d_links = nullptr, *d_self = nullptr;
+  int refs = 0;
+  int max_spheres = 0;
+  void free_all() {
+    if (d_spheres) cudaFree(d_spheres);
+    if (d_links) cudaFree(d_links);
+    if (d_self) cudaFree(d_self);
+    d_spheres = d_links = d_self = nullptr;
+  }
+};
+
+struct HostEnv {
+  EnvDev dev{};
+  void *d_spheres = nullptr, *d_aabbs = nullptr;
+  int refs = 0;
+  void free_all() {
+    if (d_spheres) cudaFree(d_spheres);
+    if (d_aabbs) cudaFree(d_aabbs);
+    d_spheres = d_aabbs = nullptr;
+  }
+};
+
+// kernel launch wrappers (mrv_kernels.cu)
+size_t main_smem_bytes(int warps);
+cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st);
+cudaError_t set_main_attrs(int warps);
+cudaError_t max_blocks_per_sm(int warps, bool clr, int *out);
+cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int q_single, cudaStream_t st);
+cudaError_t launch_finish(const BatchDev &B, uint8_t *valid, float *minclr, mrv_conflict *conf, int *counts,
+                          cudaStream_t st);
+cudaError_t launch_clearance(const BatchDev &B, int q, const int32_t *ts, int nt, int check_env, float *out,
+                             cudaStream_t st);
+
+}  // namespace mrv
+
+struct mrv_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  std::string device_name;
+  std::vector<mrv::HostModel> models;
+  std::vector<mrv::HostEnv> envs;
+  mrv::ModelDev *d_models = nullptr;
+  mrv::EnvDev *d_envs = nullptr;
+  size_t cap_models = 0, cap_envs = 0;
+  mrv::Scratch scratch;
+  mrv_tuning tuning{4, 4, 0, 0};
+  mrv_stats stats{};
+  long long clock_budget = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  void *h_pinned = nullptr;
+  uint32_t *h_status = nullptr;
+  unsigned long long *h_stats = nullptr;
+  int32_t *h_counts = nullptr;
+  bool pending = false, timed_pending = false;
+
+  int env_slot(int32_t id) const;
+  int push_tables();
+  int sync();
+};
+
+struct mrv_graph {
+  mrv_ctx *ctx = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  mrv::Scratch scratch;
+};
+
+namespace mrv {
+int validate_batch(mrv_ctx *ctx, const mrv_batch *b);
+BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int chunk_tiles);
+int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+                mrv_conflict *conf, bool timed);
+int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+                   mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st);
+int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr, mrv_conflict *conf);
+int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm);
+int check_device_err(uint32_t err);
+}  // namespace mrv

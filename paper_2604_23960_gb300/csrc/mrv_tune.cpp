@@ -1,0 +1,135 @@
+// Autotuner of the persistent scheduler: picks tiles per work item, warps
+// per block and blocks per SM for a batch class by timing candidates on the
+// batch itself (CUDA events around the persistent kernel), and caches the
+// winner in a text file keyed by device name and batch class.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+
+#include "mrv_internal.h"
+
+namespace mrv {
+
+static int bucket_log2(double x) { return x <= 1 ? 0 : (int)std::floor(std::log2(x)); }
+
+// class of a batch: device, query-kind mix, median robots / spheres / states
+static int batch_class(mrv_ctx *c, const mrv_batch *b, std::string *key) {
+  Scratch &S = c->scratch;
+  int rc = S.ensure(b->n_queries, b->n_slots, b->n_waypoints, b->wp_stride, c->stream);
+  if (rc) return rc;
+  BatchDev B = make_batchdev(c, b, S, -1, 1);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+  if (e == cudaSuccess) e = launch_prepare(B, st);
+  std::vector<QueryDev> hq(b->n_queries);
+  uint32_t err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), S.q, sizeof(QueryDev) * hq.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, S.err, sizeof err, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune class");
+  if (err) return check_device_err(err);
+  std::vector<int> n, m, t;
+  int ffc = 0;
+  for (auto &q : hq) {
+    n.push_back(q.n);
+    m.push_back(q.M);
+    t.push_back(q.T);
+    ffc += q.bits & 1u;
+  }
+  auto med = [](std::vector<int> &v) {
+    std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+    return v[v.size() / 2];
+  };
+  std::ostringstream o;
+  o << c->device_name << "|ffc" << (10 * ffc / (int)hq.size()) << "|n" << med(n) << "|m" << bucket_log2(med(m))
+    << "|t" << bucket_log2(med(t) + 1) << "|f" << (b->flags & (MRV_CHECK_ENV | MRV_EXHAUSTIVE));
+  std::string k = o.str();
+  for (auto &ch : k)
+    if (ch == ' ') ch = '_';
+  *key = k;
+  return MRV_OK;
+}
+
+static bool cache_lookup(const char *path, const std::string &key, mrv_tuning *t) {
+  if (!path) return false;
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream in(line);
+    std::string k;
+    mrv_tuning c{};
+    if (in >> k >> c.chunk_tiles >> c.warps_per_block >> c.blocks_per_sm && k == key) {
+      *t = c;
+      found = true;  // the last entry for a key wins
+    }
+  }
+  return found;
+}
+
+static void cache_store(const char *path, const std::string &key, const mrv_tuning &t) {
+  if (!path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << ' ' << t.chunk_tiles << ' ' << t.warps_per_block << ' ' << t.blocks_per_sm << '\n';
+}
+
+}  // namespace mrv
+
+using namespace mrv;
+
+extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_path, mrv_tuning *chosen) {
+  if (!c || !b) return fail(MRV_ERR_ARG, "NULL argument");
+  int rc = validate_batch(c, b);
+  if (rc) return rc;
+  if (!(b->flags & MRV_PTRS_ON_DEVICE) || !b->q_kind)
+    return fail(MRV_ERR_ARG, "autotune needs a device batch with q_kind (mrv_run semantics)");
+  if (b->flags & (MRV_ASYNC | MRV_PER_QUERY_LAUNCH)) return fail(MRV_ERR_ARG, "autotune runs synchronous batched calls");
+  if (b->n_queries == 0) return fail(MRV_ERR_ARG, "empty batch");
+  if (c->pending && (rc = c->sync())) return rc;
+  cudaSetDevice(c->device);
+  std::string key;
+  if ((rc = batch_class(c, b, &key))) return rc;
+  mrv_tuning best = c->tuning;
+  if (cache_lookup(cache_path, key, &best)) {
+    c->tuning = best;
+    if (chosen) *chosen = best;
+    return MRV_OK;
+  }
+  void *outs = nullptr;
+  cudaError_t e = cudaMalloc(&outs, (size_t)b->n_queries * (1 + sizeof(mrv_conflict)) + 256);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune outputs");
+  mrv_conflict *conf = (mrv_conflict *)outs;
+  uint8_t *valid = (uint8_t *)outs + ((size_t)b->n_queries * sizeof(mrv_conflict) + 255) / 256 * 256;
+  const mrv_tuning saved = c->tuning;
+  float best_ms = INFINITY;
+  static const int chunks[] = {1, 2, 4, 8, 16};
+  static const int warps[] = {2, 4, 8};
+  for (int w : warps)
+    for (int ch : chunks) {
+      mrv_tuning t{ch, w, 0, 0};
+      c->tuning = t;
+      float total = 0.f;
+      for (int rep = 0; rep < 3 && rc == MRV_OK; ++rep) {
+        rc = run_batch(c, b, -1, valid, nullptr, conf);
+        if (rep > 0) total += c->stats.device_ms;   // first run warms caches
+      }
+      if (rc) break;
+      if (total < best_ms) {
+        best_ms = total;
+        best = t;
+      }
+    }
+  cudaFree(outs);
+  if (rc) {
+    c->tuning = saved;
+    return rc;
+  }
+  c->tuning = best;
+  cache_store(cache_path, key, best);
+  if (chosen) *chosen = best;
+  return MRV_OK;
+}

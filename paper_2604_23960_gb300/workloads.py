@@ -472,3 +472,51 @@ def subset(w: Workload, idx) -> Workload:
                int(b.q_env[q]) if b.q_env is not None else w.env)
     nb = bb.build(b.resolution)
     return Workload(w.name + f"[{len(idx)}]", w.models, w.envs, nb, w.env, w.check_env, dict(w.meta))
+
+
+# ---------------------------------------------------------------------------
+# serving: four request families over four resident environments
+# ---------------------------------------------------------------------------
+
+def make_serving_families(n_per_family: int = 20000, seed: int = 206, fixtures: Optional[dict] = None,
+                          len_range=(8, 512)):
+    """Four query families sharing one model list and one env list, all in
+    the timed form with one segment per robot and L ~ logU[8, 512] steps:
+    0: 2-8 discs in the box world; 1: 2-4 cage arms (valid endpoints) in the
+    cage; 2: 2-4 cage arms without obstacles; 3: the ragged teams in the
+    padded box world.  Queries are MV or FFC with probability 1/2.
+    Returns (models, envs, [Workload per family])."""
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    arms = cage_arms(fx)
+    team = team_models(fx)
+    disc = disc_robot(0.25, 0.0, name="disc")
+    models = arms + team + [disc]            # 0-3 cage arms, 4-5 team arms, 6 team disc, 7 disc
+    envs = [world_boxes(101), cage_env(103), empty_env(), world_boxes(101, pad=TEAM_PAD)]
+    rng = np.random.default_rng(seed)
+    pools = fx["endpoint_pool"]
+    fams = []
+    for f in range(4):
+        bb = BatchBuilder(8, True)
+        for _ in range(n_per_family):
+            L = int(np.clip(round(math.exp(rng.uniform(math.log(len_range[0]), math.log(len_range[1])))),
+                            len_range[0], len_range[1]))
+            kind = int(rng.integers(0, 2))
+            if f == 0:
+                n = int(rng.integers(2, 9))
+                robots = [7] * n
+                paths = [rng.uniform(0.0, 10.0, (2, 2)) for _ in range(n)]
+            elif f in (1, 2):
+                n = int(rng.integers(2, 5))
+                robots = sorted(rng.choice(4, n, replace=False).tolist())
+                if f == 1:
+                    paths = [pools[r][rng.integers(0, pools.shape[1], 2)] for r in robots]
+                else:
+                    paths = [rng.uniform(PANDA_LO, PANDA_HI, (2, 7)) for _ in robots]
+            else:
+                nd = int(rng.integers(0, 7))
+                robots = [4, 5] + [6] * nd
+                paths = [rng.uniform(PANDA_LO, PANDA_HI, (2, 7)) for _ in range(2)] + \
+                        [rng.uniform(0.0, 10.0, (2, 2)) for _ in range(nd)]
+            bb.add(robots, paths, [[L]] * len(robots), kind, f if f != 2 else -1)
+        fams.append(Workload(f"serve{f}", models, envs, bb.build(), env=-1, check_env=True))
+    return models, envs, fams

@@ -1,0 +1,311 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Small cases are compared query by query in full (several 32-state tiles,
+ragged path lengths, every robot kind); the full-size workloads run in the
+launch configuration the benchmark times and are checked on sampled queries
+the oracle computes one by one.  Exact match is required on MV booleans and
+FFC (t, i, j) for every query whose oracle clearances keep 1e-4 m from zero;
+clearance values must agree within 1e-5 m.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2604_23960_gb300 import mrv
+from paper_2604_23960_gb300 import workloads as W
+from tests import parity as PA
+from tests.tiny import tiny_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    c = mrv.Context(0)
+    yield c
+    c.close()
+
+
+def _np(x):
+    return x if isinstance(x, np.ndarray) else x.cpu().numpy()
+
+
+# ------------------------------------------------------------------ tiny cases
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("timed", [True, False])
+def test_tiny_mv_ffc(ctx, seed, timed):
+    w = tiny_workload(1000 + seed, n_queries=40, timed=timed, max_steps=40, max_robots=4)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    for ce in (True, False):
+        v = ctx.mv_validate(ba, check_env=ce)
+        PA.check_mv(o, v, check_env=ce)
+        ve = ctx.mv_validate(ba, check_env=ce, exhaustive=True)
+        np.testing.assert_array_equal(v, ve)
+    c = ctx.ffc_find(ba)
+    PA.check_ffc(o, c)
+    np.testing.assert_array_equal(ctx.ffc_find(ba, exhaustive=True), c)
+    # device-resident batch: identical results
+    bd = ba.to("cuda")
+    np.testing.assert_array_equal(_np(ctx.mv_validate(bd)), ctx.mv_validate(ba))
+    np.testing.assert_array_equal(_np(ctx.ffc_find(bd)), c)
+    # one synchronous launch per query: identical results
+    np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_PER_QUERY_LAUNCH), ctx.mv_validate(ba))
+    np.testing.assert_array_equal(ctx.ffc_find(ba, flags=mrv.MRV_PER_QUERY_LAUNCH), c)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_min_clearance(ctx, seed):
+    w = tiny_workload(1100 + seed, n_queries=30, timed=True, max_steps=30)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    for ce in (True, False):
+        v, mc = ctx.mv_validate(ba, check_env=ce, exhaustive=True, min_clearance=True)
+        ref = o.mv_min_clearance(check_env=ce)
+        fin = np.isfinite(ref)
+        np.testing.assert_array_equal(np.isfinite(mc), fin)
+        np.testing.assert_allclose(mc[fin], ref[fin], atol=PA.CLR_TOL, rtol=0)
+
+
+def test_many_robots_mixed_kinds(ctx):
+    """Up to 8 robots per query, DH chains mixed with point robots."""
+    w = tiny_workload(1200, n_queries=60, timed=True, max_robots=8, n_models=8, max_steps=20)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    PA.check_mv(o, ctx.mv_validate(ba))
+    PA.check_ffc(o, ctx.ffc_find(ba))
+
+
+def test_clearance_diagnostic(ctx):
+    w = tiny_workload(1300, n_queries=8, timed=True, max_steps=12)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    T = o.query_T()
+    for q in range(w.batch.n_queries):
+        ts = list(range(0, int(T[q]) + 1, max(1, int(T[q]) // 5)))
+        M = sum(w.models[w.batch.slot_robot[s]].n_spheres
+                for s in range(w.batch.q_robot_off[q], w.batch.q_robot_off[q + 1]))
+        for ce in (True, False):
+            got = ctx.clearance(ba, q, ts, M, check_env=ce)
+            ref = o.clearance(q, ts, check_env=ce)
+            fin = np.isfinite(ref)
+            np.testing.assert_array_equal(np.isfinite(got), fin)
+            np.testing.assert_allclose(got[fin], ref[fin], atol=PA.CLR_TOL, rtol=0)
+
+
+# ------------------------------------------------- workload-shaped small cases
+
+def test_discs_full(ctx):
+    """Two disc robots in the box world: all 1,000 queries, MV and FFC."""
+    w = W.make_plain_discs(1000)
+    o = O.Oracle(w)
+    ba = ctx.bind(w).to("cuda")
+    v = _np(ctx.mv_validate(ba))
+    c = _np(ctx.ffc_find(ba))
+    _, und_mv = PA.check_mv(o, v)
+    _, und_ffc = PA.check_ffc(o, c)
+    assert und_mv < 5 and und_ffc < 5
+    st = ctx.stats()
+    assert st["states_checked"] <= st["states_available"]
+
+
+def test_cage_mv_small_exhaustive(ctx):
+    w = W.make_cage_mv(96)
+    o = O.Oracle(w)
+    ba = ctx.bind(w).to("cuda")
+    v = _np(ctx.mv_validate(ba))
+    PA.check_mv(o, v)
+    v2, mc = ctx.mv_validate(ba, exhaustive=True, min_clearance=True)
+    np.testing.assert_array_equal(_np(v2), v)
+    ref = o.mv_min_clearance(threads=PA.THREADS)
+    np.testing.assert_allclose(_np(mc), ref, atol=PA.CLR_TOL, rtol=0)
+    st = ctx.stats()
+    assert st["states_checked"] == st["states_available"]
+    assert st["sphere_tests"] == st["sphere_tests_available"]
+
+
+def test_cage_ffc_small(ctx):
+    w = W.make_cage_ffc(64)
+    o = O.Oracle(w)
+    ba = ctx.bind(w).to("cuda")
+    c = _np(ctx.ffc_find(ba))
+    PA.check_ffc(o, c)
+    np.testing.assert_array_equal(_np(ctx.ffc_find(ba, exhaustive=True)), c)
+
+
+def test_ragged_teams_small_mixed(ctx):
+    w = W.make_ragged_teams(400, seed=905)
+    o = O.Oracle(w)
+    ba = ctx.bind(w).to("cuda")
+    v, c = ctx.run(ba)
+    v, c = _np(v), _np(c)
+    kind = w.batch.q_kind
+    mv_idx, ffc_idx = np.nonzero(kind == 0)[0], np.nonzero(kind == 1)[0]
+    PA.check_mv(o, v[mv_idx], mv_idx)
+    PA.check_ffc(o, c[ffc_idx], ffc_idx)
+    # the same queries through the single-kind entry points
+    np.testing.assert_array_equal(_np(ctx.mv_validate(ba))[mv_idx], v[mv_idx])
+    np.testing.assert_array_equal(_np(ctx.ffc_find(ba))[ffc_idx], c[ffc_idx])
+
+
+# --------------------------------------------------------------- edge cases
+
+def _one_query(models, paths, steps=None, env=None, res=0.1, check_env=True):
+    bb = W.BatchBuilder(max(m.dof for m in models), steps is not None)
+    bb.add(list(range(len(models))), paths, steps, 0, 0 if env is not None else -1)
+    return W.Workload("edge", models, [env] if env is not None else [], bb.build(res), 0 if env is not None else -1,
+                      check_env)
+
+
+def test_empty_batch(ctx):
+    w = W.make_plain_discs(4)
+    ba = ctx.bind(w)
+    ba.n_queries = 0
+    assert ctx.mv_validate(ba).shape == (0,)
+    assert ctx.ffc_find(ba).shape == (0, 3)
+
+
+def test_single_robot_and_stationary(ctx):
+    env = W.world_boxes(3)
+    d = W.disc_robot(0.25)
+    # one robot: FFC has no pair, MV checks obstacles only
+    w = _one_query([d], [np.array([[0.1, 0.1], [9.9, 9.9]])], env=env)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    PA.check_mv(o, ctx.mv_validate(ba))
+    assert list(ctx.ffc_find(ba)[0]) == [-1, -1, -1]
+    # no motion at all: T = 0, one state
+    w0 = _one_query([d, d], [np.array([[1.0, 1.0], [1.0, 1.0]]), np.array([[1.2, 1.0], [1.2, 1.0]])])
+    assert O.Oracle(w0).query_T()[0] == 0
+    ba0 = ctx.bind(w0)
+    assert ctx.mv_validate(ba0)[0] == 0
+    assert list(ctx.ffc_find(ba0)[0]) == [0, 0, 1]
+
+
+def test_eight_arms_max_spheres(ctx):
+    """8 arms x 64 spheres = 512 spheres, the per-query maximum."""
+    fx = W.load_cage_fixtures()
+    arms = [W.panda_like(W._pose(1.3 * np.cos(a), 1.3 * np.sin(a), 0.0, a + np.pi), fx["self_pairs"])
+            for a in np.linspace(0, 2 * np.pi, 8, endpoint=False)]
+    rng = np.random.default_rng(5)
+    bb = W.BatchBuilder(7, True)
+    for _ in range(6):
+        paths = [rng.uniform(W.PANDA_LO, W.PANDA_HI, (3, 7)) for _ in arms]
+        bb.add(list(range(8)), paths, [rng.integers(10, 40, 2) for _ in arms], 0, -1)
+    w = W.Workload("eight", arms, [], bb.build(), -1, True)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    PA.check_mv(o, ctx.mv_validate(ba))
+    PA.check_ffc(o, ctx.ffc_find(ba))
+
+
+def test_errors_are_reported(ctx):
+    w = W.make_plain_discs(4)
+    ba = ctx.bind(w)
+    bad = ba.a["slot_robot_id"].copy()
+    bad[1] = 12345
+    ba2 = mrv.BatchArrays(dict(ba.a, slot_robot_id=bad), ba.n_queries, ba.n_slots, ba.n_waypoints, ba.wp_stride,
+                          ba.resolution, ba.env_id, False)
+    with pytest.raises(mrv.MrvError) as e:
+        ctx.mv_validate(ba2)
+    assert e.value.code == -3
+    # timed form needs >= 1 step per segment
+    wt = tiny_workload(7, n_queries=3, timed=True)
+    bt = ctx.bind(wt)
+    st = bt.a["seg_steps"].copy()
+    st[0] = 0
+    bt2 = mrv.BatchArrays(dict(bt.a, seg_steps=st), bt.n_queries, bt.n_slots, bt.n_waypoints, bt.wp_stride,
+                          bt.resolution, bt.env_id, False)
+    if wt.batch.slot_wp_off[1] - wt.batch.slot_wp_off[0] > 1:
+        with pytest.raises(mrv.MrvError):
+            ctx.ffc_find(bt2)
+    # too many robots in a query
+    d = W.disc_robot(0.1)
+    nine = _one_query([d] * 9, [np.array([[i, 0.0], [i, 1.0]]) for i in range(9)])
+    with pytest.raises(mrv.MrvError) as e:
+        ctx.mv_validate(ctx.bind(nine))
+    assert e.value.code == -7
+    # the context stays usable
+    PA.check_mv(O.Oracle(w), ctx.mv_validate(ba))
+
+
+def test_repeatable_and_graph_replay(ctx):
+    import torch
+    w = W.make_ragged_teams(3000, seed=77)
+    ba = ctx.bind(w).to("cuda")
+    v1, c1 = ctx.run(ba)
+    v2, c2 = ctx.run(ba)
+    assert torch.equal(v1, v2) and torch.equal(c1, c2)
+    vg = torch.full_like(v1, 7)
+    cg = torch.full_like(c1, 7)
+    g = mrv.mrv_graph_create(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), vg, cg)
+    for _ in range(3):
+        mrv.mrv_graph_launch(g)
+        ctx.sync()
+        kind = torch.as_tensor(w.batch.q_kind, device="cuda")
+        assert torch.equal(vg[kind == 0], v1[kind == 0])
+        assert torch.equal(cg[kind == 1], c1[kind == 1])
+    mrv.mrv_graph_destroy(g)
+
+
+def test_tunings_do_not_change_results(ctx, tmp_path):
+    import torch
+    w = W.make_ragged_teams(2000, seed=78)
+    ba = ctx.bind(w).to("cuda")
+    mvq = torch.as_tensor(w.batch.q_kind == 0, device="cuda")
+    ffq = ~mvq
+
+    def same(a, b):   # mrv_run leaves the other kind's output untouched
+        return torch.equal(a[0][mvq], b[0][mvq]) and torch.equal(a[1][ffq], b[1][ffq])
+
+    ref = ctx.run(ba)
+    saved = mrv.mrv_get_tuning(ctx.h)
+    for ch, wp in [(1, 2), (2, 8), (16, 4)]:
+        mrv.mrv_set_tuning(ctx.h, ch, wp, 0)
+        assert same(ctx.run(ba), ref)
+    t = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
+    assert t["chunk_tiles"] >= 1 and t["warps_per_block"] >= 1
+    assert (tmp_path / "tune.txt").read_text().strip()
+    t2 = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
+    assert t2 == t   # cached
+    assert same(ctx.run(ba), ref)
+    mrv.mrv_set_tuning(ctx.h, saved["chunk_tiles"], saved["warps_per_block"], saved["blocks_per_sm"])
+
+
+# --------------------------------------------- full sizes, benchmark launches
+
+def test_full_cage_mv_10k(ctx):
+    w = W.make_cage_mv(10000)
+    ba = ctx.bind(w).to("cuda")
+    v = _np(ctx.mv_validate(ba))
+    idx = PA.sample(w.batch.n_queries, 300, seed=1)
+    PA.check_mv(O.Oracle(w), v[idx], idx)
+
+
+def test_full_cage_ffc_100k(ctx):
+    w = W.make_cage_ffc(100000)
+    ba = ctx.bind(w).to("cuda")
+    c = _np(ctx.ffc_find(ba))
+    idx = PA.sample(w.batch.n_queries, 150, seed=2)
+    PA.check_ffc(O.Oracle(w), c[idx], idx)
+    # every reported conflict time lies inside its query
+    T = c[:, 0]
+    assert np.all((T == -1) | (T >= 0))
+    assert np.all((c[:, 1] < c[:, 2]) | (c[:, 0] == -1))
+
+
+def test_full_ragged_1m(ctx):
+    w = W.make_ragged_teams(1_000_000)
+    ba = ctx.bind(w).to("cuda")
+    v, c = ctx.run(ba)
+    v, c = _np(v), _np(c)
+    idx = PA.sample(w.batch.n_queries, 200, seed=3)
+    kind = w.batch.q_kind[idx]
+    o = O.Oracle(w)
+    PA.check_mv(o, v[idx[kind == 0]], idx[kind == 0])
+    PA.check_ffc(o, c[idx[kind == 1]], idx[kind == 1])
