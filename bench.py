@@ -61,7 +61,8 @@ class Clocks:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                       "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)   # let the sampler start before the measured work
         except OSError:
             self.p = None
         return self
@@ -238,18 +239,20 @@ def run(args):
     def step():
         mrv.mrv_graph_launch(graph)
 
-    # warm-up (also validates the run)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-            ctx.sync()
-    stats = ctx.stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kern_ms = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+    # clocks are sampled from the warm-up through the end of the timed steps
+    torch.cuda.nvtx.range_push("timed")
     with Clocks(local) as clk:
+        # warm-up (also validates the run)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+                ctx.sync()
+        stats = ctx.stats()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             for i in range(args.steps):
                 flush.zero_()
@@ -259,6 +262,7 @@ def run(args):
                 ctx.sync()
                 kern_ms.append(ctx.stats()["device_ms"])
         torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -298,6 +302,7 @@ def run(args):
     assert torch.equal(pq_valid, valid[:pq_n])
 
     # exhaustive pass (every check of every state): the roofline of the kernel
+    torch.cuda.nvtx.range_push("exhaustive")
     ctx.mv_validate(ba, exhaustive=True)
     ex_ms = []
     for _ in range(3):
@@ -305,6 +310,7 @@ def run(args):
         ctx.mv_validate(ba, exhaustive=True)
         ex_ms.append(ctx.stats()["device_ms"])
     ex_stats = ctx.stats()
+    torch.cuda.nvtx.range_pop()
 
     peaks, src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -353,7 +359,7 @@ def run(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrv", choices=["mrv", "reference"])
     ap.add_argument("--queries", type=int, default=10000)

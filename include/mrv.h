@@ -202,15 +202,21 @@ typedef struct {
   uint64_t work_items;       /* persistent-scheduler items                   */
   int32_t n_valid, n_conflicts;
   float device_ms;           /* kernel time of the last call (CUDA events)   */
+  uint64_t box_tests;        /* the sphere-box part of sphere_tests           */
 } mrv_stats;
 int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
 
-/* ---- scheduling knobs (persistent work-stealing kernel) ------------------ */
+/* ---- scheduling knobs (persistent work-stealing kernel) ------------------
+ * Work is cut into slices: a 32-state tile of a query split into tile_split
+ * slices (MV: rake lanes l = p, p+split, ...; FFC: consecutive states); a
+ * work item is slices_per_item consecutive slices of one query. */
 typedef struct {
-  int32_t chunk_tiles;       /* 32-state tiles per work item (>= 1)          */
-  int32_t warps_per_block;   /* 1..12 (16 KB of shared memory per warp)      */
+  int32_t slices_per_item;   /* slices per work item (>= 1)                  */
+  int32_t warps_per_block;   /* 1..12 (17 KB of shared memory per warp)      */
   int32_t blocks_per_sm;     /* 0 = as many as fit                           */
-  int32_t fk_states;         /* states per FK round (<= 16 / robots)        */
+  int32_t tile_split;        /* 1, 2, 4 or 8 slices per 32-state tile for
+                                kinematic-chain queries (point-robot queries
+                                always use whole tiles)                      */
 } mrv_tuning;
 int mrv_set_tuning(mrv_ctx *ctx, const mrv_tuning *t);
 int mrv_get_tuning(mrv_ctx *ctx, mrv_tuning *t);

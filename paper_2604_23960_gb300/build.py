@@ -17,7 +17,7 @@ LIB = PKG / "libmrv.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mrv_kernels.cu"]
-CPP_SOURCES = ["mrv_api.cpp", "mrv_tune.cpp", "mrv_server.cpp"]
+CPP_SOURCES = ["mrv_api.cpp", "mrv_tune.cpp", "mrv_server.cpp", "mrv_geometry.cpp"]
 
 
 def _cuda_home() -> Path:

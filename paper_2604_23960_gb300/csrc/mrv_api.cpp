@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 
 namespace mrv {
 
@@ -154,7 +155,7 @@ int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
   return MRV_OK;
 }
 
-BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int chunk_tiles) {
+BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int slices_per_item) {
   BatchDev B;
   std::memset(&B, 0, sizeof B);
   B.n_queries = b->n_queries;
@@ -173,7 +174,8 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
   B.q_env_id = b->q_env_id ? (dev ? b->q_env_id : S.in_q_env) : nullptr;
   B.q_kind = b->q_kind ? (dev ? b->q_kind : S.in_q_kind) : nullptr;
   B.forced_kind = forced_kind;
-  B.chunk_tiles = chunk_tiles;
+  B.slices_per_item = slices_per_item;
+  B.tile_split = ctx->tuning.tile_split;
   B.slot_tau = S.slot_tau;
   B.q = S.q;
   B.q_hit = S.q_hit;
@@ -240,11 +242,15 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   if ((e = launch_prepare(B, st)) != cudaSuccess) return cuda_fail(e, "prepare launch");
   const int warps = ctx->tuning.warps_per_block;
   if ((e = set_main_attrs(warps)) != cudaSuccess) return cuda_fail(e, "kernel attributes");
-  // external records become event nodes when the stream is being captured
-  if (ev0) cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal);
+  // while the stream is captured, timing events must be external records to
+  // become event nodes of the graph; outside capture they are plain records
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return cuda_fail(e, "capture status");
+  const unsigned rec_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (ev0 && (e = cudaEventRecordWithFlags(ev0, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
   e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm), warps, clr, -1, st);
   if (e != cudaSuccess) return cuda_fail(e, "main launch");
-  if (ev1) cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal);
+  if (ev1 && (e = cudaEventRecordWithFlags(ev1, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
   if ((e = launch_finish(B, valid, minclr, conf, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish launch");
   return MRV_OK;
 }
@@ -292,6 +298,7 @@ int mrv_ctx::sync() {
   stats.states_available = h_stats[2];
   stats.sphere_tests_available = h_stats[3];
   stats.work_items = h_stats[4];
+  stats.box_tests = h_stats[5];
   stats.n_valid = h_counts[0];
   stats.n_conflicts = h_counts[1];
   float ms = 0.f;
@@ -321,7 +328,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
   const bool dev = b->flags & MRV_PTRS_ON_DEVICE;
   const bool clr = minclr != nullptr;
   const bool per_query = b->flags & MRV_PER_QUERY_LAUNCH;
-  BatchDev B = make_batchdev(ctx, b, S, forced_kind, per_query ? 1 : ctx->tuning.chunk_tiles);
+  BatchDev B = make_batchdev(ctx, b, S, forced_kind, per_query ? 1 : ctx->tuning.slices_per_item);
   uint8_t *v_dst = valid ? (dev ? valid : S.out_valid) : nullptr;
   float *m_dst = minclr ? (dev ? minclr : S.out_minclr) : nullptr;
   mrv_conflict *c_dst = conf ? (dev ? conf : S.out_conf) : nullptr;
@@ -534,13 +541,34 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
       D.dh[k][3] = r[2];
       D.dh[k][4] = r[3];
     }
+  for (int s = 0; s < d->n_spheres; ++s) D.r2max = std::max(D.r2max, d->sphere_xyzr[4 * s + 3] * d->sphere_xyzr[4 * s + 3]);
+  // self pairs as (smaller, larger) index, sorted: neighbouring lanes then
+  // read the same or adjacent spheres
+  std::vector<std::pair<int32_t, int32_t>> sp(d->n_self_pairs);
+  for (int p = 0; p < d->n_self_pairs; ++p)
+    sp[p] = std::minmax(d->self_pairs[2 * p], d->self_pairs[2 * p + 1]);
+  std::sort(sp.begin(), sp.end());
+  // packed x | y << 16; the tail up to a multiple of 4 repeats the last pair
+  // (the kernel reads four pairs per load; a repeated pair changes no verdict)
+  std::vector<uint32_t> spf((sp.size() + 3) / 4 * 4);
+  for (size_t p = 0; p < spf.size(); ++p) {
+    const auto &e = sp[std::min(p, sp.size() - 1)];
+    spf[p] = (uint32_t)e.first | ((uint32_t)e.second << 16);
+  }
   int rc;
   if ((rc = upload(&m.d_spheres, d->sphere_xyzr, sizeof(float) * 4 * d->n_spheres))) return rc;
   if ((rc = upload(&m.d_links, d->sphere_link, sizeof(int32_t) * d->n_spheres))) { m.free_all(); return rc; }
-  if ((rc = upload(&m.d_self, d->self_pairs, sizeof(int32_t) * 2 * d->n_self_pairs))) { m.free_all(); return rc; }
+  if ((rc = upload(&m.d_self, spf.data(), sizeof(uint32_t) * spf.size()))) { m.free_all(); return rc; }
+  // rectangles pay off only when they are large enough to fill a warp's
+  // 4-rows-per-lane tiling; small ones stay on the sparse pair path
+  std::vector<int32_t> rects = self_pair_rectangles(d->n_spheres, sp, 256);
+  if (!rects.empty() && (int64_t)sp.size() < 64 * (int64_t)(rects.size() / 4)) rects.clear();
+  if ((rc = upload(&m.d_rects, rects.data(), sizeof(int32_t) * rects.size()))) { m.free_all(); return rc; }
+  D.self_rects = (const int4 *)m.d_rects;
+  D.n_rects = (int32_t)rects.size() / 4;
   D.spheres = (const float4 *)m.d_spheres;
   D.sphere_link = (const int32_t *)m.d_links;
-  D.self_pairs = (const int2 *)m.d_self;
+  D.self_pairs = (const uint32_t *)m.d_self;
   m.refs = 1;
   m.max_spheres = d->n_spheres;
   c->models.push_back(m);
@@ -562,16 +590,45 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
       if (!(d->aabb_lohi[6 * i + k] <= d->aabb_lohi[6 * i + 3 + k]))
         return fail(MRV_ERR_ARG, "box %d has lo > hi on axis %d", i, k);
   cudaSetDevice(c->device);
+  for (int i = 0; i < d->n_spheres; ++i) {
+    const float *x = d->spheres_xyzr + 4 * i;
+    if (!(std::isfinite(x[0]) && std::isfinite(x[1]) && std::isfinite(x[2]) && std::isfinite(x[3]) && x[3] >= 0.f))
+      return fail(MRV_ERR_ARG, "obstacle sphere %d not finite or radius < 0", i);
+  }
   HostEnv h;
   std::memset(&h.dev, 0, sizeof h.dev);
+  // per obstacle sphere k = |c|^2 - r^2 (double, rounded once), and the
+  // largest |c|^2 and r^2 that bound the rounding of the kernel's test
+  std::vector<float> k(d->n_spheres);
+  double c2max = 0.0, r2max = 0.0;
+  for (int i = 0; i < d->n_spheres; ++i) {
+    const float *x = d->spheres_xyzr + 4 * i;
+    const double c2 = (double)x[0] * x[0] + (double)x[1] * x[1] + (double)x[2] * x[2];
+    const double r2 = (double)x[3] * x[3];
+    k[i] = (float)(c2 - r2);
+    c2max = std::max(c2max, c2);
+    r2max = std::max(r2max, r2);
+  }
+  std::vector<float> lo(4 * (size_t)d->n_aabbs), hi(4 * (size_t)d->n_aabbs);
+  for (int i = 0; i < d->n_aabbs; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[4 * i + a] = d->aabb_lohi[6 * i + a];
+      hi[4 * i + a] = d->aabb_lohi[6 * i + 3 + a];
+    }
   int rc;
   if ((rc = upload(&h.d_spheres, d->spheres_xyzr, sizeof(float) * 4 * d->n_spheres))) return rc;
-  if ((rc = upload(&h.d_aabbs, d->aabb_lohi, sizeof(float) * 6 * d->n_aabbs))) { h.free_all(); return rc; }
+  if ((rc = upload(&h.d_k, k.data(), sizeof(float) * k.size()))) { h.free_all(); return rc; }
+  if ((rc = upload(&h.d_lo, lo.data(), sizeof(float) * lo.size()))) { h.free_all(); return rc; }
+  if ((rc = upload(&h.d_hi, hi.data(), sizeof(float) * hi.size()))) { h.free_all(); return rc; }
   h.dev.n_spheres = d->n_spheres;
   h.dev.n_aabbs = d->n_aabbs;
   h.dev.live = 1;
+  h.dev.c2max = (float)(c2max * (1.0 + 1e-6));
+  h.dev.r2max = (float)(r2max * (1.0 + 1e-6));
   h.dev.spheres = (const float4 *)h.d_spheres;
-  h.dev.aabbs = (const float *)h.d_aabbs;
+  h.dev.sphere_k = (const float *)h.d_k;
+  h.dev.box_lo = (const float4 *)h.d_lo;
+  h.dev.box_hi = (const float4 *)h.d_hi;
   h.refs = 1;
   c->envs.push_back(h);
   if ((rc = c->push_tables())) {
@@ -642,9 +699,11 @@ int mrv_get_stats(mrv_ctx *c, mrv_stats *out) {
 
 int mrv_set_tuning(mrv_ctx *c, const mrv_tuning *t) {
   if (!c || !t) return fail(MRV_ERR_ARG, "NULL argument");
-  if (t->chunk_tiles < 1 || t->chunk_tiles > 4096) return fail(MRV_ERR_ARG, "chunk_tiles outside 1..4096");
+  if (t->slices_per_item < 1 || t->slices_per_item > 4096) return fail(MRV_ERR_ARG, "slices_per_item outside 1..4096");
   if (t->warps_per_block < 1 || t->warps_per_block > 12) return fail(MRV_ERR_ARG, "warps_per_block outside 1..12");
   if (t->blocks_per_sm < 0) return fail(MRV_ERR_ARG, "blocks_per_sm < 0");
+  if (t->tile_split != 1 && t->tile_split != 2 && t->tile_split != 4 && t->tile_split != 8)
+    return fail(MRV_ERR_ARG, "tile_split must be 1, 2, 4 or 8");
   c->tuning = *t;
   return MRV_OK;
 }
@@ -728,7 +787,7 @@ int mrv_graph_create(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_con
     delete g;
     return rc;
   }
-  BatchDev B = make_batchdev(c, b, g->scratch, -1, c->tuning.chunk_tiles);
+  BatchDev B = make_batchdev(c, b, g->scratch, -1, c->tuning.slices_per_item);
   // attributes are set outside the capture
   set_main_attrs(c->tuning.warps_per_block);
   grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm);

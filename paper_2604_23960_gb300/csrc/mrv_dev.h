@@ -16,9 +16,9 @@ namespace mrv {
 
 constexpr int kWarp = 32;             // lanes per tile (the GPU's batch width W)
 constexpr int kMaxLinks = MRV_MAX_DOF + 2;  // frames 0..dof+1
-constexpr int kMaxLevels = 64;        // work levels (chunks per query)
+constexpr int kMaxLevels = 256;       // work levels (work items per query)
 constexpr int kEnvIdBase = 1 << 20;   // env ids = kEnvIdBase + env slot
-constexpr int kFkChains = 16;         // (state, robot) chains per FK round
+constexpr int kFkChains = 8;          // (state, robot) chains per FK round
 
 // device error bits (BatchDev::err)
 enum : uint32_t {
@@ -37,19 +37,30 @@ struct ModelDev {
   int32_t kind, dof, n_spheres, n_self;
   int32_t live;
   float point_z;
+  float r2max;                   // largest squared sphere radius
   float base[12];
   float flange[12];
   float dh[MRV_MAX_DOF][5];      // cos(alpha), sin(alpha), a, d, theta_offset
   const float4 *spheres;         // local xyz, radius
   const int32_t *sphere_link;
-  const int2 *self_pairs;
+  const uint32_t *self_pairs;    // x | y << 16 with x < y, sorted, padded by
+                                 // repeating the last pair to a multiple of 4
+  const int4 *self_rects;        // the same pairs as rectangles (x0, x1, y0, y1):
+                                 // rows x0..x1-1 against columns y0..y1-1
+  int32_t n_rects;               // 0: use the sparse list
+  int32_t pad2;
 };
 
 struct EnvDev {
   int32_t n_spheres, n_aabbs;
-  int32_t live, pad;
+  int32_t live;
+  float c2max;                   // largest |center|^2 of the obstacle spheres
+  float r2max;                   // largest squared obstacle radius
+  int32_t pad[3];
   const float4 *spheres;         // world xyz, radius
-  const float *aabbs;            // n x 6
+  const float *sphere_k;         // |center|^2 - radius^2 per obstacle sphere
+  const float4 *box_lo;          // n_aabbs: lo xyz (w unused)
+  const float4 *box_hi;          // n_aabbs: hi xyz (w unused)
 };
 
 // per-query derived record (written by the preparation kernel)
@@ -58,12 +69,19 @@ struct QueryDev {
   int32_t n;          // robots
   int32_t M;          // spheres summed over robots
   int32_t ntiles;     // 32-state tiles
+  int32_t split;      // slices per tile
+  int32_t spt;        // states per slice (32 / split)
+  int32_t nslices;    // slices per phase (ntiles * split)
+  int32_t nphase;     // 2 for hierarchical MV (env pass, then pair pass), else 1
   int32_t nchunks;    // work items of this query
-  int32_t cte;        // tiles per work item
+  int32_t cte;        // slices per work item
   int32_t env;        // env slot or -1
   uint32_t bits;      // bit 0: FFC, bit 1: flavor A (lane = state), bit 2: invalid
+  float rho2;         // largest squared sphere radius of the query's robots
+  int32_t pad;
   long long pairtests;  // robot-robot sphere tests per state
-  long long envtests;   // robot-obstacle + self tests per state (MV with env)
+  long long envtests;   // robot-obstacle sphere + self tests per state (MV with env)
+  long long boxtests;   // robot-box tests per state (MV with env)
 };
 
 struct BatchDev {
@@ -80,7 +98,8 @@ struct BatchDev {
   const int32_t *q_env_id;           // may be null
   const uint8_t *q_kind;             // may be null (all MV unless forced)
   int32_t forced_kind;               // -1 = q_kind, else MRV_KIND_*
-  int32_t chunk_tiles;
+  int32_t slices_per_item;
+  int32_t tile_split;
   // derived (device scratch)
   int32_t *slot_tau;                 // n_waypoints: time of each waypoint
   QueryDev *q;                       // n_queries
@@ -93,9 +112,9 @@ struct BatchDev {
   int32_t *cursor;                   // kMaxLevels + 1
   int32_t *counters;                 // [0] work counter, [1] n_items, [2] abort flag
   uint32_t *err;
-  unsigned long long *stats;         // [0] states checked, [1] sphere tests,
+  unsigned long long *stats;         // [0] states checked, [1] tests executed,
                                      // [2] states available, [3] tests available,
-                                     // [4] items
+                                     // [4] items, [5] box tests executed
   // tables
   const ModelDev *models;
   int32_t n_models;

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "mrv_dev.h"
+#include "mrv_geometry.h"
 
 namespace mrv {
 
@@ -43,25 +44,30 @@ struct Scratch {
 
 struct HostModel {
   ModelDev dev{};
-  void *d_spheres = nullptr, *d_links = nullptr, *d_self = nullptr;
+  void *d_spheres = nullptr, *d_links = nullptr, *d_self = nullptr, *d_rects = nullptr;
   int refs = 0;
   int max_spheres = 0;
   void free_all() {
     if (d_spheres) cudaFree(d_spheres);
     if (d_links) cudaFree(d_links);
     if (d_self) cudaFree(d_self);
-    d_spheres = d_links = d_self = nullptr;
+    if (d_rects) cudaFree(d_rects);
+    d_spheres = d_links = d_self = d_rects = nullptr;
   }
 };
 
+
+
 struct HostEnv {
   EnvDev dev{};
-  void *d_spheres = nullptr, *d_aabbs = nullptr;
+  void *d_spheres = nullptr, *d_k = nullptr, *d_lo = nullptr, *d_hi = nullptr;
   int refs = 0;
   void free_all() {
     if (d_spheres) cudaFree(d_spheres);
-    if (d_aabbs) cudaFree(d_aabbs);
-    d_spheres = d_aabbs = nullptr;
+    if (d_k) cudaFree(d_k);
+    if (d_lo) cudaFree(d_lo);
+    if (d_hi) cudaFree(d_hi);
+    d_spheres = d_k = d_lo = d_hi = nullptr;
   }
 };
 
@@ -89,7 +95,7 @@ struct mrv_ctx {
   mrv::EnvDev *d_envs = nullptr;
   size_t cap_models = 0, cap_envs = 0;
   mrv::Scratch scratch;
-  mrv_tuning tuning{4, 4, 0, 0};
+  mrv_tuning tuning{1, 4, 0, 4};
   mrv_stats stats{};
   long long clock_budget = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -112,7 +118,7 @@ struct mrv_graph {
 
 namespace mrv {
 int validate_batch(mrv_ctx *ctx, const mrv_batch *b);
-BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int chunk_tiles);
+BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int slices_per_item);
 int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
                 mrv_conflict *conf, bool timed);
 int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,

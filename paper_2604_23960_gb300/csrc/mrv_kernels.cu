@@ -6,21 +6,36 @@
 //          (PackCfgBatch, Sec. III-A): MV packs them with the rake order
 //          t = b + nb*l (nb = ceil((T+1)/32)), FFC with the linear order
 //          t = 32b + l.
-//   chunk  consecutive tiles of one query, processed in order by one warp,
-//          stopping as soon as the query is decided (MV: any collision;
-//          FFC: a conflict in an earlier state).
-//   item   one chunk; items are handed out by a global atomic counter in
-//          level order: every query's first chunk, then every query's second
-//          chunk, ... (queries sorted by chunk count), so coarse rake tiles
-//          and early FFC timesteps of all queries run first.
+//   slice  a tile cut into `split` parts: MV slice p takes the rake lanes
+//          l = p, p+split, ... (still spread over the whole motion), FFC
+//          slice p takes consecutive states.  Point-robot queries keep whole
+//          tiles (split 1, one lane per state).
+//   item   `cte` consecutive slices of one query, walked in order by one warp
+//          that stops once the query is decided (MV: any collision; FFC: a
+//          conflict at an earlier state).  Items are handed out by a global
+//          atomic counter in level order: every query's first item, then
+//          every query's second item, ... (queries sorted by item count), so
+//          coarse rake slices and early FFC states of all queries run first.
+//   phase  hierarchical MV (Alg. 1, hierarchical branch) runs every slice
+//          twice: first the robot-obstacle + self checks, then the pairs.
 // Two per-query flavors:
 //   A  (point robots, <= 16 spheres): lane l owns state t(l) of the tile and
 //      runs every check of that state; a ballot finds the first conflicting
 //      lane.
-//   B  (kinematic chains): the warp walks the tile's states; per FK round
-//      16 lanes run the (state, robot) chains into shared-memory link frames,
-//      then per state the lanes place the spheres and split the sphere-pair
-//      rows; __any_sync / __reduce_or_sync reduce the verdict.
+//   B  (kinematic chains): the warp walks a slice's states; per FK round up
+//      to 8 lanes run the (state, robot) chains into shared-memory link
+//      frames, then per state the lanes place the spheres and split the
+//      sphere rows two at a time; __any_sync / __reduce_or_sync reduce.
+//
+// Sphere-pair test of flavor B.  With centers p relative to an origin near
+// the query and k = |p|^2 - r^2, two spheres overlap iff
+//     u = k_b - 2 p_a.p_b - 2 r_a r_b  <  -k_a
+// (the expanded |p_a - p_b|^2 < (r_a + r_b)^2): four FMAs per test and one
+// running minimum per row.  The rounding error of u and k is below
+// 24 u (C^2 + rho^2) (C: largest |p|, rho: largest radius, u = 2^-24);
+// a row whose minimum falls within twice that band of -k_a is decided again
+// by the direct formula, so decisions are those of the direct FP32 formula
+// wherever the two could differ.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
@@ -30,27 +45,49 @@
 namespace mrv {
 
 constexpr int kFlavorAMaxSpheres = 16;
-constexpr int kSlotWords = 16;  // ints per RobotSlot in shared memory
+constexpr int kSlotWords = 18;                   // ints per RobotSlot in shared memory
+constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
 
 struct RobotSlot {           // per-warp staged view of one robot of the query
   const float4 *spheres;
   const int32_t *links;
-  const int2 *self;
-  int32_t mdl, m, dof, kind, n_self, w0, w1, pad;
+  const uint32_t *self;      // packed pairs x | y << 16, padded to a multiple of 4
+  const int4 *rects;         // self pairs as rectangles (rows x0..x1, columns y0..y1)
+  int32_t mdl, m, dof, kind, n_self, w0, w1, n_rects;
 };
 static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
+struct TileCtx {
+  int q, T, n, M, nb, ffc, check_env, exhaustive;
+  int split, spt, nslices;
+  int env_ns, env_nb;
+  const float4 *env_s;
+  const float *env_k;
+  const float4 *box_lo, *box_hi;
+  float env_c2, env_r2, rho2;
+  long long pairtests, envtests, boxtests;
+  unsigned long long tests, btests, states;
+};
+
+constexpr int kEnvCache = 64;    // obstacle spheres staged per warp (more: read from L1)
+constexpr int kBoxCache = 32;    // obstacle boxes staged per warp
+
 struct WarpSmem {
+  TileCtx ctx;               // the current work item's query parameters
   RobotSlot rs[MRV_MAX_ROBOTS];
   int32_t off[MRV_MAX_ROBOTS + 1];
-  int32_t pad[7];
-  // union region: flavor B frames + positions, or flavor A per-lane spheres
+  float ox, oy, oz;          // origin of the relative frame (world)
+  int32_t pad[4];
+  float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
+  float EK[kEnvCache];       // their |c|^2 - r^2
+  float4 BL[kBoxCache], BH[kBoxCache];   // obstacle boxes
   union {
     struct {
-      float xf[kFkChains * kMaxLinks * 12];
-      float4 P[MRV_MAX_QUERY_SPHERES];
+      float xf[kFkChains * kMaxLinks * 12];   // link frames of one FK round
+      float4 P[MRV_MAX_QUERY_SPHERES];         // centers relative to o, radius
+      float K[MRV_MAX_QUERY_SPHERES];          // |p|^2 - r^2
     } b;
-    float4 PA[kFlavorAMaxSpheres * kWarp];
+    float4 PA[kFlavorAMaxSpheres * kWarp];     // flavor A: world centers per lane
   } u;
 };
 
@@ -64,6 +101,12 @@ __device__ __forceinline__ int f2ord(float f) {
   return i >= 0 ? i : i ^ 0x7fffffff;
 }
 __device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // ---------------------------------------------------------------------------
 // preparation: per-query validation, waypoint times, step count T, work shape
@@ -87,8 +130,9 @@ __global__ void k_prep(BatchDev B) {
   if (q >= B.n_queries) return;
   uint32_t err = 0;
   QueryDev Q;
-  Q.T = 0; Q.n = 0; Q.M = 0; Q.ntiles = 0; Q.nchunks = 0; Q.cte = 1; Q.env = -1; Q.bits = 0;
-  Q.pairtests = 0; Q.envtests = 0;
+  Q.T = 0; Q.n = 0; Q.M = 0; Q.ntiles = 0; Q.split = 1; Q.spt = kWarp; Q.nslices = 0; Q.nphase = 1;
+  Q.nchunks = 0; Q.cte = 1; Q.env = -1; Q.bits = 0; Q.rho2 = 0.f; Q.pad = 0;
+  Q.pairtests = 0; Q.envtests = 0; Q.boxtests = 0;
   const int s0 = B.q_robot_off[q], s1 = B.q_robot_off[q + 1];
   const int n = s1 - s0;
   if (n < 1 || n > MRV_MAX_ROBOTS || s0 < 0 || s1 > B.n_slots) err |= kErrRobots;
@@ -106,6 +150,7 @@ __global__ void k_prep(BatchDev B) {
   bool all_point = true;
   int ms[MRV_MAX_ROBOTS];
   long long self_total = 0;
+  float rho2 = 0.f;
   if (!err) {
     for (int i = 0; i < n; ++i) {
       const int s = s0 + i;
@@ -116,6 +161,7 @@ __global__ void k_prep(BatchDev B) {
       ms[i] = m.n_spheres;
       M += m.n_spheres;
       self_total += m.n_self;
+      rho2 = fmaxf(rho2, m.r2max);
       if (m.kind != MRV_ROBOT_POINT) all_point = false;
       const int w0 = B.slot_wp_off[s], w1 = B.slot_wp_off[s + 1];
       if (w0 < 0 || w1 <= w0 || w1 > B.n_waypoints) { err |= kErrWaypoints; break; }
@@ -153,26 +199,40 @@ __global__ void k_prep(BatchDev B) {
     Q.n = n;
     Q.M = M;
     Q.env = env;
-    if (all_point && M <= kFlavorAMaxSpheres) Q.bits |= 2u;
+    Q.rho2 = rho2;
+    const bool flavor_a = all_point && M <= kFlavorAMaxSpheres;
+    if (flavor_a) Q.bits |= 2u;
+    const bool mv = !(Q.bits & 1u);
+    const bool check_env = mv && (B.flags & MRV_CHECK_ENV);
     Q.ntiles = (int)((T + 1 + kWarp - 1) / kWarp);
-    int cte = B.chunk_tiles < 1 ? 1 : B.chunk_tiles;
-    const int need = (Q.ntiles + kMaxLevels - 1) / kMaxLevels;
+    int split = flavor_a ? 1 : B.tile_split;
+    if (split != 1 && split != 2 && split != 4 && split != 8) split = 4;
+    Q.split = split;
+    Q.spt = kWarp / split;
+    Q.nslices = Q.ntiles * split;
+    Q.nphase = (check_env && (B.flags & MRV_HIERARCHICAL)) ? 2 : 1;
+    const int total = Q.nslices * Q.nphase;
+    int cte = B.slices_per_item < 1 ? 1 : B.slices_per_item;
+    const int need = (total + kMaxLevels - 1) / kMaxLevels;
     if (cte < need) cte = need;
     Q.cte = cte;
-    Q.nchunks = (Q.ntiles + cte - 1) / cte;
+    Q.nchunks = (total + cte - 1) / cte;
     long long pt = 0;
     for (int i = 0; i < n; ++i)
       for (int j = i + 1; j < n; ++j) pt += (long long)ms[i] * ms[j];
     Q.pairtests = pt;
-    long long et = 0;
-    const bool mv = !(Q.bits & 1u);
-    if (mv && (B.flags & MRV_CHECK_ENV)) {
-      if (env >= 0) et = (long long)M * (B.envs[env].n_spheres + B.envs[env].n_aabbs);
+    long long et = 0, bt = 0;
+    if (check_env) {
+      if (env >= 0) {
+        et = (long long)M * B.envs[env].n_spheres;
+        bt = (long long)M * B.envs[env].n_aabbs;
+      }
       et += self_total;
     }
     Q.envtests = et;
+    Q.boxtests = bt;
     atomicAdd(&B.stats[2], (unsigned long long)(T + 1));
-    atomicAdd(&B.stats[3], (unsigned long long)((T + 1) * (pt + et)));
+    atomicAdd(&B.stats[3], (unsigned long long)((T + 1) * (pt + et + bt)));
   }
   B.q[q] = Q;
   B.q_hit[q] = 0;
@@ -181,19 +241,19 @@ __global__ void k_prep(BatchDev B) {
   atomicAdd(&B.hist[Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks], 1);
 }
 
-// level layout: queries sorted by chunk count (descending); level c holds the
-// queries with more than c chunks, which are the first cnt_c sorted queries.
+// level layout: queries sorted by item count (descending); level c holds the
+// queries with more than c items, which are the first cnt_c sorted queries.
 __global__ void k_levels(BatchDev B) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int start = 0;
   for (int k = kMaxLevels; k >= 0; --k) {
-    B.cursor[k] = start;           // first sorted position of chunk count k
+    B.cursor[k] = start;           // first sorted position of item count k
     start += B.hist[k];
   }
   int acc = 0;
   B.level_start[0] = 0;
   for (int c = 0; c < kMaxLevels; ++c) {
-    acc += B.cursor[c];            // queries with more than c chunks
+    acc += B.cursor[c];            // queries with more than c items
     B.level_start[c + 1] = acc;
   }
   B.counters[1] = acc;             // number of work items
@@ -248,7 +308,7 @@ __device__ __forceinline__ void store_frame(float *X, int link, const float *R, 
 // SpheresFK link frames (Sec. III-A): base, then one modified-DH joint at a
 // time, R' = R RotX(alpha) RotZ(theta), p' = p + a R e_x + d R' e_z, then the
 // flange.  Frames are written to X[link*12] (3x4 row-major).
-__device__ void chain_frames(const ModelDev &m, const float *q, float *X) {
+__device__ __noinline__ void chain_frames(const ModelDev &m, const float *q, float *X) {
   float R[9], p[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -296,6 +356,7 @@ __device__ void chain_frames(const ModelDev &m, const float *q, float *X) {
   store_frame(X, m.dof + 1, R2, p2);
 }
 
+// direct forms: |a - b|^2 < (ra + rb)^2, clearance |a - b| - ra - rb
 __device__ __forceinline__ bool sph_hit(const float4 a, const float4 b) {
   const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   const float rr = a.w + b.w;
@@ -307,34 +368,41 @@ __device__ __forceinline__ float sph_clr(const float4 a, const float4 b) {
   return sqrtf(dx * dx + dy * dy + dz * dz) - (a.w + b.w);
 }
 
-__device__ __forceinline__ float box_d2(const float4 a, const float *bx) {
-  const float ex = fmaxf(fmaxf(bx[0] - a.x, a.x - bx[3]), 0.f);
-  const float ey = fmaxf(fmaxf(bx[1] - a.y, a.y - bx[4]), 0.f);
-  const float ez = fmaxf(fmaxf(bx[2] - a.z, a.z - bx[5]), 0.f);
-  return ex * ex + ey * ey + ez * ez;
+// squared distance from a point to a box (0 inside)
+__device__ __forceinline__ float box_d2(float x, float y, float z, const float4 lo, const float4 hi) {
+  const float ex = x - fminf(fmaxf(x, lo.x), hi.x);
+  const float ey = y - fminf(fmaxf(y, lo.y), hi.y);
+  const float ez = z - fminf(fmaxf(z, lo.z), hi.z);
+  return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+}
+
+// expanded test value u = k_b + A . (b, r_b), A = -2 (p_a, r_a)
+__device__ __forceinline__ float uval(const float4 A, const float4 b, float kb) {
+  return fmaf(A.x, b.x, fmaf(A.y, b.y, fmaf(A.z, b.z, fmaf(A.w, b.w, kb))));
 }
 
 // ---------------------------------------------------------------------------
-// tile processing
+// work contexts
 // ---------------------------------------------------------------------------
 
-struct TileCtx {
-  int q, T, n, M, nb, ffc, check_env, exhaustive;
-  int env_ns, env_nb;
-  const float4 *env_s;
-  const float *env_b;
-  long long pairtests, envtests;
-  unsigned long long tests, states;
-};
 
-__device__ __forceinline__ int tile_state(const TileCtx &C, int b, int l) {
-  return C.ffc ? b * kWarp + l : b + C.nb * l;
+
+// state of position j of slice k (monotone in j for both packings)
+__device__ __forceinline__ int slice_state(const TileCtx &C, int k, int j) {
+  if (C.ffc) return k * C.spt + j;
+  const int b = k / C.split, p = k - b * C.split;
+  return b + C.nb * (p + C.split * j);
 }
 
-// result of a tile: MV -> 1 if a collision was found; FFC -> key or INT_MAX
+// ---------------------------------------------------------------------------
+// flavor A: one lane per state (point robots)
+// ---------------------------------------------------------------------------
+
+// MV -> 1 if a collision was found; FFC -> smallest key t*32 + pair or INT_MAX
 template <bool CLR>
-__device__ int tile_flavor_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, int lane, float &minclr) {
-  const int t = tile_state(C, b, lane);
+__device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int lane, float &minclr, bool do_env,
+                       bool do_pairs) {
+  const int t = slice_state(C, k, lane);
   const bool valid = t <= C.T;
   float4 *PA = S.u.PA;
   if (valid) {
@@ -344,16 +412,16 @@ __device__ int tile_flavor_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, 
       float q[MRV_MAX_DOF];
       interp(B, rs.w0, rs.w1, rs.dof, t, q);
       const float z = rs.dof == 2 ? m.point_z : q[2];
-      for (int k = 0; k < rs.m; ++k) {
-        const float4 s = rs.spheres[k];
+      for (int kk = 0; kk < rs.m; ++kk) {
+        const float4 s = rs.spheres[kk];
         float lx = s.x, ly = s.y, lz = s.z;
-        if (rs.links[k] == 1) { lx += q[0]; ly += q[1]; lz += z; }
+        if (rs.links[kk] == 1) { lx += q[0]; ly += q[1]; lz += z; }
         float4 w;
         w.x = m.base[0] * lx + m.base[1] * ly + m.base[2] * lz + m.base[3];
         w.y = m.base[4] * lx + m.base[5] * ly + m.base[6] * lz + m.base[7];
         w.z = m.base[8] * lx + m.base[9] * ly + m.base[10] * lz + m.base[11];
         w.w = s.w;
-        PA[(S.off[r] + k) * kWarp + lane] = w;
+        PA[(S.off[r] + kk) * kWarp + lane] = w;
       }
     }
   }
@@ -361,7 +429,7 @@ __device__ int tile_flavor_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, 
   C.states += nvalid;
   if (!C.ffc) {
     bool hit = false;
-    if (valid && C.check_env) {
+    if (valid && do_env && C.check_env) {
       for (int a = 0; a < C.M; ++a) {
         const float4 pa = PA[a * kWarp + lane];
         for (int o = 0; o < C.env_ns; ++o) {
@@ -369,20 +437,21 @@ __device__ int tile_flavor_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, 
           else hit |= sph_hit(pa, C.env_s[o]);
         }
         for (int o = 0; o < C.env_nb; ++o) {
-          const float d2 = box_d2(pa, C.env_b + 6 * o);
+          const float d2 = box_d2(pa.x, pa.y, pa.z, C.box_lo[o], C.box_hi[o]);
           if (CLR) minclr = fminf(minclr, sqrtf(d2) - pa.w);
           else hit |= d2 < pa.w * pa.w;
         }
       }
       for (int r = 0; r < C.n; ++r)
         for (int p = 0; p < S.rs[r].n_self; ++p) {
-          const int2 sp = S.rs[r].self[p];
-          const float4 x = PA[(S.off[r] + sp.x) * kWarp + lane], y = PA[(S.off[r] + sp.y) * kWarp + lane];
+          const uint32_t sp = S.rs[r].self[p];
+          const float4 x = PA[(S.off[r] + (int)(sp & 0xffffu)) * kWarp + lane];
+          const float4 y = PA[(S.off[r] + (int)(sp >> 16)) * kWarp + lane];
           if (CLR) minclr = fminf(minclr, sph_clr(x, y));
           else hit |= sph_hit(x, y);
         }
     }
-    if (valid)
+    if (valid && do_pairs)
       for (int i = 0; i < C.n; ++i)
         for (int a = S.off[i]; a < S.off[i + 1]; ++a) {
           const float4 pa = PA[a * kWarp + lane];
@@ -392,7 +461,11 @@ __device__ int tile_flavor_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, 
             else hit |= sph_hit(pa, pb);
           }
         }
-    C.tests += (unsigned long long)nvalid * (unsigned long long)(C.pairtests + (C.check_env ? C.envtests : 0));
+    if (do_env && C.check_env) {
+      C.tests += (unsigned long long)nvalid * (unsigned long long)(C.envtests + C.boxtests);
+      C.btests += (unsigned long long)nvalid * (unsigned long long)C.boxtests;
+    }
+    if (do_pairs) C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
     if (CLR) hit = minclr < 0.f;
     return __any_sync(0xffffffffu, hit) ? 1 : 0;
   }
@@ -411,108 +484,286 @@ __device__ int tile_flavor_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, 
   if (!m) return 0x7fffffff;
   const int l0 = __ffs(m) - 1;
   const int p0 = __shfl_sync(0xffffffffu, first, l0);
-  return tile_state(C, b, l0) * 32 + p0;
+  return slice_state(C, k, l0) * 32 + p0;
+}
+
+// ---------------------------------------------------------------------------
+// flavor B: the warp walks the states of a slice (kinematic chains)
+// ---------------------------------------------------------------------------
+
+// decision of a row from its minimum u against threshold -k_a
+__device__ __forceinline__ int decide(float m, float ka, float eps) {
+  const float tau = -ka;
+  return m < tau - eps ? 1 : (m < tau + eps ? 2 : 0);   // 1 hit, 2 uncertain, 0 clear
+}
+
+// Rectangle test: rows [ra, rb) of (P, shifted by sh into the column frame)
+// against columns [ca, cb) of (Q, QK).  Each lane holds 4 rows (row-lane rho,
+// rows base + rho + RL*r) and scans one of G = 32/RL column chunks; the row
+// minima are combined over the chunks by shuffles and decided once.  Returns
+// the lane's "some row collides" (callers reduce over the warp).  Rows whose
+// minimum is within the rounding band are decided by the direct formula.
+__device__ __noinline__ bool rect_test(const float4 *P, int ra, int rb, const float4 *Q, const float *QK, int ca,
+                                       int cb, float shx, float shy, float shz, float eps, int lane) {
+  const int nrows = rb - ra;
+  if (nrows <= 0 || cb <= ca) return false;
+  int RL = 1;
+  while (RL * 4 < nrows && RL < kWarp) RL <<= 1;
+  const int G = kWarp / RL;
+  const int rho = lane & (RL - 1), gam = lane / RL;
+  const int chunk = (cb - ca + G - 1) / G;
+  const int c0 = ca + gam * chunk, c1 = min(c0 + chunk, cb);
+  bool hit = false;
+  for (int base = ra; base < rb; base += RL * 4) {
+    float4 A[4];
+    float ka[4], m[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int a = min(base + rho + RL * r, rb - 1);
+      const float4 p = P[a];
+      const float x = p.x + shx, y = p.y + shy, z = p.z + shz;
+      A[r] = make_float4(-2.f * x, -2.f * y, -2.f * z, -2.f * p.w);
+      ka[r] = fmaf(x, x, fmaf(y, y, fmaf(z, z, -p.w * p.w)));
+      m[r] = INFINITY;
+    }
+#pragma unroll 2
+    for (int c = c0; c < c1; ++c) {
+      const float4 q = Q[c];
+      const float qk = QK[c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) m[r] = fminf(m[r], uval(A[r], q, qk));
+    }
+    for (int o = RL; o < kWarp; o <<= 1)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) m[r] = fminf(m[r], __shfl_xor_sync(0xffffffffu, m[r], o));
+    if (gam == 0) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int a = base + rho + RL * r;
+        if (a >= rb) continue;
+        int d = decide(m[r], ka[r], eps);
+        if (d == 2) {   // near-tangent: the direct formula decides
+          const float4 p = P[a];
+          const float4 w = make_float4(p.x + shx, p.y + shy, p.z + shz, p.w);
+          d = 0;
+          for (int c = ca; c < cb; ++c) d |= sph_hit(w, Q[c]);
+        }
+        hit |= d != 0;
+      }
+    }
+  }
+  return hit;
+}
+
+// rows [ra, rb) (world = P + o) against the obstacle boxes; each lane takes
+// 4 rows per round and scans every box
+__device__ bool box_rows(const float4 *P, int ra, int rb, const float4 *BL, const float4 *BH, int nb, float ox,
+                         float oy, float oz, int lane) {
+  bool hit = false;
+  for (int base = ra; base < rb; base += 4 * kWarp) {
+    float4 w[4];
+    float rr[4];
+    bool h[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int a = min(base + lane + kWarp * r, rb - 1);
+      const float4 p = P[a];
+      w[r] = make_float4(p.x + ox, p.y + oy, p.z + oz, p.w);
+      rr[r] = p.w * p.w;
+      h[r] = false;
+    }
+#pragma unroll 2
+    for (int o = 0; o < nb; ++o) {
+      const float4 lo = BL[o], hi = BH[o];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) h[r] |= box_d2(w[r].x, w[r].y, w[r].z, lo, hi) < rr[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) hit |= h[r] && (base + lane + kWarp * r < rb);
+  }
+  return hit;
+}
+
+// MV robot-robot checks at one state: robot i's rows against every sphere of
+// the robots after it
+__device__ bool pairs_mv(const float4 *P, const float *K, const int *off, int n, int M, int lane, float eps) {
+  bool hit = false;
+  for (int i = 0; i + 1 < n; ++i)
+    hit |= rect_test(P, off[i], off[i + 1], P, K, off[i + 1], M, 0.f, 0.f, 0.f, eps, lane);
+  return hit;
+}
+
+// FFC robot-robot checks at one state: bitmask of colliding pairs
+__device__ unsigned pairs_ffc(const float4 *P, const float *K, const int *off, int n, int lane, float eps) {
+  unsigned pm = 0;
+  for (int i = 0; i + 1 < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const bool h = rect_test(P, off[i], off[i + 1], P, K, off[j], off[j + 1], 0.f, 0.f, 0.f, eps, lane);
+      if (__any_sync(0xffffffffu, h)) pm |= 1u << pair_index(i, j, n);
+    }
+  return pm;
+}
+
+// MV robot-obstacle checks (obstacle spheres staged in shared memory up to
+// the cache size, the rest read through L1; boxes by the clamp distance) and
+// self-collision pairs (rectangles of the model, or its sparse pair list)
+__device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, const float *K, int lane, float cw2,
+                       float eps) {
+  const int M = C.M;
+  bool hit = false;
+  if (C.env_ns) {
+    const float epsw = kEpsU * (fmaxf(cw2, C.env_c2) + fmaxf(C.rho2, C.env_r2));
+    const int ns_c = min(C.env_ns, kEnvCache);
+    hit |= rect_test(P, 0, M, S.ES, S.EK, 0, ns_c, S.ox, S.oy, S.oz, epsw, lane);
+    if (C.env_ns > ns_c) hit |= rect_test(P, 0, M, C.env_s, C.env_k, ns_c, C.env_ns, S.ox, S.oy, S.oz, epsw, lane);
+  }
+  if (C.env_nb) {
+    const int nb_c = min(C.env_nb, kBoxCache);
+    hit |= box_rows(P, 0, M, S.BL, S.BH, nb_c, S.ox, S.oy, S.oz, lane);
+    if (C.env_nb > nb_c) hit |= box_rows(P, 0, M, C.box_lo + nb_c, C.box_hi + nb_c, C.env_nb - nb_c, S.ox, S.oy, S.oz, lane);
+  }
+  for (int r = 0; r < C.n; ++r) {
+    const int o = S.off[r];
+    const int nr = S.rs[r].n_rects;
+    if (nr > 0) {
+      for (int k = 0; k < nr; ++k) {
+        const int4 R = __ldg(&S.rs[r].rects[k]);
+        hit |= rect_test(P, o + R.x, o + R.y, P, K, o + R.z, o + R.w, 0.f, 0.f, 0.f, eps, lane);
+      }
+    } else {
+      // sparse pairs (sorted): consecutive lanes take consecutive pairs, so
+      // a warp's first spheres mostly coincide and its second spheres are
+      // adjacent (no bank conflicts); four pairs per lane per round
+      const int ns = S.rs[r].n_self;
+      const uint32_t *sp = S.rs[r].self;
+      const float4 *Pr = P + o;
+      for (int p0 = 0; p0 < ns; p0 += 4 * kWarp) {
+        uint32_t e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int p = p0 + lane + kWarp * u;
+          e[u] = p < ns ? __ldg(&sp[p]) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (p0 + lane + kWarp * u < ns) hit |= sph_hit(Pr[e[u] & 0xffffu], Pr[e[u] >> 16]);
+      }
+    }
+  }
+  return hit;
+}
+
+// clearance mode (exhaustive MV with min_clearance_out): direct formulas
+__device__ void clr_state(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, bool do_env, bool do_pairs,
+                          float &minclr) {
+  const int M = C.M, n = C.n;
+  if (do_env && C.check_env) {
+    for (int a = lane; a < M; a += kWarp) {
+      const float4 pa = P[a];
+      const float4 w = make_float4(pa.x + S.ox, pa.y + S.oy, pa.z + S.oz, pa.w);
+      for (int o = 0; o < C.env_ns; ++o) minclr = fminf(minclr, sph_clr(w, C.env_s[o]));
+      for (int o = 0; o < C.env_nb; ++o)
+        minclr = fminf(minclr, sqrtf(box_d2(w.x, w.y, w.z, C.box_lo[o], C.box_hi[o])) - w.w);
+    }
+    for (int r = 0; r < n; ++r)
+      for (int p = lane; p < S.rs[r].n_self; p += kWarp) {
+        const uint32_t e = S.rs[r].self[p];
+        minclr = fminf(minclr, sph_clr(P[S.off[r] + (e & 0xffffu)], P[S.off[r] + (e >> 16)]));
+      }
+  }
+  if (do_pairs)
+    for (int a = lane; a < S.off[n - 1]; a += kWarp) {
+      int r = 0;
+      while (a >= S.off[r + 1]) ++r;
+      const float4 pa = P[a];
+      for (int b = S.off[r + 1]; b < M; ++b) minclr = fminf(minclr, sph_clr(pa, P[b]));
+    }
 }
 
 template <bool CLR>
-__device__ int tile_flavor_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, int lane, float &minclr) {
+__device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int lane, float &minclr, bool do_env,
+                       bool do_pairs) {
   const int n = C.n, M = C.M;
   const int CS = (kFkChains / n) < 1 ? 1 : (kFkChains / n);   // states per FK round
   float *xf = S.u.b.xf;
   float4 *P = S.u.b.P;
-  const int rows = S.off[n - 1];
+  float *K = S.u.b.K;
+  const bool need_env = do_env && C.check_env;
   int found = C.ffc ? 0x7fffffff : 0;
-  for (int l0 = 0; l0 < kWarp; l0 += CS) {
-    if (tile_state(C, b, l0) > C.T) break;   // states grow with l in both orders
+  for (int j0 = 0; j0 < C.spt; j0 += CS) {
+    if (slice_state(C, k, j0) > C.T) break;   // states grow with j in both packings
     // (state, robot) chains
     if (lane < CS * n) {
-      const int l = l0 + lane / n, r = lane % n;
-      const int t = tile_state(C, b, l);
-      if (l < kWarp && t <= C.T) {
-        const RobotSlot &rs = S.rs[r];
-        float q[MRV_MAX_DOF];
-        interp(B, rs.w0, rs.w1, rs.dof, t, q);
-        chain_frames(B.models[rs.mdl], q, xf + lane * (kMaxLinks * 12));
+      const int j = j0 + lane / n, r = lane % n;
+      if (j < C.spt) {
+        const int t = slice_state(C, k, j);
+        if (t <= C.T) {
+          const RobotSlot &rs = S.rs[r];
+          float q[MRV_MAX_DOF];
+          interp(B, rs.w0, rs.w1, rs.dof, t, q);
+          chain_frames(B.models[rs.mdl], q, xf + lane * (kMaxLinks * 12));
+        }
       }
     }
     __syncwarp();
-    for (int l = l0; l < l0 + CS && l < kWarp; ++l) {
-      const int t = tile_state(C, b, l);
+    for (int j = j0; j < j0 + CS && j < C.spt; ++j) {
+      const int t = slice_state(C, k, j);
       if (t > C.T) break;
       C.states += 1;
-      // sphere placement
-      for (int a = lane; a < M; a += kWarp) {
-        int r = 0;
-        while (a >= S.off[r + 1]) ++r;
-        const int k = a - S.off[r];
-        const float4 s = S.rs[r].spheres[k];
-        const float *X = xf + ((l - l0) * n + r) * (kMaxLinks * 12) + S.rs[r].links[k] * 12;
-        float4 w;
-        w.x = fmaf(X[0], s.x, fmaf(X[1], s.y, fmaf(X[2], s.z, X[3])));
-        w.y = fmaf(X[4], s.x, fmaf(X[5], s.y, fmaf(X[6], s.z, X[7])));
-        w.z = fmaf(X[8], s.x, fmaf(X[9], s.y, fmaf(X[10], s.z, X[11])));
-        w.w = s.w;
-        P[a] = w;
+      // sphere placement relative to the query origin, robot by robot
+      float c2 = 0.f, cw2 = 0.f;
+      for (int r = 0; r < n; ++r) {
+        const float *Xr = xf + ((j - j0) * n + r) * (kMaxLinks * 12);
+        const float4 *sph = S.rs[r].spheres;
+        const int32_t *lnk = S.rs[r].links;
+        const int m = S.rs[r].m, a0 = S.off[r];
+#pragma unroll 2
+        for (int kk = lane; kk < m; kk += kWarp) {
+          const float4 s = __ldg(&sph[kk]);
+          const float *X = Xr + __ldg(&lnk[kk]) * 12;
+          const float wx = fmaf(X[0], s.x, fmaf(X[1], s.y, fmaf(X[2], s.z, X[3])));
+          const float wy = fmaf(X[4], s.x, fmaf(X[5], s.y, fmaf(X[6], s.z, X[7])));
+          const float wz = fmaf(X[8], s.x, fmaf(X[9], s.y, fmaf(X[10], s.z, X[11])));
+          const float px = wx - S.ox, py = wy - S.oy, pz = wz - S.oz;
+          P[a0 + kk] = make_float4(px, py, pz, s.w);
+          const float pp = fmaf(px, px, fmaf(py, py, pz * pz));
+          K[a0 + kk] = fmaf(-s.w, s.w, pp);
+          c2 = fmaxf(c2, pp);
+          cw2 = fmaxf(cw2, fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+        }
       }
+      c2 = warp_max(c2);
+      if (need_env) cw2 = warp_max(cw2);
       __syncwarp();
+      const float eps = kEpsU * (c2 + C.rho2);
       if (!C.ffc) {
         bool hit = false;
-        if (C.check_env) {
-          for (int a = lane; a < M; a += kWarp) {
-            const float4 pa = P[a];
-            for (int o = 0; o < C.env_ns; ++o) {
-              if (CLR) minclr = fminf(minclr, sph_clr(pa, C.env_s[o]));
-              else hit |= sph_hit(pa, C.env_s[o]);
-            }
-            for (int o = 0; o < C.env_nb; ++o) {
-              const float d2 = box_d2(pa, C.env_b + 6 * o);
-              if (CLR) minclr = fminf(minclr, sqrtf(d2) - pa.w);
-              else hit |= d2 < pa.w * pa.w;
-            }
-          }
-          for (int r = 0; r < n; ++r) {
-            const int ns = S.rs[r].n_self;
-            const int2 *sp = S.rs[r].self;
-            const float4 *Pr = P + S.off[r];
-            for (int p = lane; p < ns; p += kWarp) {
-              const int2 e = sp[p];
-              if (CLR) minclr = fminf(minclr, sph_clr(Pr[e.x], Pr[e.y]));
-              else hit |= sph_hit(Pr[e.x], Pr[e.y]);
-            }
-          }
-          C.tests += (unsigned long long)C.envtests;
+        if (CLR) {
+          clr_state(C, S, P, lane, do_env, do_pairs, minclr);
+          hit = minclr < 0.f;
+        } else if (need_env) {
           // combined order (Alg. 1): env + self of every robot, then pairs
-          if (!CLR && !C.exhaustive && __any_sync(0xffffffffu, hit)) return 1;
-        }
-        for (int a = lane; a < rows; a += kWarp) {
-          int r = 0;
-          while (a >= S.off[r + 1]) ++r;
-          const float4 pa = P[a];
-#pragma unroll 4
-          for (int bb = S.off[r + 1]; bb < M; ++bb) {
-            if (CLR) minclr = fminf(minclr, sph_clr(pa, P[bb]));
-            else hit |= sph_hit(pa, P[bb]);
+          hit = env_mv(C, S, P, K, lane, cw2, eps);
+          if (!C.exhaustive && __any_sync(0xffffffffu, hit)) {
+            C.tests += (unsigned long long)(C.envtests + C.boxtests);
+            C.btests += (unsigned long long)C.boxtests;
+            return 1;
           }
         }
-        C.tests += (unsigned long long)C.pairtests;
-        if (CLR) hit = minclr < 0.f;
+        if (need_env) {
+          C.tests += (unsigned long long)(C.envtests + C.boxtests);
+          C.btests += (unsigned long long)C.boxtests;
+        }
+        if (do_pairs) {
+          if (!CLR) hit |= pairs_mv(P, K, S.off, n, M, lane, eps);
+          C.tests += (unsigned long long)C.pairtests;
+        }
         if (__any_sync(0xffffffffu, hit)) {
           if (!C.exhaustive) return 1;
           found = 1;
         }
       } else {
-        unsigned pm = 0;
-        for (int a = lane; a < rows; a += kWarp) {
-          int r = 0;
-          while (a >= S.off[r + 1]) ++r;
-          const float4 pa = P[a];
-          for (int j = r + 1; j < n; ++j) {
-            bool h = false;
-#pragma unroll 4
-            for (int bb = S.off[j]; bb < S.off[j + 1]; ++bb) h |= sph_hit(pa, P[bb]);
-            if (h) pm |= 1u << pair_index(r, j, n);
-          }
-        }
+        unsigned pm = pairs_ffc(P, K, S.off, n, lane, eps);
         C.tests += (unsigned long long)C.pairtests;
         pm = __reduce_or_sync(0xffffffffu, pm);
         if (pm) {
@@ -535,28 +786,33 @@ __device__ int tile_flavor_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int b, 
 template <bool CLR>
 __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane) {
   const QueryDev Q = B.q[q];
-  TileCtx C;
+  TileCtx &C = S.ctx;   // kept in shared memory: read where used, not held in registers
+  __syncwarp();
   C.q = q; C.T = Q.T; C.n = Q.n; C.M = Q.M; C.nb = Q.ntiles;
   C.ffc = Q.bits & 1u;
   C.check_env = (!C.ffc) && (B.flags & MRV_CHECK_ENV);
   C.exhaustive = (B.flags & MRV_EXHAUSTIVE) ? 1 : 0;
-  C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_b = nullptr;
+  C.split = Q.split; C.spt = Q.spt; C.nslices = Q.nslices;
+  C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
+  C.env_c2 = 0.f; C.env_r2 = 0.f; C.rho2 = Q.rho2;
   if (C.check_env && Q.env >= 0) {
     const EnvDev &E = B.envs[Q.env];
-    C.env_ns = E.n_spheres; C.env_nb = E.n_aabbs; C.env_s = E.spheres; C.env_b = E.aabbs;
+    C.env_ns = E.n_spheres; C.env_nb = E.n_aabbs; C.env_s = E.spheres; C.env_k = E.sphere_k;
+    C.box_lo = E.box_lo; C.box_hi = E.box_hi; C.env_c2 = E.c2max; C.env_r2 = E.r2max;
   }
-  C.pairtests = Q.pairtests; C.envtests = Q.envtests;
-  C.tests = 0; C.states = 0;
-  // stage the query's robots
+  C.pairtests = Q.pairtests; C.envtests = Q.envtests; C.boxtests = Q.boxtests;
+  C.tests = 0; C.btests = 0; C.states = 0;
+  // stage the query's robots; origin of the relative frame = robot 0's base
   const int s0 = B.q_robot_off[q];
   if (lane < C.n) {
     const int id = B.slot_robot_id[s0 + lane];
     const ModelDev &m = B.models[id];
     RobotSlot rs;
-    rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs;
+    rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects;
     rs.mdl = id; rs.m = m.n_spheres; rs.dof = m.dof; rs.kind = m.kind; rs.n_self = m.n_self;
-    rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.pad = 0;
+    rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.n_rects = m.n_rects;
     S.rs[lane] = rs;
+    if (lane == 0) { S.ox = m.base[3]; S.oy = m.base[7]; S.oz = m.base[11]; }
   }
   __syncwarp();
   if (lane == 0) {
@@ -564,20 +820,35 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     S.off[0] = 0;
     for (int r = 0; r < C.n; ++r) { acc += S.rs[r].m; S.off[r + 1] = acc; }
   }
+  if (C.check_env && !(Q.bits & 2u)) {
+    for (int o = lane; o < min(C.env_ns, kEnvCache); o += kWarp) {
+      S.ES[o] = C.env_s[o];
+      S.EK[o] = C.env_k[o];
+    }
+    for (int o = lane; o < min(C.env_nb, kBoxCache); o += kWarp) {
+      S.BL[o] = C.box_lo[o];
+      S.BH[o] = C.box_hi[o];
+    }
+  }
   __syncwarp();
-  const int b0 = c * Q.cte;
-  const int b1 = min(b0 + Q.cte, Q.ntiles);
+  const int total = Q.nslices * Q.nphase;
+  const int k0 = c * Q.cte;
+  const int k1 = min(k0 + Q.cte, total);
   float minclr = INFINITY;
-  for (int b = b0; b < b1; ++b) {
+  for (int kt = k0; kt < k1; ++kt) {
+    const int phase = Q.nphase == 2 ? kt / Q.nslices : -1;
+    const int k = Q.nphase == 2 ? kt - phase * Q.nslices : kt;
+    const bool do_env = phase != 1, do_pairs = phase != 0;
     if (!C.exhaustive) {
       // one lane reads the query's shared verdict so the warp decides together
       int stop = 0;
       if (lane == 0)
-        stop = !C.ffc ? *(volatile int *)&B.q_hit[q] != 0 : *(volatile int *)&B.q_best[q] < b * kWarp * 32;
+        stop = !C.ffc ? *(volatile int *)&B.q_hit[q] != 0
+                      : *(volatile int *)&B.q_best[q] < slice_state(C, k, 0) * 32;
       if (__shfl_sync(0xffffffffu, stop, 0)) break;
     }
-    int res = (Q.bits & 2u) ? tile_flavor_a<CLR>(B, C, S, b, lane, minclr)
-                            : tile_flavor_b<CLR>(B, C, S, b, lane, minclr);
+    const int res = (Q.bits & 2u) ? slice_a<CLR>(B, C, S, k, lane, minclr, do_env, do_pairs)
+                                  : slice_b<CLR>(B, C, S, k, lane, minclr, do_env, do_pairs);
     if (!C.ffc) {
       if (res) {
         if (lane == 0) atomicExch(&B.q_hit[q], 1);
@@ -596,22 +867,26 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
   if (lane == 0) {
     atomicAdd(&B.stats[0], C.states);
     atomicAdd(&B.stats[1], C.tests);
+    atomicAdd(&B.stats[5], C.btests);
   }
   __syncwarp();
 }
 
+// up to 12 warps per block; the register cap (168) lets 12 warps share an SM,
+// which is also what the shared memory of 3 blocks of 4 warps allows
 template <bool CLR>
-__global__ void k_main(BatchDev B, int q_lo, int q_hi) {
+__global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
   extern __shared__ float4 smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   WarpSmem &S = *reinterpret_cast<WarpSmem *>(reinterpret_cast<char *>(smem_raw) + warp * warp_smem_bytes());
   const long long t_start = clock64();
-  if (q_lo >= 0) {
-    // single-query mode (one launch per query): block x = chunk x of q_lo
-    const QueryDev Q = B.q[q_lo];
+  if (q_single >= 0) {
+    // one launch per query: warp w of block x takes items x*warps + w, ...
+    const QueryDev Q = B.q[q_single];
+    if (Q.bits & 4u) return;
     for (int c = blockIdx.x * (blockDim.x >> 5) + warp; c < Q.nchunks; c += gridDim.x * (blockDim.x >> 5))
-      if (!(Q.bits & 4u)) run_chunk<CLR>(B, S, q_lo, c, lane);
+      run_chunk<CLR>(B, S, q_single, c, lane);
     return;
   }
   const int n_items = B.counters[1];
@@ -688,9 +963,9 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
     const int id = B.slot_robot_id[s0 + threadIdx.x];
     const ModelDev &m = B.models[id];
     RobotSlot r;
-    r.spheres = m.spheres; r.links = m.sphere_link; r.self = m.self_pairs;
+    r.spheres = m.spheres; r.links = m.sphere_link; r.self = m.self_pairs; r.rects = m.self_rects;
     r.mdl = id; r.m = m.n_spheres; r.dof = m.dof; r.kind = m.kind; r.n_self = m.n_self;
-    r.w0 = B.slot_wp_off[s0 + threadIdx.x]; r.w1 = B.slot_wp_off[s0 + threadIdx.x + 1]; r.pad = 0;
+    r.w0 = B.slot_wp_off[s0 + threadIdx.x]; r.w1 = B.slot_wp_off[s0 + threadIdx.x + 1]; r.n_rects = m.n_rects;
     rs[threadIdx.x] = r;
   }
   __syncthreads();
@@ -728,13 +1003,14 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
     if (check_env) {
       if (E) {
         for (int o = 0; o < E->n_spheres; ++o) m = fminf(m, sph_clr(pa, E->spheres[o]));
-        for (int o = 0; o < E->n_aabbs; ++o) m = fminf(m, sqrtf(box_d2(pa, E->aabbs + 6 * o)) - pa.w);
+        for (int o = 0; o < E->n_aabbs; ++o)
+          m = fminf(m, sqrtf(box_d2(pa.x, pa.y, pa.z, E->box_lo[o], E->box_hi[o])) - pa.w);
       }
       const int li = a - off[r];
       for (int p = 0; p < rs[r].n_self; ++p) {
-        const int2 e = rs[r].self[p];
-        if (e.x == li) m = fminf(m, sph_clr(pa, P[off[r] + e.y]));
-        else if (e.y == li) m = fminf(m, sph_clr(pa, P[off[r] + e.x]));
+        const int ex = (int)(rs[r].self[p] & 0xffffu), ey = (int)(rs[r].self[p] >> 16);
+        if (ex == li) m = fminf(m, sph_clr(pa, P[off[r] + ey]));
+        else if (ey == li) m = fminf(m, sph_clr(pa, P[off[r] + ex]));
       }
     }
     out[(size_t)k * Q.M + a] = m;
@@ -776,8 +1052,8 @@ cudaError_t max_blocks_per_sm(int warps, bool clr, int *out) {
 
 cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int q_single, cudaStream_t st) {
   const size_t smem = main_smem_bytes(warps);
-  if (clr) k_main<true><<<grid, warps * 32, smem, st>>>(B, q_single, q_single);
-  else k_main<false><<<grid, warps * 32, smem, st>>>(B, q_single, q_single);
+  if (clr) k_main<true><<<grid, warps * 32, smem, st>>>(B, q_single);
+  else k_main<false><<<grid, warps * 32, smem, st>>>(B, q_single);
   return cudaGetLastError();
 }
 

@@ -184,7 +184,7 @@ void mrv_server::launch(Slot &s) {
   mrv_conflict *conf_h = (mrv_conflict *)((char *)s.pin_out + (((size_t)nq + 255) & ~size_t(255)));
   uint32_t *err_h = (uint32_t *)((char *)conf_h + sizeof(mrv_conflict) * (size_t)nq);
   if (!rc) {
-    BatchDev B = make_batchdev(ctx, &b, s.scratch, -1, ctx->tuning.chunk_tiles);
+    BatchDev B = make_batchdev(ctx, &b, s.scratch, -1, ctx->tuning.slices_per_item);
     rc = enqueue_run_on(ctx, B, s.scratch, false, s.scratch.out_valid, nullptr, s.scratch.out_conf, s.stream, s.ev0,
                         s.ev1);
   }

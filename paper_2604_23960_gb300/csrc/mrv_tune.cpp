@@ -1,5 +1,5 @@
-// Autotuner of the persistent scheduler: picks tiles per work item, warps
-// per block and blocks per SM for a batch class by timing candidates on the
+// Autotuner of the persistent scheduler: picks slices per work item, slices
+// per tile and warps per block for a batch class by timing candidates on the
 // batch itself (CUDA events around the persistent kernel), and caches the
 // winner in a text file keyed by device name and batch class.
 #include <cmath>
@@ -63,7 +63,7 @@ static bool cache_lookup(const char *path, const std::string &key, mrv_tuning *t
     std::istringstream in(line);
     std::string k;
     mrv_tuning c{};
-    if (in >> k >> c.chunk_tiles >> c.warps_per_block >> c.blocks_per_sm && k == key) {
+    if (in >> k >> c.slices_per_item >> c.warps_per_block >> c.blocks_per_sm >> c.tile_split && k == key) {
       *t = c;
       found = true;  // the last entry for a key wins
     }
@@ -74,7 +74,8 @@ static bool cache_lookup(const char *path, const std::string &key, mrv_tuning *t
 static void cache_store(const char *path, const std::string &key, const mrv_tuning &t) {
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << ' ' << t.chunk_tiles << ' ' << t.warps_per_block << ' ' << t.blocks_per_sm << '\n';
+  f << key << ' ' << t.slices_per_item << ' ' << t.warps_per_block << ' ' << t.blocks_per_sm << ' ' << t.tile_split
+    << '\n';
 }
 
 }  // namespace mrv
@@ -106,11 +107,13 @@ extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_pa
   uint8_t *valid = (uint8_t *)outs + ((size_t)b->n_queries * sizeof(mrv_conflict) + 255) / 256 * 256;
   const mrv_tuning saved = c->tuning;
   float best_ms = INFINITY;
-  static const int chunks[] = {1, 2, 4, 8, 16};
+  static const int chunks[] = {1, 2, 4};
+  static const int splits[] = {1, 2, 4, 8};
   static const int warps[] = {2, 4, 8};
   for (int w : warps)
-    for (int ch : chunks) {
-      mrv_tuning t{ch, w, 0, 0};
+    for (int sp : splits)
+      for (int ch : chunks) {
+      mrv_tuning t{ch, w, 0, sp};
       c->tuning = t;
       float total = 0.f;
       for (int rep = 0; rep < 3 && rc == MRV_OK; ++rep) {

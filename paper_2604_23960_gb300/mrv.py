@@ -64,12 +64,12 @@ class Conflict(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("states_available", C.c_uint64), ("states_checked", C.c_uint64), ("sphere_tests", C.c_uint64),
                 ("sphere_tests_available", C.c_uint64), ("work_items", C.c_uint64), ("n_valid", C.c_int32),
-                ("n_conflicts", C.c_int32), ("device_ms", C.c_float)]
+                ("n_conflicts", C.c_int32), ("device_ms", C.c_float), ("box_tests", C.c_uint64)]
 
 
 class Tuning(C.Structure):
-    _fields_ = [("chunk_tiles", C.c_int32), ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("fk_states", C.c_int32)]
+    _fields_ = [("slices_per_item", C.c_int32), ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("tile_split", C.c_int32)]
 
 
 class ServerOpts(C.Structure):
@@ -213,8 +213,8 @@ def mrv_get_stats(ctx) -> dict:
     return {k: getattr(s, k) for k, _ in Stats._fields_}
 
 
-def mrv_set_tuning(ctx, chunk_tiles=4, warps_per_block=4, blocks_per_sm=0):
-    t = Tuning(chunk_tiles, warps_per_block, blocks_per_sm, 0)
+def mrv_set_tuning(ctx, slices_per_item=1, warps_per_block=4, blocks_per_sm=0, tile_split=4):
+    t = Tuning(slices_per_item, warps_per_block, blocks_per_sm, tile_split)
     _check(lib().mrv_set_tuning(ctx, C.byref(t)), ctx)
 
 

@@ -54,6 +54,8 @@ def test_tiny_mv_ffc(ctx, seed, timed):
     bd = ba.to("cuda")
     np.testing.assert_array_equal(_np(ctx.mv_validate(bd)), ctx.mv_validate(ba))
     np.testing.assert_array_equal(_np(ctx.ffc_find(bd)), c)
+    # hierarchical order (Alg. 1): same verdicts
+    np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_HIERARCHICAL), ctx.mv_validate(ba))
     # one synchronous launch per query: identical results
     np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_PER_QUERY_LAUNCH), ctx.mv_validate(ba))
     np.testing.assert_array_equal(ctx.ffc_find(ba, flags=mrv.MRV_PER_QUERY_LAUNCH), c)
@@ -120,6 +122,7 @@ def test_cage_mv_small_exhaustive(ctx):
     ba = ctx.bind(w).to("cuda")
     v = _np(ctx.mv_validate(ba))
     PA.check_mv(o, v)
+    np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=mrv.MRV_HIERARCHICAL)), v)
     v2, mc = ctx.mv_validate(ba, exhaustive=True, min_clearance=True)
     np.testing.assert_array_equal(_np(v2), v)
     ref = o.mv_min_clearance(threads=PA.THREADS)
@@ -265,16 +268,19 @@ def test_tunings_do_not_change_results(ctx, tmp_path):
 
     ref = ctx.run(ba)
     saved = mrv.mrv_get_tuning(ctx.h)
-    for ch, wp in [(1, 2), (2, 8), (16, 4)]:
-        mrv.mrv_set_tuning(ctx.h, ch, wp, 0)
+    try:
+        for ch, wp, sp in [(1, 2, 1), (2, 8, 2), (16, 4, 8), (3, 12, 4), (1, 1, 4)]:
+            mrv.mrv_set_tuning(ctx.h, ch, wp, 0, sp)
+            assert same(ctx.run(ba), ref)
+        t = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
+        assert t["slices_per_item"] >= 1 and t["warps_per_block"] >= 1
+        assert (tmp_path / "tune.txt").read_text().strip()
+        t2 = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
+        assert t2 == t   # cached
         assert same(ctx.run(ba), ref)
-    t = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
-    assert t["chunk_tiles"] >= 1 and t["warps_per_block"] >= 1
-    assert (tmp_path / "tune.txt").read_text().strip()
-    t2 = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
-    assert t2 == t   # cached
-    assert same(ctx.run(ba), ref)
-    mrv.mrv_set_tuning(ctx.h, saved["chunk_tiles"], saved["warps_per_block"], saved["blocks_per_sm"])
+    finally:
+        mrv.mrv_set_tuning(ctx.h, saved["slices_per_item"], saved["warps_per_block"], saved["blocks_per_sm"],
+                           saved["tile_split"])
 
 
 # --------------------------------------------- full sizes, benchmark launches
