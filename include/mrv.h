@@ -181,6 +181,28 @@ int ffc_find(mrv_ctx *ctx, const mrv_batch *batch, mrv_conflict *out);
  * written); entries of the other output are left untouched. */
 int mrv_run(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out, mrv_conflict *conflict_out);
 
+/* ---- MotionValidation without allocation ---------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory while they validate motions, e.g. a planner
+ * inside a latency-bounded control loop (cudaMalloc / cudaFree can block, and
+ * cudaFree synchronizes the device) or an application whose device memory is
+ * already fully budgeted by its own allocator.  It computes exactly what
+ * mv_validate computes (early termination, MRV_CHECK_ENV honoured), but its
+ * per-call scratch is one static device array of about 0.66 MB that every GPU
+ * loading the library holds until the process exits, so the call performs no
+ * allocation.  The caller passes device pointers (MRV_PTRS_ON_DEVICE) for the
+ * batch and valid_out; at most MRV_NOALLOC_MAX_QUERIES queries and
+ * MRV_NOALLOC_MAX_WAYPOINTS waypoints (MRV_ERR_LIMIT beyond); MRV_ASYNC,
+ * MRV_EXHAUSTIVE and MRV_PER_QUERY_LAUNCH are rejected (MRV_ERR_ARG).  The
+ * first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls on a
+ * device share the array: each call resets what must start from zero, and
+ * calls whose work overlaps on the device race, so issue them on one stream
+ * or synchronize between them.  Returns after valid_out is written. */
+#define MRV_NOALLOC_MAX_QUERIES 4096
+#define MRV_NOALLOC_MAX_WAYPOINTS 65536
+int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out);
+
 /* Diagnostic: per-sphere minimum clearance of query `q` of the batch at the
  * listed timesteps (0 <= ts[k] <= T).  out: nt x M floats, M = spheres of the
  * query's robots in slot order; each value is the minimum over the checks

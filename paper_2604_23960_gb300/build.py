@@ -16,7 +16,7 @@ BUILD = PKG / "_build"
 LIB = PKG / "libmrv.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["mrv_kernels.cu"]
+CU_SOURCES = ["mrv_kernels.cu", "mrv_noalloc.cu"]
 CPP_SOURCES = ["mrv_api.cpp", "mrv_tune.cpp", "mrv_server.cpp", "mrv_geometry.cpp"]
 
 

@@ -1,0 +1,121 @@
+// MotionValidation without any allocation during the call.
+//
+// Some callers cannot allocate device memory when they validate motions: a
+// planner running inside a latency-bounded control loop (cudaMalloc and
+// cudaFree can block and cudaFree synchronizes the whole device), or a host
+// application whose device memory is owned by another allocator and fully
+// budgeted.  This entry point runs the same preparation, persistent and
+// result kernels as mv_validate, but every piece of per-call scratch lives in
+// one file-scope device array reserved when the library's device code is
+// loaded, so the call itself allocates nothing.
+//
+// The array is shared by every call on a device and keeps whatever the last
+// call left in it; each call re-initialises all of it that must start from a
+// known value (counters, error word, histograms by memset; per-query records
+// and waypoint times are rewritten by the preparation kernel).  Two calls
+// whose work overlaps on the same device race on the array: issue them on one
+// stream, or synchronize between them.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "mrv_internal.h"
+
+namespace mrv {
+namespace {
+
+// per-call scratch: waypoint times, per-query records and verdict words,
+// the sorted query list, level tables, counters, error word and statistics
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+constexpr size_t kBytes =
+    align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_WAYPOINTS) + align_up(sizeof(QueryDev) * MRV_NOALLOC_MAX_QUERIES) +
+    3 * align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) + align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) +
+    3 * align_up(sizeof(int32_t) * (kMaxLevels + 1)) + align_up(sizeof(int32_t) * 8) + align_up(sizeof(uint32_t) * 2) +
+    align_up(sizeof(unsigned long long) * 8) + align_up(sizeof(int32_t) * 4);
+
+static __device__ __align__(256) unsigned char g_scratch[kBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_addr[kMaxDevices];   // device address of g_scratch, per device
+
+// The address of g_scratch on the current device (host code cannot use the
+// symbol itself as a device pointer).  Looked up once per device.
+int scratch_address(int device, void **out) {
+  if (device < 0 || device >= kMaxDevices) return fail(MRV_ERR_ARG, "device %d outside 0..%d", device, kMaxDevices - 1);
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!g_scratch_addr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch symbol address");
+    g_scratch_addr[device] = p;
+  }
+  *out = g_scratch_addr[device];
+  return MRV_OK;
+}
+
+// Points a Scratch view at the static array (no staging buffers: inputs and
+// outputs are the caller's device arrays).
+void carve(void *base, int64_t nq, int64_t nw, Scratch *S) {
+  char *p = static_cast<char *>(base);
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    void *r = p + o;
+    o += align_up(n);
+    return r;
+  };
+  S->slot_tau = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_WAYPOINTS);
+  S->q = (QueryDev *)take(sizeof(QueryDev) * MRV_NOALLOC_MAX_QUERIES);
+  S->q_hit = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
+  S->q_best = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
+  S->q_minclr = (float *)take(sizeof(float) * MRV_NOALLOC_MAX_QUERIES);
+  S->sorted = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
+  S->hist = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
+  S->level_start = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
+  S->cursor = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
+  S->counters = (int32_t *)take(sizeof(int32_t) * 8);
+  S->err = (uint32_t *)take(sizeof(uint32_t) * 2);
+  S->stats = (unsigned long long *)take(sizeof(unsigned long long) * 8);
+  S->counts = (int32_t *)take(sizeof(int32_t) * 4);
+  (void)nq;
+  (void)nw;
+}
+
+}  // namespace
+}  // namespace mrv
+
+using namespace mrv;
+
+extern "C" int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *b, uint8_t *valid_out) {
+  if (!ctx || !b) return fail(MRV_ERR_ARG, "NULL argument");
+  if (!(b->flags & MRV_PTRS_ON_DEVICE))
+    return fail(MRV_ERR_ARG, "mv_validate_noalloc takes device pointers only (set MRV_PTRS_ON_DEVICE)");
+  if (b->flags & (MRV_ASYNC | MRV_PER_QUERY_LAUNCH | MRV_EXHAUSTIVE))
+    return fail(MRV_ERR_ARG, "mv_validate_noalloc runs the synchronous batched early-exit path only");
+  int rc = validate_batch(ctx, b);
+  if (rc) return rc;
+  if (b->n_queries == 0) return MRV_OK;
+  if (!valid_out) return fail(MRV_ERR_ARG, "valid_out is NULL");
+  if (b->n_queries > MRV_NOALLOC_MAX_QUERIES)
+    return fail(MRV_ERR_LIMIT, "%d queries exceed the allocation-free maximum of %d", b->n_queries,
+                MRV_NOALLOC_MAX_QUERIES);
+  if (b->n_waypoints > MRV_NOALLOC_MAX_WAYPOINTS)
+    return fail(MRV_ERR_LIMIT, "%d waypoints exceed the allocation-free maximum of %d", b->n_waypoints,
+                MRV_NOALLOC_MAX_WAYPOINTS);
+  if (ctx->pending && (rc = ctx->sync())) return rc;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  void *base = nullptr;
+  if ((rc = scratch_address(ctx->device, &base))) return rc;
+  Scratch S;   // a view only: it owns nothing (base stays null)
+  carve(base, b->n_queries, b->n_waypoints, &S);
+  const BatchDev B = make_batchdev(ctx, b, S, MRV_KIND_MV, ctx->tuning.slices_per_item);
+  if ((rc = enqueue_run_on(ctx, B, S, false, valid_out, nullptr, nullptr, ctx->stream, nullptr, nullptr))) return rc;
+  // the error word comes back through the context's pinned status word
+  e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mv_validate_noalloc");
+  return check_device_err(ctx->h_status[0]);
+}

@@ -34,6 +34,8 @@ MRV_KIND_MV = 0
 MRV_KIND_FFC = 1
 MRV_MAX_ROBOTS = 8
 MRV_MAX_QUERY_SPHERES = 512
+MRV_NOALLOC_MAX_QUERIES = 4096
+MRV_NOALLOC_MAX_WAYPOINTS = 65536
 ERR_NAMES = {-1: "MRV_ERR_ARG", -2: "MRV_ERR_OOM", -3: "MRV_ERR_NOT_FOUND", -4: "MRV_ERR_CUDA",
              -5: "MRV_ERR_TIMEOUT", -6: "MRV_ERR_BUSY", -7: "MRV_ERR_LIMIT"}
 
@@ -96,6 +98,7 @@ SIGNATURES = {
     "ffc_find": (C.c_int, [P, C.POINTER(BatchS), P]),
     "mrv_run": (C.c_int, [P, C.POINTER(BatchS), P, P]),
     "mrv_clearance": (C.c_int, [P, C.POINTER(BatchS), C.c_int32, P, C.c_int32, P]),
+    "mv_validate_noalloc": (C.c_int, [P, C.POINTER(BatchS), P]),
     "mrv_sync": (C.c_int, [P]),
     "mrv_get_stats": (C.c_int, [P, C.POINTER(Stats)]),
     "mrv_set_tuning": (C.c_int, [P, C.POINTER(Tuning)]),
@@ -189,6 +192,12 @@ def mrv_release(ctx, rid: int):
 
 def mv_validate(ctx, batch: BatchS, valid_out, min_clearance_out=None):
     _check(lib().mv_validate(ctx, C.byref(batch), _ptr(valid_out), _ptr(min_clearance_out)), ctx)
+
+
+def mv_validate_noalloc(ctx, batch: BatchS, valid_out):
+    """MV of a device-resident batch with no allocation during the call (the
+    scratch is a static device array; see include/mrv.h for the limits)."""
+    _check(lib().mv_validate_noalloc(ctx, C.byref(batch), _ptr(valid_out)), ctx)
 
 
 def ffc_find(ctx, batch: BatchS, out):
