@@ -162,6 +162,77 @@ def serving(ctx, duration_s=6.0, loads=(0.5, 0.8, 0.95), n_clients=64, seed=206)
     return out
 
 
+def other_configs(ctx, flush, per_query_n=1000, reps=3):
+    """Throughput of the other workload configurations (device-resident
+    inputs, batched persistent launch; the ragged batch replays a CUDA graph)
+    next to one synchronous launch per query on a sample of the same batch."""
+    import torch
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import workloads as W
+    out = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best.append(time.perf_counter() - t0)
+        return statistics.median(best)
+
+    def per_query(w, call):
+        sub = W.subset(w, np.arange(min(per_query_n, w.batch.n_queries)))
+        bs = ctx.bind(sub, ctx.robot_ids, ctx.env_ids).to("cuda")
+        call(bs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        call(bs)
+        torch.cuda.synchronize()
+        return sub.batch.n_queries / (time.perf_counter() - t0)
+
+    # two discs in the box world, 1,000 queries: MV and FFC
+    w = W.make_plain_discs(1000)
+    ba = ctx.bind(w).to("cuda")
+    for kind, call in (("mv", lambda b, f=0: ctx.mv_validate(b, flags=f)), ("ffc", lambda b, f=0: ctx.ffc_find(b, flags=f))):
+        dt = timed(lambda: call(ba))
+        pq = per_query(w, lambda b: call(b, mrv.MRV_PER_QUERY_LAUNCH))
+        out[f"discs_{kind}_1k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
+                                   "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3}
+    # four arms, 100k timed path-sets: FFC
+    w = W.make_cage_ffc(100000)
+    ba = ctx.bind(w).to("cuda")
+    dt = timed(lambda: ctx.ffc_find(ba))
+    st = ctx.stats()
+    pq = per_query(w, lambda b: ctx.ffc_find(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
+    out["cage_ffc_100k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
+                            "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
+                            "effort_states": st["states_checked"] / max(1, st["states_available"]),
+                            "kernel_ms": st["device_ms"]}
+    # ragged teams, 1M mixed MV/FFC queries in one persistent graph launch
+    w = W.make_ragged_teams(1_000_000)
+    ba = ctx.bind(w).to("cuda")
+    nq = w.batch.n_queries
+    valid = torch.empty(nq, dtype=torch.uint8, device="cuda")
+    conf = torch.empty((nq, 3), dtype=torch.int32, device="cuda")
+    g = mrv.mrv_graph_create(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), valid, conf)
+
+    def replay():
+        mrv.mrv_graph_launch(g)
+        ctx.sync()
+    dt = timed(replay)
+    st = ctx.stats()
+    mrv.mrv_graph_destroy(g)
+    pq = per_query(w, lambda b: ctx.run(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
+    out["ragged_teams_1m"] = {"value": nq / dt, "per_query_launch": pq, "speedup": nq / dt / pq, "ms": dt * 1e3,
+                              "effort_states": st["states_checked"] / max(1, st["states_available"]),
+                              "kernel_ms": st["device_ms"]}
+    return out
+
+
 def cpu_baseline(w, seconds_hint: float = 20.0):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
     from oracle import oracle as O
@@ -344,6 +415,8 @@ def run(args):
         "gpu_launches": 5 * args.steps,
         "clocks": clocks,
     }
+    if not args.no_configs:
+        line["configs"] = other_configs(ctx, flush)
     if not args.no_serve:
         line["serving"] = serving(ctx, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -368,6 +441,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -215,6 +215,18 @@ int mrv_clearance(mrv_ctx *ctx, const mrv_batch *batch, int32_t q, const int32_t
 /* Waits for MRV_ASYNC work on the context's stream; returns its status. */
 int mrv_sync(mrv_ctx *ctx);
 
+/* ---- failure detection -----------------------------------------------------
+ * kernel_budget_ms > 0 bounds the persistent kernel of every later call:
+ * each warp stops taking work items once its SM clock has run that long
+ * since the warp started, and the call returns MRV_ERR_TIMEOUT (its outputs
+ * are then incomplete).  0 = no bound (default).  The kernel never waits on
+ * anything, so the bound only cuts long batches short; the context stays
+ * usable.  (No counterpart in the paper.) */
+typedef struct {
+  double kernel_budget_ms;
+} mrv_limits;
+int mrv_set_limits(mrv_ctx *ctx, const mrv_limits *limits);
+
 /* ---- statistics of the last completed call -------------------------------- */
 typedef struct {
   uint64_t states_available; /* sum over queries of (T+1)                    */

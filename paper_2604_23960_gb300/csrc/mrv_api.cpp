@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <utility>
 
 namespace mrv {
@@ -22,6 +24,24 @@ int fail(int code, const char *fmt, ...) {
   va_end(ap);
   g_err = buf;
   return code;
+}
+
+// Host-side fault injection for tests: whenever the environment variable
+// MRV_FAULT_INJECT_ALLOC takes a value not seen before, the next device
+// allocation of this process fails as if the device were out of memory.
+cudaError_t dev_malloc(void **p, size_t n) {
+  static std::mutex mu;
+  static std::string seen;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const char *v = std::getenv("MRV_FAULT_INJECT_ALLOC");
+    if (v && *v && seen != v) {
+      seen = v;
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, n);
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -72,7 +92,7 @@ int Scratch::ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStre
       cap = 0;
     }
     size_t want = need + need / 4;
-    cudaError_t e = cudaMalloc(&base, want);
+    cudaError_t e = dev_malloc(&base, want);
     if (e != cudaSuccess) {
       cudaGetLastError();
       base = nullptr;
@@ -392,7 +412,7 @@ int mrv_ctx::push_tables() {
     if (need <= *cap && *dptr) return cudaSuccess;
     size_t c = std::max<size_t>(16, need * 2);
     void *p = nullptr;
-    cudaError_t r = cudaMalloc(&p, c * elem);
+    cudaError_t r = dev_malloc(&p, c * elem);
     if (r != cudaSuccess) return r;
     if (*dptr) cudaFree(*dptr);
     *dptr = p;
@@ -418,7 +438,7 @@ namespace mrv {
 static int upload(void **dst, const void *src, size_t n) {
   *dst = nullptr;
   if (n == 0) return MRV_OK;
-  cudaError_t e = cudaMalloc(dst, n);
+  cudaError_t e = dev_malloc(dst, n);
   if (e != cudaSuccess) {
     *dst = nullptr;
     return cuda_fail(e, "upload allocation");
@@ -691,6 +711,19 @@ int mrv_sync(mrv_ctx *c) {
   return c->sync();
 }
 
+int mrv_set_limits(mrv_ctx *c, const mrv_limits *l) {
+  if (!c || !l) return fail(MRV_ERR_ARG, "NULL argument");
+  if (!(l->kernel_budget_ms >= 0.0) || l->kernel_budget_ms > 1e9) return fail(MRV_ERR_ARG, "budget outside 0..1e9 ms");
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device) != cudaSuccess || khz <= 0) {
+    cudaGetLastError();
+    khz = 2070000;   // the GB300's maximum SM clock, a safe upper bound on ticks per ms
+  }
+  c->clock_budget = l->kernel_budget_ms > 0.0 ? (long long)(l->kernel_budget_ms * khz) : 0;
+  if (l->kernel_budget_ms > 0.0 && c->clock_budget < 1) c->clock_budget = 1;
+  return MRV_OK;
+}
+
 int mrv_get_stats(mrv_ctx *c, mrv_stats *out) {
   if (!c || !out) return fail(MRV_ERR_ARG, "NULL argument");
   *out = c->stats;
@@ -749,7 +782,7 @@ int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, 
   void *tmp = nullptr;
   if (!dev) {
     const size_t bytes = sizeof(int32_t) * nt + sizeof(float) * (size_t)nt * hq.M;
-    if ((e = cudaMalloc(&tmp, bytes)) != cudaSuccess) return cuda_fail(e, "clearance buffers");
+    if ((e = dev_malloc(&tmp, bytes)) != cudaSuccess) return cuda_fail(e, "clearance buffers");
     d_ts = (const int32_t *)tmp;
     d_out = (float *)((char *)tmp + sizeof(int32_t) * nt);
     e = cudaMemcpyAsync((void *)d_ts, ts, sizeof(int32_t) * nt, cudaMemcpyHostToDevice, st);

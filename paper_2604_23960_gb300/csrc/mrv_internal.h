@@ -14,6 +14,7 @@ namespace mrv {
 extern thread_local std::string g_err;
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
+cudaError_t dev_malloc(void **p, size_t n);   // cudaMalloc with test fault injection
 
 // device scratch of one run: derived per-query arrays, counters, staged
 // inputs and outputs; one arena, grown on demand, carved at 256-byte offsets

@@ -101,7 +101,7 @@ extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_pa
     return MRV_OK;
   }
   void *outs = nullptr;
-  cudaError_t e = cudaMalloc(&outs, (size_t)b->n_queries * (1 + sizeof(mrv_conflict)) + 256);
+  cudaError_t e = dev_malloc(&outs, (size_t)b->n_queries * (1 + sizeof(mrv_conflict)) + 256);
   if (e != cudaSuccess) return cuda_fail(e, "autotune outputs");
   mrv_conflict *conf = (mrv_conflict *)outs;
   uint8_t *valid = (uint8_t *)outs + ((size_t)b->n_queries * sizeof(mrv_conflict) + 255) / 256 * 256;

@@ -74,6 +74,10 @@ class Tuning(C.Structure):
                 ("tile_split", C.c_int32)]
 
 
+class Limits(C.Structure):
+    _fields_ = [("kernel_budget_ms", C.c_double)]
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("n_streams", C.c_int32), ("device_budget_bytes", C.c_size_t), ("max_batch_queries", C.c_int32),
                 ("max_pending", C.c_int32)]
@@ -100,6 +104,7 @@ SIGNATURES = {
     "mrv_clearance": (C.c_int, [P, C.POINTER(BatchS), C.c_int32, P, C.c_int32, P]),
     "mv_validate_noalloc": (C.c_int, [P, C.POINTER(BatchS), P]),
     "mrv_sync": (C.c_int, [P]),
+    "mrv_set_limits": (C.c_int, [P, C.POINTER(Limits)]),
     "mrv_get_stats": (C.c_int, [P, C.POINTER(Stats)]),
     "mrv_set_tuning": (C.c_int, [P, C.POINTER(Tuning)]),
     "mrv_get_tuning": (C.c_int, [P, C.POINTER(Tuning)]),
@@ -214,6 +219,10 @@ def mrv_clearance(ctx, batch: BatchS, q: int, ts, out):
 
 def mrv_sync(ctx):
     _check(lib().mrv_sync(ctx), ctx)
+
+
+def mrv_set_limits(ctx, kernel_budget_ms: float = 0.0):
+    _check(lib().mrv_set_limits(ctx, C.byref(Limits(kernel_budget_ms))), ctx)
 
 
 def mrv_get_stats(ctx) -> dict:

@@ -50,7 +50,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
     from paper_2604_23960_gb300 import mrv
     pairs = {"mrv_batch": mrv.BatchS, "mrv_robot_desc": mrv.RobotDesc, "mrv_env_desc": mrv.EnvDesc,
              "mrv_conflict": mrv.Conflict, "mrv_stats": mrv.Stats, "mrv_tuning": mrv.Tuning,
-             "mrv_server_opts": mrv.ServerOpts, "mrv_server_stats": mrv.ServerStats}
+             "mrv_server_opts": mrv.ServerOpts, "mrv_server_stats": mrv.ServerStats, "mrv_limits": mrv.Limits}
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{ROOT / "include" / "mrv.h"}"', "int main(void){"]
     for cname, py in pairs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
