@@ -65,6 +65,8 @@ extern "C" {
 #define MRV_ASYNC 0x10u           /* return before completion (see above)   */
 #define MRV_PER_QUERY_LAUNCH 0x20u /* baseline: one synchronous kernel
                                       launch per query                      */
+#define MRV_NO_BROADPHASE 0x40u   /* test every sphere pair (no frame-level
+                                     bounding-sphere culling); same results */
 
 /* ---- query kinds (mrv_run) ---------------------------------------------- */
 #define MRV_KIND_MV 0

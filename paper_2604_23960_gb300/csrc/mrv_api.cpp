@@ -153,7 +153,7 @@ int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
   if (!b->q_robot_off || !b->slot_robot_id || !b->slot_wp_off || !b->waypoints)
     return fail(MRV_ERR_ARG, "missing batch array");
   if (b->flags & ~(uint32_t)(MRV_CHECK_ENV | MRV_HIERARCHICAL | MRV_EXHAUSTIVE | MRV_PTRS_ON_DEVICE | MRV_ASYNC |
-                             MRV_PER_QUERY_LAUNCH))
+                             MRV_PER_QUERY_LAUNCH | MRV_NO_BROADPHASE))
     return fail(MRV_ERR_ARG, "unknown flag bits 0x%x", b->flags);
   if ((b->flags & MRV_ASYNC) && !(b->flags & MRV_PTRS_ON_DEVICE))
     return fail(MRV_ERR_ARG, "MRV_ASYNC requires MRV_PTRS_ON_DEVICE");
@@ -562,30 +562,45 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
       D.dh[k][4] = r[3];
     }
   for (int s = 0; s < d->n_spheres; ++s) D.r2max = std::max(D.r2max, d->sphere_xyzr[4 * s + 3] * d->sphere_xyzr[4 * s + 3]);
-  // self pairs as (smaller, larger) index, sorted: neighbouring lanes then
-  // read the same or adjacent spheres
-  std::vector<std::pair<int32_t, int32_t>> sp(d->n_self_pairs);
-  for (int p = 0; p < d->n_self_pairs; ++p)
-    sp[p] = std::minmax(d->self_pairs[2 * p], d->self_pairs[2 * p + 1]);
-  std::sort(sp.begin(), sp.end());
+  // spheres grouped by frame with one bounding sphere per frame; self pairs
+  // grouped by frame pair (the order within a group keeps neighbouring lanes
+  // on the same or adjacent spheres)
+  const int n_links = d->kind == MRV_ROBOT_POINT ? 2 : d->dof + 2;
+  const PreparedModel PM = prepare_model(n_links, d->n_spheres, d->sphere_link, d->sphere_xyzr, d->n_self_pairs,
+                                         d->self_pairs);
+  const auto &sp = PM.self;
   // packed x | y << 16; the tail up to a multiple of 4 repeats the last pair
-  // (the kernel reads four pairs per load; a repeated pair changes no verdict)
+  // (a repeated pair changes no verdict)
   std::vector<uint32_t> spf((sp.size() + 3) / 4 * 4);
   for (size_t p = 0; p < spf.size(); ++p) {
     const auto &e = sp[std::min(p, sp.size() - 1)];
     spf[p] = (uint32_t)e.first | ((uint32_t)e.second << 16);
   }
+  D.n_links = n_links;
+  for (int l = 0; l <= n_links; ++l) D.link_start[l] = PM.link_start[l];
+  for (int l = 0; l < n_links; ++l)
+    for (int k = 0; k < 4; ++k) D.link_bs[l][k] = PM.link_bs[4 * l + k];
   int rc;
-  if ((rc = upload(&m.d_spheres, d->sphere_xyzr, sizeof(float) * 4 * d->n_spheres))) return rc;
-  if ((rc = upload(&m.d_links, d->sphere_link, sizeof(int32_t) * d->n_spheres))) { m.free_all(); return rc; }
+  if ((rc = upload(&m.d_spheres, PM.spheres.data(), sizeof(float) * PM.spheres.size()))) return rc;
+  if ((rc = upload(&m.d_links, PM.links.data(), sizeof(int32_t) * PM.links.size()))) { m.free_all(); return rc; }
   if ((rc = upload(&m.d_self, spf.data(), sizeof(uint32_t) * spf.size()))) { m.free_all(); return rc; }
+  if ((rc = upload(&m.d_groups, PM.self_groups.data(), sizeof(int32_t) * PM.self_groups.size()))) {
+    m.free_all();
+    return rc;
+  }
+  if ((rc = upload(&m.d_perm, PM.perm.data(), sizeof(int32_t) * PM.perm.size()))) { m.free_all(); return rc; }
   // rectangles pay off only when they are large enough to fill a warp's
   // 4-rows-per-lane tiling; small ones stay on the sparse pair path
-  std::vector<int32_t> rects = self_pair_rectangles(d->n_spheres, sp, 256);
+  std::vector<std::pair<int32_t, int32_t>> spr(sp);
+  std::sort(spr.begin(), spr.end());
+  std::vector<int32_t> rects = self_pair_rectangles(d->n_spheres, spr, 256);
   if (!rects.empty() && (int64_t)sp.size() < 64 * (int64_t)(rects.size() / 4)) rects.clear();
   if ((rc = upload(&m.d_rects, rects.data(), sizeof(int32_t) * rects.size()))) { m.free_all(); return rc; }
   D.self_rects = (const int4 *)m.d_rects;
   D.n_rects = (int32_t)rects.size() / 4;
+  D.self_groups = (const int4 *)m.d_groups;
+  D.n_groups = (int32_t)PM.self_groups.size() / 4;
+  D.perm = (const int32_t *)m.d_perm;
   D.spheres = (const float4 *)m.d_spheres;
   D.sphere_link = (const int32_t *)m.d_links;
   D.self_pairs = (const uint32_t *)m.d_self;

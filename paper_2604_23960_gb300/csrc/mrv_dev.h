@@ -41,14 +41,21 @@ struct ModelDev {
   float base[12];
   float flange[12];
   float dh[MRV_MAX_DOF][5];      // cos(alpha), sin(alpha), a, d, theta_offset
-  const float4 *spheres;         // local xyz, radius
+  const float4 *spheres;         // local xyz, radius; sorted by frame
   const int32_t *sphere_link;
-  const uint32_t *self_pairs;    // x | y << 16 with x < y, sorted, padded by
-                                 // repeating the last pair to a multiple of 4
+  const uint32_t *self_pairs;    // x | y << 16 with x < y, grouped by frame
+                                 // pair, padded by repeating the last pair to a
+                                 // multiple of 4 (indices of the sorted spheres)
   const int4 *self_rects;        // the same pairs as rectangles (x0, x1, y0, y1):
                                  // rows x0..x1-1 against columns y0..y1-1
   int32_t n_rects;               // 0: use the sparse list
-  int32_t pad2;
+  int32_t n_links;               // frames 0..n_links-1 (DH: dof + 2, point: 2)
+  int32_t link_start[kMaxLinks + 1];  // spheres (sorted by frame) of frame l
+  float link_bs[kMaxLinks][4];   // frame-local bounding sphere (radius < 0: empty)
+  const int4 *self_groups;       // (frame u, frame v, first pair, count)
+  int32_t n_groups;
+  int32_t pad3;
+  const int32_t *perm;           // sorted sphere index -> caller's index
 };
 
 struct EnvDev {

@@ -16,4 +16,25 @@ namespace mrv {
 std::vector<int32_t> self_pair_rectangles(int m, const std::vector<std::pair<int32_t, int32_t>> &pairs,
                                           int max_rects);
 
+// A robot model rearranged for the kernels: spheres grouped by the frame
+// they are attached to, one bounding sphere per frame (for the link-level
+// broadphase), self pairs grouped by frame pair.
+struct PreparedModel {
+  int n_links = 0;                     // frames 0..n_links-1
+  std::vector<float> spheres;          // m x 4, sorted by frame (stable)
+  std::vector<int32_t> links;          // frame of each sorted sphere
+  std::vector<int32_t> perm;           // sorted index -> caller's index
+  std::vector<int32_t> link_start;     // n_links + 1: spheres of frame l are [start[l], start[l+1])
+  std::vector<float> link_bs;          // n_links x 4: frame-local center, radius (radius < 0: no spheres)
+  std::vector<std::pair<int32_t, int32_t>> self;  // (x < y) in sorted indices, by (frame x, frame y, x, y)
+  std::vector<int32_t> self_groups;    // n_groups x 4: frame u, frame v, first pair, pair count
+};
+
+// Bounding sphere of a frame: center = middle of the bounding box of the
+// frame's sphere centers, radius = max(|c_s - center| + r_s) computed in
+// double and enlarged by a relative 1e-6 and an absolute 1e-4 (so an FP32
+// separation test of two bounding spheres never hides a sphere overlap).
+PreparedModel prepare_model(int n_links, int m, const int32_t *link, const float *xyzr, int n_self,
+                            const int32_t *pairs);
+
 }  // namespace mrv

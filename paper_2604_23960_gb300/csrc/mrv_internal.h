@@ -45,15 +45,15 @@ struct Scratch {
 
 struct HostModel {
   ModelDev dev{};
-  void *d_spheres = nullptr, *d_links = nullptr, *d_self = nullptr, *d_rects = nullptr;
+  void *d_spheres = nullptr, *d_links = nullptr, *d_self = nullptr, *d_rects = nullptr, *d_groups = nullptr,
+       *d_perm = nullptr;
   int refs = 0;
   int max_spheres = 0;
   void free_all() {
-    if (d_spheres) cudaFree(d_spheres);
-    if (d_links) cudaFree(d_links);
-    if (d_self) cudaFree(d_self);
-    if (d_rects) cudaFree(d_rects);
-    d_spheres = d_links = d_self = d_rects = nullptr;
+    for (void **p : {&d_spheres, &d_links, &d_self, &d_rects, &d_groups, &d_perm}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
   }
 };
 

@@ -45,7 +45,7 @@
 namespace mrv {
 
 constexpr int kFlavorAMaxSpheres = 16;
-constexpr int kSlotWords = 18;                   // ints per RobotSlot in shared memory
+constexpr int kSlotWords = 18;                   // words per RobotSlot in shared memory
 constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
 
 struct RobotSlot {           // per-warp staged view of one robot of the query
@@ -53,12 +53,13 @@ struct RobotSlot {           // per-warp staged view of one robot of the query
   const int32_t *links;
   const uint32_t *self;      // packed pairs x | y << 16, padded to a multiple of 4
   const int4 *rects;         // self pairs as rectangles (rows x0..x1, columns y0..y1)
+  const ModelDev *md;        // the model (frame ranges, bounding spheres, groups)
   int32_t mdl, m, dof, kind, n_self, w0, w1, n_rects;
 };
 static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
 struct TileCtx {
-  int q, T, n, M, nb, ffc, check_env, exhaustive;
+  int q, T, n, M, nb, ffc, check_env, exhaustive, broad;
   int split, spt, nslices;
   int env_ns, env_nb;
   const float4 *env_s;
@@ -81,6 +82,8 @@ struct WarpSmem {
   float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
   float EK[kEnvCache];       // their |c|^2 - r^2
   float4 BL[kBoxCache], BH[kBoxCache];   // obstacle boxes
+  float4 BS[MRV_MAX_ROBOTS * kMaxLinks];  // per (robot, frame) bounding sphere at the
+                                          // current state (center relative to o; w < 0: none)
   union {
     struct {
       float xf[kFkChains * kMaxLinks * 12];   // link frames of one FK round
@@ -92,6 +95,8 @@ struct WarpSmem {
 };
 
 __host__ __device__ constexpr size_t warp_smem_bytes() { return (sizeof(WarpSmem) + 15) & ~size_t(15); }
+// 12 warps (3 blocks of 4) must fit the SM's 228 KB with 1 KB reserved per block
+static_assert(12 * ((sizeof(WarpSmem) + 15) & ~size_t(15)) + 3 * 1024 <= 233472, "shared memory per warp");
 
 __device__ __forceinline__ int pair_index(int i, int j, int n) { return i * n - i * (i + 1) / 2 + (j - i - 1); }
 
@@ -653,6 +658,150 @@ __device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, con
   return hit;
 }
 
+// ---------------------------------------------------------------------------
+// frame-level broadphase (default for kinematic chains)
+// ---------------------------------------------------------------------------
+// Every frame of every robot carries a bounding sphere of its spheres
+// (enlarged so that an FP32 separation test is conservative).  Sphere tests
+// run only for frame pairs (and frame / obstacle pairs) whose bounding spheres
+// overlap; all others cannot hold a collision.  Verdicts are those of the
+// full test.
+
+// bounding spheres of every (robot, frame) at the state whose frames sit in
+// FK slot jj of xf
+__device__ void link_spheres(const TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane) {
+  const int n = C.n;
+  for (int k = lane; k < n * kMaxLinks; k += kWarp) {
+    const int r = k / kMaxLinks, l = k - r * kMaxLinks;
+    const ModelDev &md = *S.rs[r].md;
+    float4 o = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (l < md.n_links && md.link_bs[l][3] >= 0.f) {
+      const float *X = xf + ((jj * n + r) * kMaxLinks + l) * 12;
+      const float cx = md.link_bs[l][0], cy = md.link_bs[l][1], cz = md.link_bs[l][2];
+      o.x = fmaf(X[0], cx, fmaf(X[1], cy, fmaf(X[2], cz, X[3]))) - S.ox;
+      o.y = fmaf(X[4], cx, fmaf(X[5], cy, fmaf(X[6], cz, X[7]))) - S.oy;
+      o.z = fmaf(X[8], cx, fmaf(X[9], cy, fmaf(X[10], cz, X[11]))) - S.oz;
+      o.w = md.link_bs[l][3];
+    }
+    S.BS[k] = o;
+  }
+}
+
+// robot-robot checks: MV -> 1 on a collision; FFC -> bitmask of colliding
+// pairs.  Lane k owns the bounding sphere of (robot i, frame u) and scans the
+// frame spheres of every later robot (broadcast reads); where two overlap
+// the lane tests their spheres itself (overlaps are rare).
+__device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, bool ffc,
+                                unsigned long long &ntests) {
+  unsigned pm = 0;
+  const int nk = C.n * kMaxLinks;
+  for (int k0 = 0; k0 < nk; k0 += kWarp) {
+    const int k = k0 + lane;
+    const int i = k / kMaxLinks, u = k - i * kMaxLinks;   // constant divisor
+    const float4 bu = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
+    if (bu.w >= 0.f) {
+      const ModelDev &mi = *S.rs[i].md;
+      const int a0 = S.off[i] + mi.link_start[u], a1 = S.off[i] + mi.link_start[u + 1];
+      for (int k2 = (i + 1) * kMaxLinks; k2 < nk; ++k2) {
+        const float4 bv = S.BS[k2];
+        if (bv.w < 0.f) continue;
+        ntests += 1;
+        if (!sph_hit(bu, bv)) continue;
+        const int j = k2 / kMaxLinks, v = k2 - j * kMaxLinks;
+        const ModelDev &mj = *S.rs[j].md;
+        const int b0 = S.off[j] + mj.link_start[v], b1 = S.off[j] + mj.link_start[v + 1];
+        bool h = false;
+        for (int a = a0; a < a1 && !h; ++a) {
+          const float4 pa = P[a];
+          for (int b = b0; b < b1; ++b) h |= sph_hit(pa, P[b]);
+          ntests += (unsigned long long)(b1 - b0);
+        }
+        if (h) pm |= ffc ? (1u << pair_index(i, j, C.n)) : 1u;
+      }
+    }
+  }
+  return pm;
+}
+
+// robot-obstacle and self checks (MV with the environment).  Lane k owns
+// the bounding sphere of (robot r, frame l) and scans the obstacle spheres and
+// boxes (broadcast reads); overlaps are resolved sphere by sphere in the lane.
+__device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, unsigned long long &ntests,
+                          unsigned long long &nbox) {
+  bool hit = false;
+  const int nk = C.n * kMaxLinks;
+  const int ns_c = min(C.env_ns, kEnvCache), nb_c = min(C.env_nb, kBoxCache);
+  for (int k0 = 0; k0 < nk; k0 += kWarp) {
+    const int k = k0 + lane;
+    const float4 bl = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
+    if (bl.w < 0.f) continue;
+    const int r = k / kMaxLinks, l = k - r * kMaxLinks;
+    const ModelDev &md = *S.rs[r].md;
+    const int a0 = S.off[r] + md.link_start[l], a1 = S.off[r] + md.link_start[l + 1];
+    const float4 bw = make_float4(bl.x + S.ox, bl.y + S.oy, bl.z + S.oz, bl.w);
+    for (int e = 0; e < C.env_ns; ++e) {
+      const float4 es = e < ns_c ? S.ES[e] : __ldg(&C.env_s[e]);
+      ntests += 1;
+      if (!sph_hit(bw, es)) continue;
+      for (int a = a0; a < a1; ++a) {
+        const float4 p = P[a];
+        hit |= sph_hit(make_float4(p.x + S.ox, p.y + S.oy, p.z + S.oz, p.w), es);
+        ntests += 1;
+      }
+    }
+    const float rr = bw.w * bw.w;
+    for (int b = 0; b < C.env_nb; ++b) {
+      const float4 lo = b < nb_c ? S.BL[b] : __ldg(&C.box_lo[b]);
+      const float4 hi = b < nb_c ? S.BH[b] : __ldg(&C.box_hi[b]);
+      ntests += 1;
+      nbox += 1;
+      if (!(box_d2(bw.x, bw.y, bw.z, lo, hi) < rr)) continue;
+      for (int a = a0; a < a1; ++a) {
+        const float4 p = P[a];
+        hit |= box_d2(p.x + S.ox, p.y + S.oy, p.z + S.oz, lo, hi) < p.w * p.w;
+        ntests += 1;
+        nbox += 1;
+      }
+    }
+  }
+  if (!C.exhaustive && __any_sync(0xffffffffu, hit)) return true;
+  // self pairs, grouped by frame pair: lanes test the groups' bounding
+  // spheres, then the warp walks the overlapping groups' pairs together
+  for (int r = 0; r < C.n; ++r) {
+    const ModelDev &md = *S.rs[r].md;
+    const int o = S.off[r];
+    const int ng = md.n_groups;
+    for (int g0 = 0; g0 < ng; g0 += kWarp) {
+      const int g = g0 + lane;
+      int4 G = make_int4(0, 0, 0, 0);
+      bool ov = false;
+      if (g < ng) {
+        G = __ldg(&md.self_groups[g]);
+        ov = sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y]);
+        ntests += 1;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, ov);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int gs = __shfl_sync(0xffffffffu, G.z, src), gc = __shfl_sync(0xffffffffu, G.w, src);
+        for (int p = lane; p < gc; p += kWarp) {
+          const uint32_t e = __ldg(&md.self_pairs[gs + p]);
+          hit |= sph_hit(P[o + (int)(e & 0xffffu)], P[o + (int)(e >> 16)]);
+          ntests += 1;
+        }
+      }
+    }
+  }
+  return hit;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // clearance mode (exhaustive MV with min_clearance_out): direct formulas
 __device__ void clr_state(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, bool do_env, bool do_pairs,
                           float &minclr) {
@@ -736,6 +885,42 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
       if (need_env) cw2 = warp_max(cw2);
       __syncwarp();
       const float eps = kEpsU * (c2 + C.rho2);
+      if (!CLR && C.broad) {
+        // frame-level broadphase, then exact tests of the overlapping frames
+        link_spheres(C, S, xf, j - j0, lane);
+        __syncwarp();
+        unsigned long long nt = 0, nbx = 0;
+        int res = 0;
+        if (!C.ffc) {
+          bool hit = false;
+          if (need_env) hit = env_broad(C, S, P, lane, nt, nbx);
+          // warp-uniform decision before the pair phase (it votes inside)
+          const bool env_hit = __any_sync(0xffffffffu, hit);
+          if (do_pairs && !(env_hit && !C.exhaustive)) hit |= pairs_broad(C, S, P, lane, false, nt) != 0;
+          res = __any_sync(0xffffffffu, hit);
+        } else {
+          res = (int)__reduce_or_sync(0xffffffffu, pairs_broad(C, S, P, lane, true, nt));
+        }
+        nt = warp_sum(nt);
+        nbx = warp_sum(nbx);
+        if (lane == 0) {
+          C.tests += nt;
+          C.btests += nbx;
+        }
+        __syncwarp();
+        if (res) {
+          if (!C.ffc) {
+            if (!C.exhaustive) return 1;
+            found = 1;
+          } else {
+            const int key = t * 32 + (__ffs((unsigned)res) - 1);
+            if (!C.exhaustive) return key;
+            if (key < found) found = key;
+          }
+        }
+        __syncwarp();
+        continue;
+      }
       if (!C.ffc) {
         bool hit = false;
         if (CLR) {
@@ -793,6 +978,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
   C.check_env = (!C.ffc) && (B.flags & MRV_CHECK_ENV);
   C.exhaustive = (B.flags & MRV_EXHAUSTIVE) ? 1 : 0;
   C.split = Q.split; C.spt = Q.spt; C.nslices = Q.nslices;
+  C.broad = (B.flags & MRV_NO_BROADPHASE) ? 0 : 1;
   C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
   C.env_c2 = 0.f; C.env_r2 = 0.f; C.rho2 = Q.rho2;
   if (C.check_env && Q.env >= 0) {
@@ -808,7 +994,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     const int id = B.slot_robot_id[s0 + lane];
     const ModelDev &m = B.models[id];
     RobotSlot rs;
-    rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects;
+    rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects; rs.md = &m;
     rs.mdl = id; rs.m = m.n_spheres; rs.dof = m.dof; rs.kind = m.kind; rs.n_self = m.n_self;
     rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.n_rects = m.n_rects;
     S.rs[lane] = rs;
@@ -963,7 +1149,7 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
     const int id = B.slot_robot_id[s0 + threadIdx.x];
     const ModelDev &m = B.models[id];
     RobotSlot r;
-    r.spheres = m.spheres; r.links = m.sphere_link; r.self = m.self_pairs; r.rects = m.self_rects;
+    r.spheres = m.spheres; r.links = m.sphere_link; r.self = m.self_pairs; r.rects = m.self_rects; r.md = &m;
     r.mdl = id; r.m = m.n_spheres; r.dof = m.dof; r.kind = m.kind; r.n_self = m.n_self;
     r.w0 = B.slot_wp_off[s0 + threadIdx.x]; r.w1 = B.slot_wp_off[s0 + threadIdx.x + 1]; r.n_rects = m.n_rects;
     rs[threadIdx.x] = r;
@@ -1013,7 +1199,8 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
         else if (ey == li) m = fminf(m, sph_clr(pa, P[off[r] + ex]));
       }
     }
-    out[(size_t)k * Q.M + a] = m;
+    // spheres are stored sorted by frame; the output keeps the caller's order
+    out[(size_t)k * Q.M + off[r] + rs[r].md->perm[a - off[r]]] = m;
   }
 }
 

@@ -56,6 +56,11 @@ def test_tiny_mv_ffc(ctx, seed, timed):
     np.testing.assert_array_equal(_np(ctx.ffc_find(bd)), c)
     # hierarchical order (Alg. 1): same verdicts
     np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_HIERARCHICAL), ctx.mv_validate(ba))
+    # every sphere pair tested (no frame-level broadphase): same verdicts
+    for ce in (True, False):
+        np.testing.assert_array_equal(ctx.mv_validate(ba, check_env=ce, flags=mrv.MRV_NO_BROADPHASE),
+                                      ctx.mv_validate(ba, check_env=ce))
+    np.testing.assert_array_equal(ctx.ffc_find(ba, flags=mrv.MRV_NO_BROADPHASE), c)
     # one synchronous launch per query: identical results
     np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_PER_QUERY_LAUNCH), ctx.mv_validate(ba))
     np.testing.assert_array_equal(ctx.ffc_find(ba, flags=mrv.MRV_PER_QUERY_LAUNCH), c)
@@ -123,12 +128,15 @@ def test_cage_mv_small_exhaustive(ctx):
     v = _np(ctx.mv_validate(ba))
     PA.check_mv(o, v)
     np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=mrv.MRV_HIERARCHICAL)), v)
+    np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=mrv.MRV_NO_BROADPHASE)), v)
     v2, mc = ctx.mv_validate(ba, exhaustive=True, min_clearance=True)
     np.testing.assert_array_equal(_np(v2), v)
     ref = o.mv_min_clearance(threads=PA.THREADS)
     np.testing.assert_allclose(_np(mc), ref, atol=PA.CLR_TOL, rtol=0)
     st = ctx.stats()
     assert st["states_checked"] == st["states_available"]
+    ctx.mv_validate(ba, exhaustive=True, flags=mrv.MRV_NO_BROADPHASE)
+    st = ctx.stats()
     assert st["sphere_tests"] == st["sphere_tests_available"]
 
 
@@ -138,6 +146,7 @@ def test_cage_ffc_small(ctx):
     ba = ctx.bind(w).to("cuda")
     c = _np(ctx.ffc_find(ba))
     PA.check_ffc(o, c)
+    np.testing.assert_array_equal(_np(ctx.ffc_find(ba, flags=mrv.MRV_NO_BROADPHASE)), c)
     np.testing.assert_array_equal(_np(ctx.ffc_find(ba, exhaustive=True)), c)
 
 
