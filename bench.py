@@ -30,7 +30,18 @@ sys.path.insert(0, str(ROOT))
 METRIC = "MV/FFC motion-checks/s vs per-query launch; p50/p99 latency, 1 GB300"
 WORKLOAD = "cage_mv: MV, 4 Panda-like 7-DOF arms x 64 spheres, cage env 40 spheres + 12 boxes, " \
            "10k start/goal joint-space motions, resolution 1/32 rad"
-FLOPS_PER_TEST = 10     # FP32 flops of one sphere-sphere test (3 sub, 1 mul + 2 fma, radius add + square)
+# FP32 flops per unit of work the kernel counts (FMA = 2):
+FLOPS_PER_TEST = 10     # sphere-sphere test: 3 sub, 1 mul + 2 fma, radius add + square
+FLOPS_PER_BOX = 13      # sphere-box test: per axis clamp + sub + fma, radius square
+FLOPS_PER_CHAIN = 390   # 7-joint modified-DH chain + flange: 48 per joint, 54 for the flange
+FLOPS_PER_SPHERE = 28   # sphere placement: 3x4 transform, shift, |p|^2 - r^2
+
+
+def work_flops(st):
+    """Algorithmic FP32 flops of one call from its counters."""
+    box = st["box_tests"]
+    return (FLOPS_PER_TEST * (st["sphere_tests"] - box) + FLOPS_PER_BOX * box
+            + FLOPS_PER_CHAIN * st["fk_chains"] + FLOPS_PER_SPHERE * st["spheres_placed"])
 MAKERS = None
 
 
@@ -294,7 +305,9 @@ def run(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     ctx = mrv.Context(local, stream.cuda_stream)
-    w = W.make_cage_mv(args.queries)
+    # weak scaling: every rank validates its own 10k motions (distinct seeds),
+    # with no collective on the data path
+    w = W.make_cage_mv(args.queries, query_seed=203 + rank)
     ba_host = ctx.bind(w)
     ba = ba_host.to("cuda")
     nq = w.batch.n_queries
@@ -331,7 +344,8 @@ def run(args):
                 step()
                 ev[i][1].record(stream)
                 ctx.sync()
-                kern_ms.append(ctx.stats()["device_ms"])
+                st_step = ctx.stats()
+                kern_ms.append(st_step["device_ms"])
         torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     if world > 1:
@@ -353,12 +367,22 @@ def run(args):
         for i in range(max(3, min(args.steps, 10))):
             flush.zero_()
             torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
             t0 = time.perf_counter()
             out = ctx.mv_validate(bh)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     assert int(out.sum()) == nvalid
     h2d = sum(v.numel() * v.element_size() for k, v in bh.a.items() if v is not None and k != "q_kind")
-    e2e_val = nq / (statistics.median(e2e_ms) / 1e3)
+    e2e_t = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = nq * world / (float(e2e_t.item()) / 1e3)
+    if rank != 0:   # the remaining measurements run on rank 0 only
+        mrv.mrv_graph_destroy(graph)
+        ctx.close()
+        dist.destroy_process_group()
+        return
 
     # one synchronous launch per query (the plain GPU path)
     pq_n = min(nq, args.per_query_n)
@@ -372,23 +396,29 @@ def run(args):
     pq_rate = pq_n / (time.perf_counter() - t0)
     assert torch.equal(pq_valid, valid[:pq_n])
 
-    # exhaustive pass (every check of every state): the roofline of the kernel
+    # exhaustive passes (every state of every motion): with the frame-level
+    # broadphase, and testing every sphere pair (the dense, ALU-bound regime)
     torch.cuda.nvtx.range_push("exhaustive")
-    ctx.mv_validate(ba, exhaustive=True)
-    ex_ms = []
-    for _ in range(3):
-        flush.zero_()
-        ctx.mv_validate(ba, exhaustive=True)
-        ex_ms.append(ctx.stats()["device_ms"])
-    ex_stats = ctx.stats()
+    ex = {}
+    for name, flags in (("broadphase", 0), ("dense", mrv.MRV_NO_BROADPHASE)):
+        ctx.mv_validate(ba, exhaustive=True, flags=flags)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            ctx.mv_validate(ba, exhaustive=True, flags=flags)
+            ms.append(ctx.stats()["device_ms"])
+        ex[name] = (statistics.median(ms), ctx.stats())
     torch.cuda.nvtx.range_pop()
 
     peaks, src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     kms = statistics.mean(kern_ms)
-    achieved = stats["sphere_tests"] * FLOPS_PER_TEST / (kms / 1e3) / 1e12
-    ex_achieved = ex_stats["sphere_tests"] * FLOPS_PER_TEST / (statistics.median(ex_ms) / 1e3) / 1e12
+    achieved = work_flops(st_step) / (kms / 1e3) / 1e12
+    ex_out = {name: {"kernel_ms": ms, "achieved": work_flops(st) / (ms / 1e3) / 1e12,
+                     "frac": work_flops(st) / (ms / 1e3) / 1e12 / fp32_peak,
+                     "sphere_tests": st["sphere_tests"], "fk_chains": st["fk_chains"]}
+              for name, (ms, st) in ex.items()}
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "motion-checks/s", "n_gpus": world, "steps": args.steps,
@@ -400,16 +430,17 @@ def run(args):
                    "tuning": mrv.mrv_get_tuning(ctx.h)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "k_main (persistent MV kernel), early exit",
+                     "kernel": "k_main (persistent MV kernel), early exit, frame-level broadphase",
+                     "work": "sphere/box tests (bounding-sphere and exact), FK chains and sphere placement, "
+                             "counted by the kernel per step",
                      "peak_source": f"SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} sm_max_mhz)"},
-        "roofline_exhaustive": {"achieved": ex_achieved, "frac": ex_achieved / fp32_peak,
-                                "kernel_ms": statistics.median(ex_ms), "sphere_tests": ex_stats["sphere_tests"]},
+        "roofline_exhaustive": ex_out,
         "e2e": {"value": e2e_val, "unit": "motion-checks/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(nq),
                 "api": "mv_validate with pinned host buffers", "ms_median": statistics.median(e2e_ms)},
         "per_query_launch": {"value": pq_rate, "unit": "motion-checks/s", "queries": pq_n,
                              "speedup_batched": value / world / pq_rate},
-        "effort": {"states": stats["states_checked"] / max(1, stats["states_available"]),
-                   "sphere_tests": stats["sphere_tests"] / max(1, stats["sphere_tests_available"])},
+        "effort": {"states": st_step["states_checked"] / max(1, st_step["states_available"]),
+                   "sphere_tests_vs_dense": st_step["sphere_tests"] / max(1, st_step["sphere_tests_available"])},
         "valid_total": f"{nvalid}/{nq}",
         "kernel_ms_mean": kms,
         "gpu_launches": 5 * args.steps,
@@ -419,12 +450,11 @@ def run(args):
         line["configs"] = other_configs(ctx, flush)
     if not args.no_serve:
         line["serving"] = serving(ctx, args.serve_seconds)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     mrv.mrv_graph_destroy(graph)
     ctx.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -233,12 +233,15 @@ int mrv_set_limits(mrv_ctx *ctx, const mrv_limits *limits);
 typedef struct {
   uint64_t states_available; /* sum over queries of (T+1)                    */
   uint64_t states_checked;   /* states whose checks ran                      */
-  uint64_t sphere_tests;     /* sphere-sphere + sphere-box tests executed    */
+  uint64_t sphere_tests;     /* sphere-sphere + sphere-box tests executed,
+                                including frame bounding-sphere tests        */
   uint64_t sphere_tests_available; /* tests of an exhaustive run             */
   uint64_t work_items;       /* persistent-scheduler items                   */
   int32_t n_valid, n_conflicts;
   float device_ms;           /* kernel time of the last call (CUDA events)   */
   uint64_t box_tests;        /* the sphere-box part of sphere_tests           */
+  uint64_t fk_chains;        /* (state, robot) kinematic chains evaluated     */
+  uint64_t spheres_placed;   /* sphere centers computed (states x spheres)    */
 } mrv_stats;
 int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
 

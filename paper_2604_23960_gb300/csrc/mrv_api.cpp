@@ -319,6 +319,8 @@ int mrv_ctx::sync() {
   stats.sphere_tests_available = h_stats[3];
   stats.work_items = h_stats[4];
   stats.box_tests = h_stats[5];
+  stats.fk_chains = h_stats[6];
+  stats.spheres_placed = h_stats[7];
   stats.n_valid = h_counts[0];
   stats.n_conflicts = h_counts[1];
   float ms = 0.f;

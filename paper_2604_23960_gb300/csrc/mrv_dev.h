@@ -121,7 +121,8 @@ struct BatchDev {
   uint32_t *err;
   unsigned long long *stats;         // [0] states checked, [1] tests executed,
                                      // [2] states available, [3] tests available,
-                                     // [4] items, [5] box tests executed
+                                     // [4] items, [5] box tests executed,
+                                     // [6] FK chains, [7] spheres placed
   // tables
   const ModelDev *models;
   int32_t n_models;

@@ -67,7 +67,7 @@ struct TileCtx {
   const float4 *box_lo, *box_hi;
   float env_c2, env_r2, rho2;
   long long pairtests, envtests, boxtests;
-  unsigned long long tests, btests, states;
+  unsigned long long tests, btests, states, chains, placed;
 };
 
 constexpr int kEnvCache = 64;    // obstacle spheres staged per warp (more: read from L1)
@@ -431,7 +431,13 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
     }
   }
   const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-  C.states += nvalid;
+  __syncwarp();
+  if (lane == 0) {
+    C.states += nvalid;
+    C.chains += (unsigned long long)nvalid * C.n;
+    C.placed += (unsigned long long)nvalid * C.M;
+  }
+  __syncwarp();
   if (!C.ffc) {
     bool hit = false;
     if (valid && do_env && C.check_env) {
@@ -466,11 +472,13 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
             else hit |= sph_hit(pa, pb);
           }
         }
-    if (do_env && C.check_env) {
-      C.tests += (unsigned long long)nvalid * (unsigned long long)(C.envtests + C.boxtests);
-      C.btests += (unsigned long long)nvalid * (unsigned long long)C.boxtests;
+    if (lane == 0) {
+      if (do_env && C.check_env) {
+        C.tests += (unsigned long long)nvalid * (unsigned long long)(C.envtests + C.boxtests);
+        C.btests += (unsigned long long)nvalid * (unsigned long long)C.boxtests;
+      }
+      if (do_pairs) C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
     }
-    if (do_pairs) C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
     if (CLR) hit = minclr < 0.f;
     return __any_sync(0xffffffffu, hit) ? 1 : 0;
   }
@@ -484,7 +492,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
           for (int bb = S.off[j]; bb < S.off[j + 1]; ++bb) h |= sph_hit(PA[a * kWarp + lane], PA[bb * kWarp + lane]);
         if (h) first = pair_index(i, j, C.n);
       }
-  C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
+  if (lane == 0) C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
   const unsigned m = __ballot_sync(0xffffffffu, first != 0x7fffffff);
   if (!m) return 0x7fffffff;
   const int l0 = __ffs(m) - 1;
@@ -854,11 +862,19 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
         }
       }
     }
+    if (lane == 0) {   // FK chains of this round (statistics)
+      int ns = 0;
+      for (int j = j0; j < j0 + CS && j < C.spt && slice_state(C, k, j) <= C.T; ++j) ++ns;
+      C.chains += (unsigned long long)(ns * n);
+    }
     __syncwarp();
     for (int j = j0; j < j0 + CS && j < C.spt; ++j) {
       const int t = slice_state(C, k, j);
       if (t > C.T) break;
-      C.states += 1;
+      if (lane == 0) {
+        C.states += 1;
+        C.placed += (unsigned long long)M;
+      }
       // sphere placement relative to the query origin, robot by robot
       float c2 = 0.f, cw2 = 0.f;
       for (int r = 0; r < n; ++r) {
@@ -930,18 +946,20 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
           // combined order (Alg. 1): env + self of every robot, then pairs
           hit = env_mv(C, S, P, K, lane, cw2, eps);
           if (!C.exhaustive && __any_sync(0xffffffffu, hit)) {
-            C.tests += (unsigned long long)(C.envtests + C.boxtests);
-            C.btests += (unsigned long long)C.boxtests;
+            if (lane == 0) {
+              C.tests += (unsigned long long)(C.envtests + C.boxtests);
+              C.btests += (unsigned long long)C.boxtests;
+            }
             return 1;
           }
         }
-        if (need_env) {
+        if (need_env && lane == 0) {
           C.tests += (unsigned long long)(C.envtests + C.boxtests);
           C.btests += (unsigned long long)C.boxtests;
         }
         if (do_pairs) {
           if (!CLR) hit |= pairs_mv(P, K, S.off, n, M, lane, eps);
-          C.tests += (unsigned long long)C.pairtests;
+          if (lane == 0) C.tests += (unsigned long long)C.pairtests;
         }
         if (__any_sync(0xffffffffu, hit)) {
           if (!C.exhaustive) return 1;
@@ -949,7 +967,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
         }
       } else {
         unsigned pm = pairs_ffc(P, K, S.off, n, lane, eps);
-        C.tests += (unsigned long long)C.pairtests;
+        if (lane == 0) C.tests += (unsigned long long)C.pairtests;
         pm = __reduce_or_sync(0xffffffffu, pm);
         if (pm) {
           const int key = t * 32 + (__ffs(pm) - 1);
@@ -987,7 +1005,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     C.box_lo = E.box_lo; C.box_hi = E.box_hi; C.env_c2 = E.c2max; C.env_r2 = E.r2max;
   }
   C.pairtests = Q.pairtests; C.envtests = Q.envtests; C.boxtests = Q.boxtests;
-  C.tests = 0; C.btests = 0; C.states = 0;
+  C.tests = 0; C.btests = 0; C.states = 0; C.chains = 0; C.placed = 0;
   // stage the query's robots; origin of the relative frame = robot 0's base
   const int s0 = B.q_robot_off[q];
   if (lane < C.n) {
@@ -1050,10 +1068,13 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     for (int o = 16; o > 0; o >>= 1) minclr = fminf(minclr, __shfl_xor_sync(0xffffffffu, minclr, o));
     if (lane == 0) atomicMin((int *)&B.q_minclr[q], f2ord(minclr));
   }
+  __syncwarp();
   if (lane == 0) {
     atomicAdd(&B.stats[0], C.states);
     atomicAdd(&B.stats[1], C.tests);
     atomicAdd(&B.stats[5], C.btests);
+    atomicAdd(&B.stats[6], C.chains);
+    atomicAdd(&B.stats[7], C.placed);
   }
   __syncwarp();
 }
