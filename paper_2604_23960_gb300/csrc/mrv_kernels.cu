@@ -45,7 +45,7 @@
 namespace mrv {
 
 constexpr int kFlavorAMaxSpheres = 16;
-constexpr int kSlotWords = 18;                   // words per RobotSlot in shared memory
+constexpr int kSlotWords = 26;                   // words per RobotSlot in shared memory
 constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
 
 struct RobotSlot {           // per-warp staged view of one robot of the query
@@ -55,6 +55,8 @@ struct RobotSlot {           // per-warp staged view of one robot of the query
   const int4 *rects;         // self pairs as rectangles (rows x0..x1, columns y0..y1)
   const ModelDev *md;        // the model (frame ranges, bounding spheres, groups)
   int32_t mdl, m, dof, kind, n_self, w0, w1, n_rects;
+  int32_t n_links, n_groups;
+  int16_t ls[kMaxLinks + 2]; // frame ranges of the sorted spheres (copy of md->link_start)
 };
 static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
@@ -683,7 +685,7 @@ __device__ void link_spheres(const TileCtx &C, WarpSmem &S, const float *xf, int
     const int r = k / kMaxLinks, l = k - r * kMaxLinks;
     const ModelDev &md = *S.rs[r].md;
     float4 o = make_float4(0.f, 0.f, 0.f, -1.f);
-    if (l < md.n_links && md.link_bs[l][3] >= 0.f) {
+    if (l < S.rs[r].n_links && md.link_bs[l][3] >= 0.f) {
       const float *X = xf + ((jj * n + r) * kMaxLinks + l) * 12;
       const float cx = md.link_bs[l][0], cy = md.link_bs[l][1], cz = md.link_bs[l][2];
       o.x = fmaf(X[0], cx, fmaf(X[1], cy, fmaf(X[2], cz, X[3]))) - S.ox;
@@ -708,16 +710,14 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float
     const int i = k / kMaxLinks, u = k - i * kMaxLinks;   // constant divisor
     const float4 bu = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
     if (bu.w >= 0.f) {
-      const ModelDev &mi = *S.rs[i].md;
-      const int a0 = S.off[i] + mi.link_start[u], a1 = S.off[i] + mi.link_start[u + 1];
+      const int a0 = S.off[i] + S.rs[i].ls[u], a1 = S.off[i] + S.rs[i].ls[u + 1];
       for (int k2 = (i + 1) * kMaxLinks; k2 < nk; ++k2) {
         const float4 bv = S.BS[k2];
         if (bv.w < 0.f) continue;
         ntests += 1;
         if (!sph_hit(bu, bv)) continue;
         const int j = k2 / kMaxLinks, v = k2 - j * kMaxLinks;
-        const ModelDev &mj = *S.rs[j].md;
-        const int b0 = S.off[j] + mj.link_start[v], b1 = S.off[j] + mj.link_start[v + 1];
+        const int b0 = S.off[j] + S.rs[j].ls[v], b1 = S.off[j] + S.rs[j].ls[v + 1];
         bool h = false;
         for (int a = a0; a < a1 && !h; ++a) {
           const float4 pa = P[a];
@@ -744,8 +744,7 @@ __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, 
     const float4 bl = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
     if (bl.w < 0.f) continue;
     const int r = k / kMaxLinks, l = k - r * kMaxLinks;
-    const ModelDev &md = *S.rs[r].md;
-    const int a0 = S.off[r] + md.link_start[l], a1 = S.off[r] + md.link_start[l + 1];
+    const int a0 = S.off[r] + S.rs[r].ls[l], a1 = S.off[r] + S.rs[r].ls[l + 1];
     const float4 bw = make_float4(bl.x + S.ox, bl.y + S.oy, bl.z + S.oz, bl.w);
     for (int e = 0; e < C.env_ns; ++e) {
       const float4 es = e < ns_c ? S.ES[e] : __ldg(&C.env_s[e]);
@@ -778,7 +777,7 @@ __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, 
   for (int r = 0; r < C.n; ++r) {
     const ModelDev &md = *S.rs[r].md;
     const int o = S.off[r];
-    const int ng = md.n_groups;
+    const int ng = S.rs[r].n_groups;
     for (int g0 = 0; g0 < ng; g0 += kWarp) {
       const int g = g0 + lane;
       int4 G = make_int4(0, 0, 0, 0);
@@ -882,7 +881,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
         const float4 *sph = S.rs[r].spheres;
         const int32_t *lnk = S.rs[r].links;
         const int m = S.rs[r].m, a0 = S.off[r];
-#pragma unroll 2
+#pragma unroll 4
         for (int kk = lane; kk < m; kk += kWarp) {
           const float4 s = __ldg(&sph[kk]);
           const float *X = Xr + __ldg(&lnk[kk]) * 12;
@@ -1015,6 +1014,9 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects; rs.md = &m;
     rs.mdl = id; rs.m = m.n_spheres; rs.dof = m.dof; rs.kind = m.kind; rs.n_self = m.n_self;
     rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.n_rects = m.n_rects;
+    rs.n_links = m.n_links; rs.n_groups = m.n_groups;
+#pragma unroll
+    for (int l = 0; l < kMaxLinks + 2; ++l) rs.ls[l] = (int16_t)(l <= m.n_links ? m.link_start[l] : m.n_spheres);
     S.rs[lane] = rs;
     if (lane == 0) { S.ox = m.base[3]; S.oy = m.base[7]; S.oz = m.base[11]; }
   }
