@@ -72,6 +72,22 @@ struct TileCtx {
   unsigned long long tests, btests, states, chains, placed;
 };
 
+constexpr int kCand = 64;        // broadphase candidates per list and state
+
+// Candidates of one state found by the bounding-sphere tests, and the frames
+// whose spheres must be placed to resolve them (bit k of need/placed = frame
+// slot k = robot k / kMaxLinks, frame k % kMaxLinks).
+struct Cands {
+  uint32_t pc[kCand];        // robot-robot: frame slot k << 8 | frame slot k2
+  uint32_t ec[kCand];        // frame slot << 24 | obstacle sphere
+  uint32_t bc[kCand];        // frame slot << 24 | obstacle box
+  uint32_t sc[kCand];        // robot << 16 | self-pair group, then robot << 16 | first pair
+  int32_t pf[kCand + 1];     // exclusive prefix of the tests of the list being resolved
+  int32_t np, ne, nb, ns, overflow, pad;
+  uint32_t need[3], placed[3];
+};
+static_assert(sizeof(Cands) <= sizeof(float) * MRV_MAX_QUERY_SPHERES, "candidate lists fit the K array");
+
 constexpr int kEnvCache = 64;    // obstacle spheres staged per warp (more: read from L1)
 constexpr int kBoxCache = 32;    // obstacle boxes staged per warp
 
@@ -84,13 +100,20 @@ struct WarpSmem {
   float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
   float EK[kEnvCache];       // their |c|^2 - r^2
   float4 BL[kBoxCache], BH[kBoxCache];   // obstacle boxes
+  // robot pairs i < j of the query (i << 4 | j) and the exclusive prefix of
+  // their frame-pair counts n_links_i x n_links_j
+  uint8_t rp[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2];
+  int16_t rpf[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2 + 2];
   float4 BS[MRV_MAX_ROBOTS * kMaxLinks];  // per (robot, frame) bounding sphere at the
                                           // current state (center relative to o; w < 0: none)
   union {
     struct {
       float xf[kFkChains * kMaxLinks * 12];   // link frames of one FK round
       float4 P[MRV_MAX_QUERY_SPHERES];         // centers relative to o, radius
-      float K[MRV_MAX_QUERY_SPHERES];          // |p|^2 - r^2
+      union {
+        float K[MRV_MAX_QUERY_SPHERES];        // dense path: |p|^2 - r^2
+        Cands cl;                              // broadphase: candidate lists
+      };
     } b;
     float4 PA[kFlavorAMaxSpheres * kWarp];     // flavor A: world centers per lane
   } u;
@@ -803,10 +826,328 @@ __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, 
   return hit;
 }
 
+// --- candidate-list broadphase with lazy sphere placement -------------------
+//
+// Per state: the frames' bounding spheres are tested against the obstacles,
+// each other (self-pair groups) and the other robots' frames; overlaps go to
+// per-warp candidate lists and mark the frames involved.  Only those frames'
+// spheres are placed, and the exact tests of the lists are spread over the
+// lanes as one flat index space (candidate x sphere).  A list that overflows
+// sends its phase to the in-lane path with every sphere placed.
+
+struct BroadAcc {            // per-lane statistics of a slice
+  uint32_t tests, boxes, placed;
+};
+
+__device__ __forceinline__ void push_cand(uint32_t *list, int32_t *count, int32_t *overflow, uint32_t v) {
+  const int i = atomicAdd(count, 1);
+  if (i < kCand) list[i] = v;
+  else *overflow = 1;
+}
+
+// frame slot k with an obstacle index e; indices past 24 bits go to the
+// in-lane path through the overflow flag
+__device__ __forceinline__ void push_obst(uint32_t *list, int32_t *count, int32_t *overflow, int k, int e) {
+  if (e > 0xffffff) *overflow = 1;
+  else push_cand(list, count, overflow, ((uint32_t)k << 24) | (uint32_t)e);
+}
+
+__device__ __forceinline__ void need_frame(Cands &cl, int k) { atomicOr(&cl.need[k >> 5], 1u << (k & 31)); }
+
+// Exclusive prefix of the per-item test counts c (lane i0 + lane holds item
+// i0 + lane's) into pf, called for i0 = 0, 32, ...; returns the new base.
+__device__ __forceinline__ int scan_chunk(int32_t *pf, int i, int n, int c, int base, int lane) {
+  int x = c;
+#pragma unroll
+  for (int d = 1; d < kWarp; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (i < n) pf[i] = base + x - c;
+  return base + __shfl_sync(0xffffffffu, x, kWarp - 1);
+}
+
+__device__ __forceinline__ int frame_count(const WarpSmem &S, int k) {
+  const int r = k / kMaxLinks, l = k - r * kMaxLinks;
+  return S.rs[r].ls[l + 1] - S.rs[r].ls[l];
+}
+
+__device__ __forceinline__ int frame_first(const WarpSmem &S, int k) {
+  const int r = k / kMaxLinks, l = k - r * kMaxLinks;
+  return S.off[r] + S.rs[r].ls[l];
+}
+
+// prefix of spheres-per-frame over a list of frame-slot << 24 entries
+__device__ int scan_frames(Cands &cl, const uint32_t *list, int n, const WarpSmem &S, int lane) {
+  int base = 0;
+  for (int i0 = 0; i0 < n; i0 += kWarp) {
+    const int i = i0 + lane;
+    const int c = i < n ? frame_count(S, (int)(list[i] >> 24)) : 0;
+    base = scan_chunk(cl.pf, i, n, c, base, lane);
+  }
+  if (lane == 0) cl.pf[n] = base;
+  __syncwarp();
+  return base;
+}
+
+// places the spheres of the frames marked in cl.need and not placed yet
+__device__ void place_needed(const TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane, BroadAcc &acc) {
+  Cands &cl = S.u.b.cl;
+  const uint32_t w0 = cl.need[0] & ~cl.placed[0], w1 = cl.need[1] & ~cl.placed[1], w2 = cl.need[2] & ~cl.placed[2];
+  if (!(w0 | w1 | w2)) return;
+  float4 *P = S.u.b.P;
+  const int n = C.n;
+  for (int r = 0; r < n; ++r) {
+    const int k0 = r * kMaxLinks, wd = k0 >> 5, sh = k0 & 31;
+    const uint32_t lo = wd == 0 ? w0 : (wd == 1 ? w1 : w2);
+    const uint32_t hi = wd == 0 ? w1 : (wd == 1 ? w2 : 0u);
+    const uint32_t mr = (uint32_t)((((unsigned long long)hi << 32) | lo) >> sh) & ((1u << kMaxLinks) - 1u);
+    if (!mr) continue;
+    const float *Xr = xf + (jj * n + r) * (kMaxLinks * 12);
+    const float4 *sph = S.rs[r].spheres;
+    const int32_t *lnk = S.rs[r].links;
+    const int a0 = S.off[r];
+    // spheres are sorted by frame: walk from the first to the last frame to place
+    const int s0 = S.rs[r].ls[__ffs(mr) - 1], s1 = S.rs[r].ls[32 - __clz(mr)];
+    for (int kk = s0 + lane; kk < s1; kk += kWarp) {
+      const int l = __ldg(&lnk[kk]);
+      if (!((mr >> l) & 1u)) continue;
+      const float4 sp = __ldg(&sph[kk]);
+      const float *X = Xr + l * 12;
+      const float wx = fmaf(X[0], sp.x, fmaf(X[1], sp.y, fmaf(X[2], sp.z, X[3])));
+      const float wy = fmaf(X[4], sp.x, fmaf(X[5], sp.y, fmaf(X[6], sp.z, X[7])));
+      const float wz = fmaf(X[8], sp.x, fmaf(X[9], sp.y, fmaf(X[10], sp.z, X[11])));
+      P[a0 + kk] = make_float4(wx - S.ox, wy - S.oy, wz - S.oz, sp.w);
+      acc.placed += 1;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    cl.placed[0] |= w0;
+    cl.placed[1] |= w1;
+    cl.placed[2] |= w2;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void need_all(Cands &cl, int lane) {
+  if (lane == 0) cl.need[0] = cl.need[1] = cl.need[2] = 0xffffffffu;
+  __syncwarp();
+}
+
+// One state of the broadphase path: MV -> 1 on a collision, FFC -> the
+// bitmask of colliding robot pairs.
+__device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane, bool need_env,
+                                bool do_pairs, BroadAcc &acc) {
+  Cands &cl = S.u.b.cl;
+  const float4 *P = S.u.b.P;
+  const int n = C.n, nk = n * kMaxLinks;
+  if (lane == 0) {
+    cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = 0;
+    cl.need[0] = cl.need[1] = cl.need[2] = 0;
+    cl.placed[0] = cl.placed[1] = cl.placed[2] = 0;
+  }
+  __syncwarp();
+  bool hit = false;
+  if (need_env) {
+    // frames x obstacles, lane = (frame group lane & 3, obstacle group lane >> 2)
+    const int fg = lane & 3, og = lane >> 2;
+    const int ns_c = min(C.env_ns, kEnvCache), nb_c = min(C.env_nb, kBoxCache);
+    for (int k = fg; k < nk; k += 4) {
+      const float4 bl = S.BS[k];
+      if (bl.w < 0.f) continue;
+      const float4 bw = make_float4(bl.x + S.ox, bl.y + S.oy, bl.z + S.oz, bl.w);
+      bool nd = false;
+      for (int e = og; e < C.env_ns; e += 8) {
+        const float4 es = e < ns_c ? S.ES[e] : __ldg(&C.env_s[e]);
+        acc.tests += 1;
+        if (sph_hit(bw, es)) {
+          push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
+          nd = true;
+        }
+      }
+      const float rr = bw.w * bw.w;
+      for (int b = og; b < C.env_nb; b += 8) {
+        const float4 lo = b < nb_c ? S.BL[b] : __ldg(&C.box_lo[b]);
+        const float4 hi = b < nb_c ? S.BH[b] : __ldg(&C.box_hi[b]);
+        acc.tests += 1;
+        acc.boxes += 1;
+        if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
+          push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
+          nd = true;
+        }
+      }
+      if (nd) need_frame(cl, k);
+    }
+    // self-pair groups by their frames' bounding spheres
+    for (int r = 0; r < n; ++r) {
+      const ModelDev &md = *S.rs[r].md;
+      for (int g = lane; g < S.rs[r].n_groups; g += kWarp) {
+        const int4 G = __ldg(&md.self_groups[g]);
+        acc.tests += 1;
+        if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
+          push_cand(cl.sc, &cl.ns, &cl.overflow, ((uint32_t)r << 16) | (uint32_t)g);
+          need_frame(cl, r * kMaxLinks + G.x);
+          need_frame(cl, r * kMaxLinks + G.y);
+        }
+      }
+    }
+    __syncwarp();
+    if (cl.overflow) {   // too many candidates: resolve this phase in the lanes
+      need_all(cl, lane);
+      place_needed(C, S, xf, jj, lane, acc);
+      unsigned long long t = 0, bx = 0;
+      hit = env_broad(C, S, P, lane, t, bx);
+      acc.tests += (uint32_t)t;
+      acc.boxes += (uint32_t)bx;
+    } else {
+      place_needed(C, S, xf, jj, lane, acc);
+      const int ne = cl.ne, nbx = cl.nb, ns = cl.ns;
+      if (ne) {
+        const int tot = scan_frames(cl, cl.ec, ne, S, lane);
+        int it = 0;
+        for (int f = lane; f < tot; f += kWarp) {
+          while (cl.pf[it + 1] <= f) ++it;
+          const uint32_t v = cl.ec[it];
+          const int e = (int)(v & 0xffffffu);
+          const float4 es = e < kEnvCache ? S.ES[e] : __ldg(&C.env_s[e]);
+          const float4 p = P[frame_first(S, (int)(v >> 24)) + f - cl.pf[it]];
+          hit |= sph_hit(make_float4(p.x + S.ox, p.y + S.oy, p.z + S.oz, p.w), es);
+        }
+        acc.tests += (uint32_t)((tot - lane + kWarp - 1) / kWarp);
+        __syncwarp();
+      }
+      if (nbx) {
+        const int tot = scan_frames(cl, cl.bc, nbx, S, lane);
+        int it = 0;
+        for (int f = lane; f < tot; f += kWarp) {
+          while (cl.pf[it + 1] <= f) ++it;
+          const uint32_t v = cl.bc[it];
+          const int b = (int)(v & 0xffffffu);
+          const float4 lo = b < kBoxCache ? S.BL[b] : __ldg(&C.box_lo[b]);
+          const float4 hi = b < kBoxCache ? S.BH[b] : __ldg(&C.box_hi[b]);
+          const float4 p = P[frame_first(S, (int)(v >> 24)) + f - cl.pf[it]];
+          hit |= box_d2(p.x + S.ox, p.y + S.oy, p.z + S.oz, lo, hi) < p.w * p.w;
+        }
+        const uint32_t c = (uint32_t)((tot - lane + kWarp - 1) / kWarp);
+        acc.tests += c;
+        acc.boxes += c;
+        __syncwarp();
+      }
+      if (ns) {
+        // self pairs of the overlapping groups as one flat range
+        int base = 0;
+        for (int i0 = 0; i0 < ns; i0 += kWarp) {
+          const int i = i0 + lane;
+          int c = 0;
+          if (i < ns) {
+            const uint32_t v = cl.sc[i];
+            const int r = (int)(v >> 16);
+            const int4 G = __ldg(&S.rs[r].md->self_groups[v & 0xffffu]);
+            c = G.w;
+            cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)G.z;
+          }
+          base = scan_chunk(cl.pf, i, ns, c, base, lane);
+        }
+        if (lane == 0) cl.pf[ns] = base;
+        __syncwarp();
+        int it = 0;
+        for (int f = lane; f < base; f += kWarp) {
+          while (cl.pf[it + 1] <= f) ++it;
+          const uint32_t v = cl.sc[it];
+          const int r = (int)(v >> 16), o = S.off[r];
+          const uint32_t e = __ldg(&S.rs[r].self[(v & 0xffffu) + (uint32_t)(f - cl.pf[it])]);
+          hit |= sph_hit(P[o + (int)(e & 0xffffu)], P[o + (int)(e >> 16)]);
+        }
+        acc.tests += (uint32_t)((base - lane + kWarp - 1) / kWarp);
+        __syncwarp();
+      }
+    }
+    if (__any_sync(0xffffffffu, hit) && !C.exhaustive) return 1u;
+  }
+  if (!do_pairs) return __any_sync(0xffffffffu, hit) ? 1u : 0u;
+  // robot-robot: every (robot pair, frame pair) as one flat range
+  if (lane == 0) {
+    cl.np = 0;
+    cl.overflow = 0;
+  }
+  __syncwarp();
+  const int npair = n * (n - 1) / 2;
+  const int ftot = S.rpf[npair];
+  {
+    int it = 0;
+    for (int f = lane; f < ftot; f += kWarp) {
+      while (S.rpf[it + 1] <= f) ++it;
+      const int i = S.rp[it] >> 4, j = S.rp[it] & 15;
+      const int nj = S.rs[j].n_links, g = f - S.rpf[it];
+      const int u = (int)(((float)g + 0.5f) * __frcp_rn((float)nj));   // g < 100: exact
+      const int v = g - u * nj;
+      const int k = i * kMaxLinks + u, k2 = j * kMaxLinks + v;
+      const float4 bu = S.BS[k], bv = S.BS[k2];
+      if (bu.w < 0.f || bv.w < 0.f) continue;
+      acc.tests += 1;
+      if (sph_hit(bu, bv)) {
+        push_cand(cl.pc, &cl.np, &cl.overflow, ((uint32_t)k << 8) | (uint32_t)k2);
+        need_frame(cl, k);
+        need_frame(cl, k2);
+      }
+    }
+  }
+  __syncwarp();
+  unsigned pm = 0;
+  const int np = cl.np;
+  if (cl.overflow) {
+    need_all(cl, lane);
+    place_needed(C, S, xf, jj, lane, acc);
+    unsigned long long t = 0;
+    pm = pairs_broad(C, S, P, lane, C.ffc != 0, t);
+    acc.tests += (uint32_t)t;
+  } else if (np > 0) {
+    place_needed(C, S, xf, jj, lane, acc);
+    // lanes take (candidate, sphere of frame k) and test it against frame k2
+    int base = 0;
+    for (int i0 = 0; i0 < np; i0 += kWarp) {
+      const int i = i0 + lane;
+      const int c = i < np ? frame_count(S, (int)(cl.pc[i] >> 8)) : 0;
+      base = scan_chunk(cl.pf, i, np, c, base, lane);
+    }
+    if (lane == 0) cl.pf[np] = base;
+    __syncwarp();
+    int it = 0;
+    for (int f = lane; f < base; f += kWarp) {
+      while (cl.pf[it + 1] <= f) ++it;
+      const uint32_t v = cl.pc[it];
+      const int k = (int)(v >> 8), k2 = (int)(v & 0xffu);
+      const float4 pa = P[frame_first(S, k) + f - cl.pf[it]];
+      const int b0 = frame_first(S, k2), b1 = b0 + frame_count(S, k2);
+      bool h = false;
+      for (int b = b0; b < b1; ++b) h |= sph_hit(pa, P[b]);
+      acc.tests += (uint32_t)(b1 - b0);
+      if (h) pm |= C.ffc ? (1u << pair_index(k / kMaxLinks, k2 / kMaxLinks, n)) : 1u;
+    }
+  }
+  if (C.ffc) return __reduce_or_sync(0xffffffffu, pm);
+  return __any_sync(0xffffffffu, hit || pm != 0) ? 1u : 0u;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// adds a slice's per-lane broadphase statistics to the work item's
+__device__ __forceinline__ void flush_acc(TileCtx &C, BroadAcc &acc, int lane) {
+  const unsigned long long t = warp_sum((unsigned long long)acc.tests);
+  const unsigned long long b = warp_sum((unsigned long long)acc.boxes);
+  const unsigned long long p = warp_sum((unsigned long long)acc.placed);
+  if (lane == 0) {
+    C.tests += t;
+    C.btests += b;
+    C.placed += p;
+  }
+  __syncwarp();
+  acc.tests = acc.boxes = acc.placed = 0u;
 }
 
 // clearance mode (exhaustive MV with min_clearance_out): direct formulas
@@ -846,6 +1187,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   float *K = S.u.b.K;
   const bool need_env = do_env && C.check_env;
   int found = C.ffc ? 0x7fffffff : 0;
+  BroadAcc acc = {0u, 0u, 0u};
   for (int j0 = 0; j0 < C.spt; j0 += CS) {
     if (slice_state(C, k, j0) > C.T) break;   // states grow with j in both packings
     // (state, robot) chains
@@ -870,10 +1212,33 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
     for (int j = j0; j < j0 + CS && j < C.spt; ++j) {
       const int t = slice_state(C, k, j);
       if (t > C.T) break;
-      if (lane == 0) {
-        C.states += 1;
-        C.placed += (unsigned long long)M;
+      if (lane == 0) C.states += 1;
+      if (!CLR && C.broad) {
+        // frame-level broadphase; spheres are placed only for the frames whose
+        // bounding spheres overlap something, then resolved exactly
+        link_spheres(C, S, xf, j - j0, lane);
+        __syncwarp();
+        const unsigned res = broad_state(C, S, xf, j - j0, lane, need_env, do_pairs, acc);
+        __syncwarp();
+        if (res) {
+          if (!C.ffc) {
+            if (!C.exhaustive) {
+              flush_acc(C, acc, lane);
+              return 1;
+            }
+            found = 1;
+          } else {
+            const int key = t * 32 + (__ffs(res) - 1);
+            if (!C.exhaustive) {
+              flush_acc(C, acc, lane);
+              return key;
+            }
+            if (key < found) found = key;
+          }
+        }
+        continue;
       }
+      if (lane == 0) C.placed += (unsigned long long)M;
       // sphere placement relative to the query origin, robot by robot
       float c2 = 0.f, cw2 = 0.f;
       for (int r = 0; r < n; ++r) {
@@ -900,42 +1265,6 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
       if (need_env) cw2 = warp_max(cw2);
       __syncwarp();
       const float eps = kEpsU * (c2 + C.rho2);
-      if (!CLR && C.broad) {
-        // frame-level broadphase, then exact tests of the overlapping frames
-        link_spheres(C, S, xf, j - j0, lane);
-        __syncwarp();
-        unsigned long long nt = 0, nbx = 0;
-        int res = 0;
-        if (!C.ffc) {
-          bool hit = false;
-          if (need_env) hit = env_broad(C, S, P, lane, nt, nbx);
-          // warp-uniform decision before the pair phase (it votes inside)
-          const bool env_hit = __any_sync(0xffffffffu, hit);
-          if (do_pairs && !(env_hit && !C.exhaustive)) hit |= pairs_broad(C, S, P, lane, false, nt) != 0;
-          res = __any_sync(0xffffffffu, hit);
-        } else {
-          res = (int)__reduce_or_sync(0xffffffffu, pairs_broad(C, S, P, lane, true, nt));
-        }
-        nt = warp_sum(nt);
-        nbx = warp_sum(nbx);
-        if (lane == 0) {
-          C.tests += nt;
-          C.btests += nbx;
-        }
-        __syncwarp();
-        if (res) {
-          if (!C.ffc) {
-            if (!C.exhaustive) return 1;
-            found = 1;
-          } else {
-            const int key = t * 32 + (__ffs((unsigned)res) - 1);
-            if (!C.exhaustive) return key;
-            if (key < found) found = key;
-          }
-        }
-        __syncwarp();
-        continue;
-      }
       if (!C.ffc) {
         bool hit = false;
         if (CLR) {
@@ -978,6 +1307,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
     }
     __syncwarp();
   }
+  if (!CLR && C.broad) flush_acc(C, acc, lane);
   return found;
 }
 
@@ -988,6 +1318,14 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
 template <bool CLR>
 __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane) {
   const QueryDev Q = B.q[q];
+  if (!(B.flags & MRV_EXHAUSTIVE)) {
+    // a verdict reached since the item was claimed: skip the staging too
+    int stop = 0;
+    if (lane == 0)
+      stop = !(Q.bits & 1u) ? *(volatile int *)&B.q_hit[q] != 0
+                            : *(volatile int *)&B.q_best[q] < c * Q.cte * Q.spt * 32;
+    if (__shfl_sync(0xffffffffu, stop, 0)) return;
+  }
   TileCtx &C = S.ctx;   // kept in shared memory: read where used, not held in registers
   __syncwarp();
   C.q = q; C.T = Q.T; C.n = Q.n; C.M = Q.M; C.nb = Q.ntiles;
@@ -1025,6 +1363,15 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     int acc = 0;
     S.off[0] = 0;
     for (int r = 0; r < C.n; ++r) { acc += S.rs[r].m; S.off[r + 1] = acc; }
+    int p = 0, f = 0;
+    for (int i = 0; i < C.n; ++i)
+      for (int j = i + 1; j < C.n; ++j) {
+        S.rp[p] = (uint8_t)(i << 4 | j);
+        S.rpf[p] = (int16_t)f;
+        f += S.rs[i].n_links * S.rs[j].n_links;
+        ++p;
+      }
+    S.rpf[p] = (int16_t)f;
   }
   if (C.check_env && !(Q.bits & 2u)) {
     for (int o = lane; o < min(C.env_ns, kEnvCache); o += kWarp) {
@@ -1099,12 +1446,20 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
     return;
   }
   const int n_items = B.counters[1];
+  const bool skip_dead = !(B.flags & MRV_EXHAUSTIVE);
   unsigned long long items = 0;
+  // Items are claimed g at a time.  Lane l < g resolves item base + l (level,
+  // query) and whether its query already has a verdict: items are ordered by
+  // level, so an item claimed after its query's verdict is past it (MV: any
+  // collision ends the query; FFC: the conflict lies at a lower level).  g
+  // doubles while whole claims are settled and drops back to 1 at live work,
+  // so live items are still spread one per claim.
+  int g = 1;
   for (;;) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(&B.counters[0], 1);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= n_items) break;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&B.counters[0], g);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_items) break;
     int halt = 0;
     if (lane == 0) {
       if (*(volatile int *)&B.counters[2]) halt = 1;
@@ -1112,15 +1467,30 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
       if (halt) atomicOr(B.err, halt == 1 ? kErrAbort : kErrTimeout);
     }
     if (__shfl_sync(0xffffffffu, halt, 0)) break;
-    int lo = 0, hi = kMaxLevels - 1;   // level: last c with level_start[c] <= idx
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (B.level_start[mid] <= idx) lo = mid;
-      else hi = mid - 1;
+    const int idx = base + lane;
+    int q = 0, lvl = 0;
+    bool live = false;
+    if (lane < g && idx < n_items) {
+      int lo = 0, hi = kMaxLevels - 1;   // level: last c with level_start[c] <= idx
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&B.level_start[mid]) <= idx) lo = mid;
+        else hi = mid - 1;
+      }
+      lvl = lo;
+      q = __ldg(&B.sorted[idx - __ldg(&B.level_start[lo])]);
+      live = !skip_dead ||
+             (*(volatile int *)&B.q_hit[q] == 0 && *(volatile int *)&B.q_best[q] == 0x7fffffff);
     }
-    const int q = B.sorted[idx - B.level_start[lo]];
-    run_chunk<CLR>(B, S, q, lo, lane);
-    ++items;
+    unsigned live_mask = __ballot_sync(0xffffffffu, live);
+    g = live_mask ? 1 : min(2 * g, kWarp);
+    while (live_mask) {
+      const int src = __ffs(live_mask) - 1;
+      live_mask &= live_mask - 1;
+      const int qq = __shfl_sync(0xffffffffu, q, src), ll = __shfl_sync(0xffffffffu, lvl, src);
+      run_chunk<CLR>(B, S, qq, ll, lane);
+      ++items;
+    }
   }
   if (lane == 0 && items) atomicAdd(&B.stats[4], items);
 }
