@@ -173,6 +173,21 @@ def serving(ctx, duration_s=6.0, loads=(0.5, 0.8, 0.95), n_clients=64, seed=206)
     return out
 
 
+def autotune(ctx, w, flags, kind=None, n_sample=None):
+    """Picks the scheduler tuning for a batch class (untimed setup): the
+    library's autotuner times its candidates on the first n_sample queries."""
+    import torch
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import workloads as W
+    sub = w if n_sample is None or n_sample >= w.batch.n_queries else W.subset(w, np.arange(n_sample))
+    bs = ctx.bind(sub, ctx.robot_ids, ctx.env_ids).to("cuda")
+    if kind is not None:
+        bs.a["q_kind"] = torch.full((sub.batch.n_queries,), kind, dtype=torch.uint8, device="cuda")
+    t = mrv.mrv_autotune(ctx.h, bs.struct(flags, with_kind=True))
+    torch.cuda.synchronize()
+    return t
+
+
 def other_configs(ctx, flush, per_query_n=1000, reps=3):
     """Throughput of the other workload configurations (device-resident
     inputs, batched persistent launch; the ragged batch replays a CUDA graph)
@@ -216,16 +231,18 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
     # four arms, 100k timed path-sets: FFC
     w = W.make_cage_ffc(100000)
     ba = ctx.bind(w).to("cuda")
+    tune = autotune(ctx, w, 0, kind=1, n_sample=20000)
     dt = timed(lambda: ctx.ffc_find(ba))
     st = ctx.stats()
     pq = per_query(w, lambda b: ctx.ffc_find(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
     out["cage_ffc_100k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                            "kernel_ms": st["device_ms"]}
+                            "kernel_ms": st["device_ms"], "tuning": tune}
     # ragged teams, 1M mixed MV/FFC queries in one persistent graph launch
     w = W.make_ragged_teams(1_000_000)
     ba = ctx.bind(w).to("cuda")
+    tune = autotune(ctx, w, mrv.MRV_CHECK_ENV, n_sample=100000)
     nq = w.batch.n_queries
     valid = torch.empty(nq, dtype=torch.uint8, device="cuda")
     conf = torch.empty((nq, 3), dtype=torch.int32, device="cuda")
@@ -240,7 +257,7 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
     pq = per_query(w, lambda b: ctx.run(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
     out["ragged_teams_1m"] = {"value": nq / dt, "per_query_launch": pq, "speedup": nq / dt / pq, "ms": dt * 1e3,
                               "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                              "kernel_ms": st["device_ms"]}
+                              "kernel_ms": st["device_ms"], "tuning": tune}
     return out
 
 
@@ -318,6 +335,9 @@ def run(args):
     kind = torch.zeros(nq, dtype=torch.uint8, device=dev)       # every query is MV
     ba.a["q_kind"] = kind
     bs = ba.struct(mrv.MRV_CHECK_ENV, with_kind=True)
+    # scheduler tuning for this batch class (untimed setup; the graph keeps it)
+    mrv.mrv_autotune(ctx.h, bs)
+    torch.cuda.synchronize()
     graph = mrv.mrv_graph_create(ctx.h, bs, valid, conf)
 
     def step():

@@ -253,7 +253,7 @@ typedef struct {
   int32_t slices_per_item;   /* slices per work item (>= 1)                  */
   int32_t warps_per_block;   /* 1..12 (17 KB of shared memory per warp)      */
   int32_t blocks_per_sm;     /* 0 = as many as fit                           */
-  int32_t tile_split;        /* 1, 2, 4 or 8 slices per 32-state tile for
+  int32_t tile_split;        /* 1, 2, 4, 8, 16 or 32 slices per 32-state tile for
                                 kinematic-chain queries (point-robot queries
                                 always use whole tiles)                      */
 } mrv_tuning;

@@ -253,6 +253,7 @@ int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *
 
 int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
                    mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+  cudaGetLastError();   // the launch checks below report this sequence's errors only
   cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
@@ -666,6 +667,33 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
   h.dev.sphere_k = (const float *)h.d_k;
   h.dev.box_lo = (const float4 *)h.d_lo;
   h.dev.box_hi = (const float4 *)h.d_hi;
+  // obstacle grid for frames up to the largest frame bounding radius of the
+  // robot models uploaded so far (0.3 m without any); larger frames of
+  // models uploaded later scan every obstacle
+  float R = 0.f;
+  for (const HostModel &m : c->models)
+    if (m.dev.live)
+      for (int l = 0; l < m.dev.n_links; ++l) R = std::max(R, m.dev.link_bs[l][3]);
+  if (!(R > 0.f)) R = 0.3f;
+  const ObstacleGrid G = build_obstacle_grid(d->n_spheres, d->spheres_xyzr, d->n_aabbs, d->aabb_lohi, (double)R);
+  h.dev.g_R = -1.f;
+  if (G.R > 0) {
+    if ((rc = upload(&h.d_goff, G.off.data(), sizeof(int32_t) * G.off.size())) ||
+        (rc = upload(&h.d_gns, G.ns.data(), sizeof(uint16_t) * G.ns.size())) ||
+        (rc = upload(&h.d_gitems, G.items.data(), sizeof(uint16_t) * std::max<size_t>(1, G.items.size())))) {
+      h.free_all();
+      return rc;
+    }
+    for (int a = 0; a < 3; ++a) {
+      h.dev.g_lo[a] = (float)G.lo[a];
+      h.dev.g_dims[a] = G.dims[a];
+    }
+    h.dev.g_inv_h = (float)(1.0 / G.h);
+    h.dev.g_R = R;
+    h.dev.g_off = (const int32_t *)h.d_goff;
+    h.dev.g_ns = (const uint16_t *)h.d_gns;
+    h.dev.g_items = (const uint16_t *)h.d_gitems;
+  }
   h.refs = 1;
   c->envs.push_back(h);
   if ((rc = c->push_tables())) {
@@ -752,8 +780,8 @@ int mrv_set_tuning(mrv_ctx *c, const mrv_tuning *t) {
   if (t->slices_per_item < 1 || t->slices_per_item > 4096) return fail(MRV_ERR_ARG, "slices_per_item outside 1..4096");
   if (t->warps_per_block < 1 || t->warps_per_block > 12) return fail(MRV_ERR_ARG, "warps_per_block outside 1..12");
   if (t->blocks_per_sm < 0) return fail(MRV_ERR_ARG, "blocks_per_sm < 0");
-  if (t->tile_split != 1 && t->tile_split != 2 && t->tile_split != 4 && t->tile_split != 8)
-    return fail(MRV_ERR_ARG, "tile_split must be 1, 2, 4 or 8");
+  if (t->tile_split < 1 || t->tile_split > 32 || (t->tile_split & (t->tile_split - 1)))
+    return fail(MRV_ERR_ARG, "tile_split must be 1, 2, 4, 8, 16 or 32");
   c->tuning = *t;
   return MRV_OK;
 }

@@ -68,6 +68,16 @@ struct EnvDev {
   const float *sphere_k;         // |center|^2 - radius^2 per obstacle sphere
   const float4 *box_lo;          // n_aabbs: lo xyz (w unused)
   const float4 *box_hi;          // n_aabbs: hi xyz (w unused)
+  // uniform grid over the obstacles for frame bounding spheres of radius
+  // <= g_R (g_R < 0: none): cell (ix, iy, iz) of a center x is
+  // floor((x - g_lo) * g_inv_h) per axis; outside 0..g_dims-1 it overlaps no
+  // obstacle.  Cell c = (iz * g_dims[1] + iy) * g_dims[0] + ix lists
+  // g_ns[c] obstacle spheres, then boxes, at g_items[g_off[c] .. g_off[c+1]).
+  float g_lo[3], g_inv_h, g_R;
+  int32_t g_dims[3];
+  const int32_t *g_off;
+  const uint16_t *g_ns;
+  const uint16_t *g_items;
 };
 
 // per-query derived record (written by the preparation kernel)

@@ -93,4 +93,124 @@ PreparedModel prepare_model(int n_links, int m, const int32_t *link, const float
   return P;
 }
 
+// distance from a point to a box (0 inside), double
+static double point_box(const double *x, const double *lo, const double *hi) {
+  double d2 = 0;
+  for (int a = 0; a < 3; ++a) {
+    const double e = x[a] < lo[a] ? lo[a] - x[a] : (x[a] > hi[a] ? x[a] - hi[a] : 0.0);
+    d2 += e * e;
+  }
+  return std::sqrt(d2);
+}
+
+// distance between two boxes (0 when they overlap), double
+static double box_box(const double *alo, const double *ahi, const double *blo, const double *bhi) {
+  double d2 = 0;
+  for (int a = 0; a < 3; ++a) {
+    const double e = blo[a] > ahi[a] ? blo[a] - ahi[a] : (alo[a] > bhi[a] ? alo[a] - bhi[a] : 0.0);
+    d2 += e * e;
+  }
+  return std::sqrt(d2);
+}
+
+ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, const float *lohi, double R,
+                                 int64_t max_items) {
+  ObstacleGrid G;
+  if (!(R > 0) || n_spheres + n_boxes == 0 || n_spheres > 65535 || n_boxes > 65535) return G;
+  // bounding box of the obstacles
+  double blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = 0; i < n_spheres; ++i)
+    for (int a = 0; a < 3; ++a) {
+      blo[a] = std::min(blo[a], (double)xyzr[4 * i + a] - xyzr[4 * i + 3]);
+      bhi[a] = std::max(bhi[a], (double)xyzr[4 * i + a] + xyzr[4 * i + 3]);
+    }
+  for (int i = 0; i < n_boxes; ++i)
+    for (int a = 0; a < 3; ++a) {
+      blo[a] = std::min(blo[a], (double)lohi[6 * i + a]);
+      bhi[a] = std::max(bhi[a], (double)lohi[6 * i + 3 + a]);
+    }
+  double scale = 1.0;
+  for (int a = 0; a < 3; ++a) scale = std::max(scale, std::max(std::fabs(blo[a]), std::fabs(bhi[a])));
+  // cell size first guess: R / 2, at most 64 cells per axis
+  double ext[3], h = R / 2;
+  for (int a = 0; a < 3; ++a) {
+    ext[a] = bhi[a] - blo[a] + 2 * (R * (1 + 1e-3) + 1e-6 * scale) + 1e-6 * scale;
+    h = std::max(h, ext[a] / 64);
+  }
+  const double slack = 1e-3 * h + 1e-6 * scale;
+  // grow the margin by the slack of the final cell size
+  for (int a = 0; a < 3; ++a) {
+    const double m = R + 2 * slack;
+    G.lo[a] = blo[a] - m;
+    ext[a] = bhi[a] - blo[a] + 2 * m;
+    G.dims[a] = std::max(1, std::min(64, (int)std::ceil(ext[a] / h)));
+    h = std::max(h, ext[a] / G.dims[a]);
+  }
+  G.h = h;
+  const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
+  const int64_t ncells = (int64_t)nx * ny * nz;
+  auto cell_range = [&](const double *lo, const double *hi, int *i0, int *i1) {
+    for (int a = 0; a < 3; ++a) {
+      i0[a] = std::max(0, (int)std::floor((lo[a] - G.lo[a]) / h) - 1);
+      i1[a] = std::min(G.dims[a] - 1, (int)std::floor((hi[a] - G.lo[a]) / h) + 1);
+    }
+  };
+  // visit(c, kind, id) for every (cell, obstacle) within reach
+  auto each = [&](auto &&visit) {
+    for (int i = 0; i < n_spheres; ++i) {
+      const double c[3] = {xyzr[4 * i], xyzr[4 * i + 1], xyzr[4 * i + 2]};
+      const double reach = R + xyzr[4 * i + 3] + slack;
+      const double lo[3] = {c[0] - reach, c[1] - reach, c[2] - reach}, hi[3] = {c[0] + reach, c[1] + reach, c[2] + reach};
+      int i0[3], i1[3];
+      cell_range(lo, hi, i0, i1);
+      for (int z = i0[2]; z <= i1[2]; ++z)
+        for (int y = i0[1]; y <= i1[1]; ++y)
+          for (int x = i0[0]; x <= i1[0]; ++x) {
+            const double clo[3] = {G.lo[0] + x * h, G.lo[1] + y * h, G.lo[2] + z * h};
+            const double chi[3] = {clo[0] + h, clo[1] + h, clo[2] + h};
+            if (point_box(c, clo, chi) < reach) visit(((int64_t)z * ny + y) * nx + x, 0, i);
+          }
+    }
+    for (int i = 0; i < n_boxes; ++i) {
+      const double reach = R + slack;
+      const double olo[3] = {lohi[6 * i], lohi[6 * i + 1], lohi[6 * i + 2]};
+      const double ohi[3] = {lohi[6 * i + 3], lohi[6 * i + 4], lohi[6 * i + 5]};
+      const double lo[3] = {olo[0] - reach, olo[1] - reach, olo[2] - reach};
+      const double hi[3] = {ohi[0] + reach, ohi[1] + reach, ohi[2] + reach};
+      int i0[3], i1[3];
+      cell_range(lo, hi, i0, i1);
+      for (int z = i0[2]; z <= i1[2]; ++z)
+        for (int y = i0[1]; y <= i1[1]; ++y)
+          for (int x = i0[0]; x <= i1[0]; ++x) {
+            const double clo[3] = {G.lo[0] + x * h, G.lo[1] + y * h, G.lo[2] + z * h};
+            const double chi[3] = {clo[0] + h, clo[1] + h, clo[2] + h};
+            if (box_box(clo, chi, olo, ohi) < reach) visit(((int64_t)z * ny + y) * nx + x, 1, i);
+          }
+    }
+  };
+  std::vector<int64_t> cnt_s(ncells, 0), cnt_b(ncells, 0);
+  int64_t total = 0;
+  each([&](int64_t c, int kind, int) {
+    (kind ? cnt_b : cnt_s)[c]++;
+    ++total;
+  });
+  if (total > max_items) return ObstacleGrid{};
+  G.off.assign(ncells + 1, 0);
+  G.ns.assign(ncells, 0);
+  for (int64_t c = 0; c < ncells; ++c) {
+    G.off[c + 1] = G.off[c] + (int32_t)(cnt_s[c] + cnt_b[c]);
+    G.ns[c] = (uint16_t)std::min<int64_t>(cnt_s[c], 65535);
+    if (cnt_s[c] > 65535) return ObstacleGrid{};
+  }
+  G.items.assign((size_t)total, 0);
+  std::vector<int32_t> fs(ncells), fb(ncells);
+  for (int64_t c = 0; c < ncells; ++c) {
+    fs[c] = G.off[c];
+    fb[c] = G.off[c] + G.ns[c];
+  }
+  each([&](int64_t c, int kind, int id) { G.items[kind ? fb[c]++ : fs[c]++] = (uint16_t)id; });
+  G.R = R;
+  return G;
+}
+
 }  // namespace mrv

@@ -37,4 +37,28 @@ struct PreparedModel {
 PreparedModel prepare_model(int n_links, int m, const int32_t *link, const float *xyzr, int n_self,
                             const int32_t *pairs);
 
+// Uniform grid over a static obstacle set for the frame-level broadphase.
+// A frame bounding sphere of radius <= R whose center lies in cell c can
+// only overlap the obstacles listed for c: cell c lists every obstacle sphere
+// within R + r_o (+ slack) of the cell's box and every box within R
+// (+ slack) of it.  The slack (1e-3 cell + 1e-6 relative) covers the FP32
+// computation of a center's cell.  Centers outside the grid overlap no
+// obstacle.  Cell (ix, iy, iz) = [lo + i h, lo + (i + 1) h) per axis, index
+// (iz * dims[1] + iy) * dims[0] + ix.
+struct ObstacleGrid {
+  double lo[3] = {0, 0, 0};
+  double h = 0;
+  double R = -1;                       // < 0: no grid (full scan)
+  int dims[3] = {0, 0, 0};
+  std::vector<int32_t> off;            // ncells + 1: items of cell c are [off[c], off[c+1])
+  std::vector<uint16_t> ns;            // obstacle spheres listed first, ns[c] of them
+  std::vector<uint16_t> items;         // obstacle sphere ids, then box ids
+};
+
+// Builds the grid for frames of radius <= R (at most 64 cells per axis,
+// cells of at least R / 2).  Returns R = -1 (no grid) when R <= 0, there are
+// no obstacles, either kind exceeds 65535, or the lists would pass max_items.
+ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, const float *lohi, double R,
+                                 int64_t max_items = int64_t(1) << 24);
+
 }  // namespace mrv

@@ -62,13 +62,13 @@ struct HostModel {
 struct HostEnv {
   EnvDev dev{};
   void *d_spheres = nullptr, *d_k = nullptr, *d_lo = nullptr, *d_hi = nullptr;
+  void *d_goff = nullptr, *d_gns = nullptr, *d_gitems = nullptr;   // obstacle grid
   int refs = 0;
   void free_all() {
-    if (d_spheres) cudaFree(d_spheres);
-    if (d_k) cudaFree(d_k);
-    if (d_lo) cudaFree(d_lo);
-    if (d_hi) cudaFree(d_hi);
-    d_spheres = d_k = d_lo = d_hi = nullptr;
+    for (void **p : {&d_spheres, &d_k, &d_lo, &d_hi, &d_goff, &d_gns, &d_gitems}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
   }
 };
 

@@ -67,6 +67,7 @@ struct TileCtx {
   const float4 *env_s;
   const float *env_k;
   const float4 *box_lo, *box_hi;
+  const EnvDev *env;         // the query's obstacle set (null: none)
   float env_c2, env_r2, rho2;
   long long pairtests, envtests, boxtests;
   unsigned long long tests, btests, states, chains, placed;
@@ -81,7 +82,8 @@ struct Cands {
   uint32_t pc[kCand];        // robot-robot: frame slot k << 8 | frame slot k2
   uint32_t ec[kCand];        // frame slot << 24 | obstacle sphere
   uint32_t bc[kCand];        // frame slot << 24 | obstacle box
-  uint32_t sc[kCand];        // robot << 16 | self-pair group, then robot << 16 | first pair
+  uint32_t sc[kCand];        // self-pair group: robot << 16 | its first pair
+  uint16_t scn[kCand];       // ... and its pair count
   int32_t pf[kCand + 1];     // exclusive prefix of the tests of the list being resolved
   int32_t np, ne, nb, ns, overflow, pad;
   uint32_t need[3], placed[3];
@@ -236,7 +238,7 @@ __global__ void k_prep(BatchDev B) {
     const bool check_env = mv && (B.flags & MRV_CHECK_ENV);
     Q.ntiles = (int)((T + 1 + kWarp - 1) / kWarp);
     int split = flavor_a ? 1 : B.tile_split;
-    if (split != 1 && split != 2 && split != 4 && split != 8) split = 4;
+    if (split < 1 || split > kWarp || (split & (split - 1))) split = 4;
     Q.split = split;
     Q.spt = kWarp / split;
     Q.nslices = Q.ntiles * split;
@@ -935,13 +937,70 @@ __device__ __forceinline__ void need_all(Cands &cl, int lane) {
   __syncwarp();
 }
 
+// last item i of a prefix list with pf[i] <= f (f < pf[n])
+__device__ __forceinline__ int list_find(const int32_t *pf, int n, int f) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pf[mid] <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Exact tests of a frame x obstacle list (cl.pf holds its sphere prefix):
+// lane l takes a contiguous run of the flat (candidate, sphere) range, so a
+// candidate's data stays in registers over its spheres.
+template <bool BOX>
+__device__ bool resolve_obstacles(const TileCtx &C, const WarpSmem &S, const uint32_t *list, int n, int tot,
+                                  int lane, BroadAcc &acc) {
+  const Cands &cl = S.u.b.cl;
+  const float4 *P = S.u.b.P;
+  const int per = (tot + kWarp - 1) / kWarp;
+  int f = lane * per;
+  const int fe = min(f + per, tot);
+  bool hit = false;
+  if (f < fe) {
+    acc.tests += (uint32_t)(fe - f);
+    if (BOX) acc.boxes += (uint32_t)(fe - f);
+    const float ox = S.ox, oy = S.oy, oz = S.oz;
+    for (int it = list_find(cl.pf, n, f); f < fe; ++it) {
+      const uint32_t v = list[it];
+      const int o = (int)(v & 0xffffffu);
+      const int ge = min(fe, cl.pf[it + 1]);
+      const float4 *Pk = P + frame_first(S, (int)(v >> 24)) - cl.pf[it];
+      if (!BOX) {
+        const float4 es = o < kEnvCache ? S.ES[o] : __ldg(&C.env_s[o]);
+#pragma unroll 4
+        for (; f < ge; ++f) {
+          const float4 p = Pk[f];
+          hit |= sph_hit(make_float4(p.x + ox, p.y + oy, p.z + oz, p.w), es);
+        }
+      } else {
+        const float4 lo = o < kBoxCache ? S.BL[o] : __ldg(&C.box_lo[o]);
+        const float4 hi = o < kBoxCache ? S.BH[o] : __ldg(&C.box_hi[o]);
+#pragma unroll 4
+        for (; f < ge; ++f) {
+          const float4 p = Pk[f];
+          hit |= box_d2(p.x + ox, p.y + oy, p.z + oz, lo, hi) < p.w * p.w;
+        }
+      }
+    }
+  }
+  return hit;
+}
+
 // One state of the broadphase path: MV -> 1 on a collision, FFC -> the
-// bitmask of colliding robot pairs.
+// bitmask of colliding robot pairs.  MV checks the obstacles, then the self
+// pairs, then the other robots, with a warp vote after each (all three
+// belong to one state, so the verdict is the same in any order; the env and
+// self checks still come before the robot-robot ones, as in Alg. 1).
 __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane, bool need_env,
                                 bool do_pairs, BroadAcc &acc) {
   Cands &cl = S.u.b.cl;
   const float4 *P = S.u.b.P;
   const int n = C.n, nk = n * kMaxLinks;
+  const bool exhaustive = C.exhaustive != 0, ffc = C.ffc != 0;
   if (lane == 0) {
     cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = 0;
     cl.need[0] = cl.need[1] = cl.need[2] = 0;
@@ -950,120 +1009,197 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
   __syncwarp();
   bool hit = false;
   if (need_env) {
-    // frames x obstacles, lane = (frame group lane & 3, obstacle group lane >> 2)
-    const int fg = lane & 3, og = lane >> 2;
-    const int ns_c = min(C.env_ns, kEnvCache), nb_c = min(C.env_nb, kBoxCache);
-    for (int k = fg; k < nk; k += 4) {
-      const float4 bl = S.BS[k];
-      if (bl.w < 0.f) continue;
-      const float4 bw = make_float4(bl.x + S.ox, bl.y + S.oy, bl.z + S.oz, bl.w);
-      bool nd = false;
-      for (int e = og; e < C.env_ns; e += 8) {
-        const float4 es = e < ns_c ? S.ES[e] : __ldg(&C.env_s[e]);
-        acc.tests += 1;
-        if (sph_hit(bw, es)) {
-          push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
-          nd = true;
+    const int env_ns = C.env_ns, env_nb = C.env_nb;
+    const int ns_c = min(env_ns, kEnvCache), nb_c = min(env_nb, kBoxCache);
+    const float4 *env_s = C.env_s, *box_lo = C.box_lo, *box_hi = C.box_hi;
+    const float ox = S.ox, oy = S.oy, oz = S.oz;
+    const float gR = C.env ? C.env->g_R : -1.f;
+    if (gR >= 0.f) {
+      // lane per frame: the obstacles listed in the grid cell of its center
+      const EnvDev &E = *C.env;
+      const float glx = E.g_lo[0], gly = E.g_lo[1], glz = E.g_lo[2], gih = E.g_inv_h;
+      const int gdx = E.g_dims[0], gdy = E.g_dims[1], gdz = E.g_dims[2];
+      for (int k = lane; k < nk; k += kWarp) {
+        const float4 bl = S.BS[k];
+        if (bl.w < 0.f) continue;
+        const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
+        int i0 = 0, is = 0, i1 = 0;   // spheres [i0, is), boxes [is, i1) of g_items
+        bool full = false;
+        if (bw.w <= gR) {
+          const float fx = (bw.x - glx) * gih, fy = (bw.y - gly) * gih, fz = (bw.z - glz) * gih;
+          if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)gdx && fy < (float)gdy && fz < (float)gdz) {
+            const int c = ((int)fz * gdy + (int)fy) * gdx + (int)fx;
+            i0 = __ldg(&E.g_off[c]);
+            i1 = __ldg(&E.g_off[c + 1]);
+            is = i0 + (int)__ldg(&E.g_ns[c]);
+          }
+        } else {
+          full = true;
         }
-      }
-      const float rr = bw.w * bw.w;
-      for (int b = og; b < C.env_nb; b += 8) {
-        const float4 lo = b < nb_c ? S.BL[b] : __ldg(&C.box_lo[b]);
-        const float4 hi = b < nb_c ? S.BH[b] : __ldg(&C.box_hi[b]);
-        acc.tests += 1;
-        acc.boxes += 1;
-        if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
-          push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
-          nd = true;
+        bool nd = false;
+        if (!full) {
+          acc.tests += (uint32_t)(i1 - i0);
+          acc.boxes += (uint32_t)(i1 - is);
+          for (int i = i0; i < is; ++i) {
+            const int e = __ldg(&E.g_items[i]);
+            const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
+            if (sph_hit(bw, es)) {
+              push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
+              nd = true;
+            }
+          }
+          const float rr = bw.w * bw.w;
+          for (int i = is; i < i1; ++i) {
+            const int b = __ldg(&E.g_items[i]);
+            const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
+            const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
+            if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
+              push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
+              nd = true;
+            }
+          }
+        } else {
+          acc.tests += (uint32_t)(env_ns + env_nb);
+          acc.boxes += (uint32_t)env_nb;
+          for (int e = 0; e < env_ns; ++e) {
+            const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
+            if (sph_hit(bw, es)) {
+              push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
+              nd = true;
+            }
+          }
+          const float rr = bw.w * bw.w;
+          for (int b = 0; b < env_nb; ++b) {
+            const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
+            const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
+            if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
+              push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
+              nd = true;
+            }
+          }
         }
+        if (nd) need_frame(cl, k);
       }
-      if (nd) need_frame(cl, k);
-    }
-    // self-pair groups by their frames' bounding spheres
-    for (int r = 0; r < n; ++r) {
-      const ModelDev &md = *S.rs[r].md;
-      for (int g = lane; g < S.rs[r].n_groups; g += kWarp) {
-        const int4 G = __ldg(&md.self_groups[g]);
-        acc.tests += 1;
-        if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
-          push_cand(cl.sc, &cl.ns, &cl.overflow, ((uint32_t)r << 16) | (uint32_t)g);
-          need_frame(cl, r * kMaxLinks + G.x);
-          need_frame(cl, r * kMaxLinks + G.y);
+    } else {
+      // no grid: frames x obstacles, lane = (frame group lane & 3, obstacle group lane >> 2)
+      const int fg = lane & 3, og = lane >> 2;
+      for (int k = fg; k < nk; k += 4) {
+        const float4 bl = S.BS[k];
+        if (bl.w < 0.f) continue;
+        const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
+        bool nd = false;
+        for (int e = og; e < env_ns; e += 8) {
+          const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
+          if (sph_hit(bw, es)) {
+            push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
+            nd = true;
+          }
         }
+        const float rr = bw.w * bw.w;
+        for (int b = og; b < env_nb; b += 8) {
+          const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
+          const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
+          if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
+            push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
+            nd = true;
+          }
+        }
+        if (nd) need_frame(cl, k);
       }
+      const uint32_t ns_l = (uint32_t)max(0, (env_ns - og + 7) >> 3), nb_l = (uint32_t)max(0, (env_nb - og + 7) >> 3);
+      int nf = 0;   // bounding spheres of this lane's frame group
+      for (int k = fg; k < nk; k += 4) nf += S.BS[k].w >= 0.f;
+      acc.tests += (uint32_t)nf * (ns_l + nb_l);
+      acc.boxes += (uint32_t)nf * nb_l;
     }
     __syncwarp();
-    if (cl.overflow) {   // too many candidates: resolve this phase in the lanes
+    if (cl.overflow) {   // too many candidates: resolve env and self in the lanes
       need_all(cl, lane);
       place_needed(C, S, xf, jj, lane, acc);
       unsigned long long t = 0, bx = 0;
       hit = env_broad(C, S, P, lane, t, bx);
       acc.tests += (uint32_t)t;
       acc.boxes += (uint32_t)bx;
+      if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
     } else {
-      place_needed(C, S, xf, jj, lane, acc);
-      const int ne = cl.ne, nbx = cl.nb, ns = cl.ns;
-      if (ne) {
-        const int tot = scan_frames(cl, cl.ec, ne, S, lane);
-        int it = 0;
-        for (int f = lane; f < tot; f += kWarp) {
-          while (cl.pf[it + 1] <= f) ++it;
-          const uint32_t v = cl.ec[it];
-          const int e = (int)(v & 0xffffffu);
-          const float4 es = e < kEnvCache ? S.ES[e] : __ldg(&C.env_s[e]);
-          const float4 p = P[frame_first(S, (int)(v >> 24)) + f - cl.pf[it]];
-          hit |= sph_hit(make_float4(p.x + S.ox, p.y + S.oy, p.z + S.oz, p.w), es);
+      if (cl.ne | cl.nb) {
+        place_needed(C, S, xf, jj, lane, acc);
+        const int ne = cl.ne, nbx = cl.nb;
+        if (ne) {
+          const int tot = scan_frames(cl, cl.ec, ne, S, lane);
+          hit |= resolve_obstacles<false>(C, S, cl.ec, ne, tot, lane, acc);
+          __syncwarp();
         }
-        acc.tests += (uint32_t)((tot - lane + kWarp - 1) / kWarp);
-        __syncwarp();
-      }
-      if (nbx) {
-        const int tot = scan_frames(cl, cl.bc, nbx, S, lane);
-        int it = 0;
-        for (int f = lane; f < tot; f += kWarp) {
-          while (cl.pf[it + 1] <= f) ++it;
-          const uint32_t v = cl.bc[it];
-          const int b = (int)(v & 0xffffffu);
-          const float4 lo = b < kBoxCache ? S.BL[b] : __ldg(&C.box_lo[b]);
-          const float4 hi = b < kBoxCache ? S.BH[b] : __ldg(&C.box_hi[b]);
-          const float4 p = P[frame_first(S, (int)(v >> 24)) + f - cl.pf[it]];
-          hit |= box_d2(p.x + S.ox, p.y + S.oy, p.z + S.oz, lo, hi) < p.w * p.w;
+        if (nbx) {
+          const int tot = scan_frames(cl, cl.bc, nbx, S, lane);
+          hit |= resolve_obstacles<true>(C, S, cl.bc, nbx, tot, lane, acc);
+          __syncwarp();
         }
-        const uint32_t c = (uint32_t)((tot - lane + kWarp - 1) / kWarp);
-        acc.tests += c;
-        acc.boxes += c;
-        __syncwarp();
+        if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
       }
-      if (ns) {
-        // self pairs of the overlapping groups as one flat range
+      // self-pair groups by their frames' bounding spheres
+      for (int r = 0; r < n; ++r) {
+        const int4 *groups = S.rs[r].md->self_groups;
+        const int ng = S.rs[r].n_groups;
+        for (int g = lane; g < ng; g += kWarp) {
+          const int4 G = __ldg(&groups[g]);
+          acc.tests += 1;
+          if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
+            const int i = atomicAdd(&cl.ns, 1);
+            if (i < kCand) {
+              cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)G.z;
+              cl.scn[i] = (uint16_t)G.w;
+            } else {
+              cl.overflow = 1;
+            }
+            need_frame(cl, r * kMaxLinks + G.x);
+            need_frame(cl, r * kMaxLinks + G.y);
+          }
+        }
+      }
+      __syncwarp();
+      if (cl.overflow) {
+        need_all(cl, lane);
+        place_needed(C, S, xf, jj, lane, acc);
+        unsigned long long t = 0, bx = 0;
+        hit |= env_broad(C, S, P, lane, t, bx);
+        acc.tests += (uint32_t)t;
+        acc.boxes += (uint32_t)bx;
+      } else if (cl.ns) {
+        place_needed(C, S, xf, jj, lane, acc);
+        const int ns = cl.ns;
         int base = 0;
         for (int i0 = 0; i0 < ns; i0 += kWarp) {
           const int i = i0 + lane;
           int c = 0;
-          if (i < ns) {
-            const uint32_t v = cl.sc[i];
-            const int r = (int)(v >> 16);
-            const int4 G = __ldg(&S.rs[r].md->self_groups[v & 0xffffu]);
-            c = G.w;
-            cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)G.z;
-          }
+          if (i < ns) c = cl.scn[i];
           base = scan_chunk(cl.pf, i, ns, c, base, lane);
         }
         if (lane == 0) cl.pf[ns] = base;
         __syncwarp();
-        int it = 0;
-        for (int f = lane; f < base; f += kWarp) {
-          while (cl.pf[it + 1] <= f) ++it;
-          const uint32_t v = cl.sc[it];
-          const int r = (int)(v >> 16), o = S.off[r];
-          const uint32_t e = __ldg(&S.rs[r].self[(v & 0xffffu) + (uint32_t)(f - cl.pf[it])]);
-          hit |= sph_hit(P[o + (int)(e & 0xffffu)], P[o + (int)(e >> 16)]);
+        // lane l takes a contiguous run of the flat pair range
+        const int per = (base + kWarp - 1) / kWarp;
+        int f = lane * per;
+        const int fe = min(f + per, base);
+        if (f < fe) {
+          acc.tests += (uint32_t)(fe - f);
+          for (int it = list_find(cl.pf, ns, f); f < fe; ++it) {
+            const uint32_t v = cl.sc[it];
+            const int r = (int)(v >> 16);
+            const int ge = min(fe, cl.pf[it + 1]);
+            const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
+            const float4 *Pr = P + S.off[r];
+#pragma unroll 4
+            for (; f < ge; ++f) {
+              const uint32_t e = __ldg(&pr[f]);
+              hit |= sph_hit(Pr[e & 0xffffu], Pr[e >> 16]);
+            }
+          }
         }
-        acc.tests += (uint32_t)((base - lane + kWarp - 1) / kWarp);
         __syncwarp();
       }
     }
-    if (__any_sync(0xffffffffu, hit) && !C.exhaustive) return 1u;
+    if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
   }
   if (!do_pairs) return __any_sync(0xffffffffu, hit) ? 1u : 0u;
   // robot-robot: every (robot pair, frame pair) as one flat range
@@ -1100,11 +1236,11 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
     need_all(cl, lane);
     place_needed(C, S, xf, jj, lane, acc);
     unsigned long long t = 0;
-    pm = pairs_broad(C, S, P, lane, C.ffc != 0, t);
+    pm = pairs_broad(C, S, P, lane, ffc, t);
     acc.tests += (uint32_t)t;
   } else if (np > 0) {
     place_needed(C, S, xf, jj, lane, acc);
-    // lanes take (candidate, sphere of frame k) and test it against frame k2
+    // flat (candidate, sphere of frame k) range; each entry tests frame k2
     int base = 0;
     for (int i0 = 0; i0 < np; i0 += kWarp) {
       const int i = i0 + lane;
@@ -1113,20 +1249,28 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
     }
     if (lane == 0) cl.pf[np] = base;
     __syncwarp();
-    int it = 0;
-    for (int f = lane; f < base; f += kWarp) {
-      while (cl.pf[it + 1] <= f) ++it;
-      const uint32_t v = cl.pc[it];
-      const int k = (int)(v >> 8), k2 = (int)(v & 0xffu);
-      const float4 pa = P[frame_first(S, k) + f - cl.pf[it]];
-      const int b0 = frame_first(S, k2), b1 = b0 + frame_count(S, k2);
-      bool h = false;
-      for (int b = b0; b < b1; ++b) h |= sph_hit(pa, P[b]);
-      acc.tests += (uint32_t)(b1 - b0);
-      if (h) pm |= C.ffc ? (1u << pair_index(k / kMaxLinks, k2 / kMaxLinks, n)) : 1u;
+    const int per = (base + kWarp - 1) / kWarp;
+    int f = lane * per;
+    const int fe = min(f + per, base);
+    if (f < fe) {
+      for (int it = list_find(cl.pf, np, f); f < fe; ++it) {
+        const uint32_t v = cl.pc[it];
+        const int k = (int)(v >> 8), k2 = (int)(v & 0xffu);
+        const int ge = min(fe, cl.pf[it + 1]);
+        const float4 *Pk = P + frame_first(S, k) - cl.pf[it];
+        const int b0 = frame_first(S, k2), b1 = b0 + frame_count(S, k2);
+        acc.tests += (uint32_t)((ge - f) * (b1 - b0));
+        bool h = false;
+        for (; f < ge; ++f) {
+          const float4 pa = Pk[f];
+#pragma unroll 4
+          for (int b = b0; b < b1; ++b) h |= sph_hit(pa, P[b]);
+        }
+        if (h) pm |= ffc ? (1u << pair_index(k / kMaxLinks, k2 / kMaxLinks, n)) : 1u;
+      }
     }
   }
-  if (C.ffc) return __reduce_or_sync(0xffffffffu, pm);
+  if (ffc) return __reduce_or_sync(0xffffffffu, pm);
   return __any_sync(0xffffffffu, hit || pm != 0) ? 1u : 0u;
 }
 
@@ -1335,9 +1479,11 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
   C.split = Q.split; C.spt = Q.spt; C.nslices = Q.nslices;
   C.broad = (B.flags & MRV_NO_BROADPHASE) ? 0 : 1;
   C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
+  C.env = nullptr;
   C.env_c2 = 0.f; C.env_r2 = 0.f; C.rho2 = Q.rho2;
   if (C.check_env && Q.env >= 0) {
     const EnvDev &E = B.envs[Q.env];
+    C.env = &E;
     C.env_ns = E.n_spheres; C.env_nb = E.n_aabbs; C.env_s = E.spheres; C.env_k = E.sphere_k;
     C.box_lo = E.box_lo; C.box_hi = E.box_hi; C.env_c2 = E.c2max; C.env_r2 = E.r2max;
   }

@@ -12,6 +12,7 @@
 // nothing spins on the device.
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -105,6 +106,7 @@ using namespace mrv;
 // Packs the slot's requests into one micro-batch in pinned memory and issues
 // copies, kernels and result copies on the slot's stream.
 void mrv_server::launch(Slot &s) {
+  cudaGetLastError();   // a launch reports its own errors only
   int32_t nq = 0, ns = 0, nw = 0, stride = 1;
   bool timed = s.reqs[0]->timed, any_env = false, any_kind = false;
   for (auto &r : s.reqs) {
@@ -117,7 +119,8 @@ void mrv_server::launch(Slot &s) {
   }
   const size_t in_bytes = sizeof(int32_t) * ((size_t)nq + 1 + ns + ns + 1 + (timed ? nw : 0) + nq) +
                           sizeof(float) * (size_t)nw * stride + nq + 64 * 8;
-  const size_t out_bytes = (size_t)nq * (1 + sizeof(mrv_conflict)) + 256;
+  // valid bytes (rounded up to 256), conflicts, the error word
+  const size_t out_bytes = (((size_t)nq + 255) & ~size_t(255)) + sizeof(mrv_conflict) * (size_t)nq + 64;
   int rc = grow_pinned(&s.pin_in, &s.pin_in_cap, in_bytes);
   if (!rc) rc = grow_pinned(&s.pin_out, &s.pin_out_cap, out_bytes);
   if (!rc) rc = s.scratch.ensure(nq, ns, nw, stride, s.stream);
@@ -193,7 +196,12 @@ void mrv_server::launch(Slot &s) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(conf_h, s.scratch.out_conf, sizeof(mrv_conflict) * nq, cudaMemcpyDeviceToHost, s.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(err_h, s.scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "server result copy");
+    if (e != cudaSuccess) {
+      char what[160];
+      std::snprintf(what, sizeof what, "server result copy (%d queries, host %p, device %p %p %p)", nq, s.pin_out,
+                    (void *)s.scratch.out_valid, (void *)s.scratch.out_conf, (void *)s.scratch.err);
+      rc = cuda_fail(e, what);
+    }
   }
   if (rc) {
     s.launch_status = rc;

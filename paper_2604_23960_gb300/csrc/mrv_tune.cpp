@@ -107,9 +107,9 @@ extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_pa
   uint8_t *valid = (uint8_t *)outs + ((size_t)b->n_queries * sizeof(mrv_conflict) + 255) / 256 * 256;
   const mrv_tuning saved = c->tuning;
   float best_ms = INFINITY;
-  static const int chunks[] = {1, 2, 4};
-  static const int splits[] = {1, 2, 4, 8};
-  static const int warps[] = {2, 4, 8};
+  static const int chunks[] = {1, 2};
+  static const int splits[] = {2, 4, 8, 16};
+  static const int warps[] = {4, 8};
   for (int w : warps)
     for (int sp : splits)
       for (int ch : chunks) {

@@ -279,7 +279,7 @@ def test_tunings_do_not_change_results(ctx, tmp_path):
     ref = ctx.run(ba)
     saved = mrv.mrv_get_tuning(ctx.h)
     try:
-        for ch, wp, sp in [(1, 2, 1), (2, 8, 2), (16, 4, 8), (3, 12, 4), (1, 1, 4)]:
+        for ch, wp, sp in [(1, 2, 1), (2, 8, 2), (16, 4, 8), (3, 12, 4), (1, 1, 4), (1, 4, 16), (2, 6, 32)]:
             mrv.mrv_set_tuning(ctx.h, ch, wp, 0, sp)
             assert same(ctx.run(ba), ref)
         t = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
