@@ -592,6 +592,13 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
     return rc;
   }
   if ((rc = upload(&m.d_perm, PM.perm.data(), sizeof(int32_t) * PM.perm.size()))) { m.free_all(); return rc; }
+  if ((rc = upload(&m.d_blocks, PM.self_blocks.data(), sizeof(int32_t) * PM.self_blocks.size())) ||
+      (rc = upload(&m.d_masks, PM.self_masks.data(), sizeof(uint32_t) * PM.self_masks.size()))) {
+    m.free_all();
+    return rc;
+  }
+  D.self_blocks = PM.self_blocks.empty() ? nullptr : (const int4 *)m.d_blocks;
+  D.self_masks = PM.self_masks.empty() ? nullptr : (const uint32_t *)m.d_masks;
   // rectangles pay off only when they are large enough to fill a warp's
   // 4-rows-per-lane tiling; small ones stay on the sparse pair path
   std::vector<std::pair<int32_t, int32_t>> spr(sp);

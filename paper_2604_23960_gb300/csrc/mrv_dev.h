@@ -53,6 +53,10 @@ struct ModelDev {
   int32_t link_start[kMaxLinks + 1];  // spheres (sorted by frame) of frame l
   float link_bs[kMaxLinks][4];   // frame-local bounding sphere (radius < 0: empty)
   const int4 *self_groups;       // (frame u, frame v, first pair, count)
+  const int4 *self_blocks;       // per group: first row sphere, first column
+                                 // sphere, rows | columns << 16 (columns <= 32),
+                                 // first row mask; null: pair list only
+  const uint32_t *self_masks;    // per block row: bit c = pair with column c
   int32_t n_groups;
   int32_t pad3;
   const int32_t *perm;           // sorted sphere index -> caller's index

@@ -90,6 +90,34 @@ PreparedModel prepare_model(int n_links, int m, const int32_t *link, const float
     P.self_groups.insert(P.self_groups.end(), {u, v, (int32_t)p, (int32_t)(e - p)});
     p = e;
   }
+  // blocks: rows = the larger frame, columns = the smaller (<= 32 spheres)
+  bool ok = true;
+  for (size_t g = 0; g < P.self_groups.size() / 4 && ok; ++g) {
+    const int u = P.self_groups[4 * g], v = P.self_groups[4 * g + 1];
+    const int nu = P.link_start[u + 1] - P.link_start[u], nv = P.link_start[v + 1] - P.link_start[v];
+    const bool rows_u = nu >= nv;
+    const int rf = rows_u ? u : v, cf = rows_u ? v : u;
+    const int nr = rows_u ? nu : nv, nc = rows_u ? nv : nu;
+    if (nc > 32) {
+      ok = false;
+      break;
+    }
+    const int first_mask = (int)P.self_masks.size();
+    P.self_masks.resize(P.self_masks.size() + nr, 0u);
+    const int p0 = P.self_groups[4 * g + 2], pc = P.self_groups[4 * g + 3];
+    for (int q = p0; q < p0 + pc; ++q) {
+      int x = P.self[q].first, y = P.self[q].second;   // x in frame u, y in frame v
+      if (!rows_u) std::swap(x, y);                      // x: row sphere, y: column sphere
+      if (u == v && x > y) std::swap(x, y);
+      P.self_masks[first_mask + (x - P.link_start[rf])] |= 1u << (y - P.link_start[cf]);
+    }
+    P.self_blocks.insert(P.self_blocks.end(),
+                         {P.link_start[rf], P.link_start[cf], nr | (nc << 16), first_mask});
+  }
+  if (!ok) {
+    P.self_blocks.clear();
+    P.self_masks.clear();
+  }
   return P;
 }
 

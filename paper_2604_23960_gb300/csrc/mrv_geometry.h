@@ -28,6 +28,13 @@ struct PreparedModel {
   std::vector<float> link_bs;          // n_links x 4: frame-local center, radius (radius < 0: no spheres)
   std::vector<std::pair<int32_t, int32_t>> self;  // (x < y) in sorted indices, by (frame x, frame y, x, y)
   std::vector<int32_t> self_groups;    // n_groups x 4: frame u, frame v, first pair, pair count
+  // the same pairs per group as a block: rows = the spheres of the frame with
+  // more of them, columns = the other frame's (at most 32), one bit mask of
+  // listed partners per row.  n_groups x 4: first row sphere, first column
+  // sphere, rows | columns << 16, first mask.  Empty when a group's smaller
+  // frame holds more than 32 spheres.
+  std::vector<int32_t> self_blocks;
+  std::vector<uint32_t> self_masks;
 };
 
 // Bounding sphere of a frame: center = middle of the bounding box of the

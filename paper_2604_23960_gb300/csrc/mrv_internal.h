@@ -46,11 +46,11 @@ struct Scratch {
 struct HostModel {
   ModelDev dev{};
   void *d_spheres = nullptr, *d_links = nullptr, *d_self = nullptr, *d_rects = nullptr, *d_groups = nullptr,
-       *d_perm = nullptr;
+       *d_perm = nullptr, *d_blocks = nullptr, *d_masks = nullptr;
   int refs = 0;
   int max_spheres = 0;
   void free_all() {
-    for (void **p : {&d_spheres, &d_links, &d_self, &d_rects, &d_groups, &d_perm}) {
+    for (void **p : {&d_spheres, &d_links, &d_self, &d_rects, &d_groups, &d_perm, &d_blocks, &d_masks}) {
       if (*p) cudaFree(*p);
       *p = nullptr;
     }

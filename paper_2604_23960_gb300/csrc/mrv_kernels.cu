@@ -45,7 +45,7 @@
 namespace mrv {
 
 constexpr int kFlavorAMaxSpheres = 16;
-constexpr int kSlotWords = 26;                   // words per RobotSlot in shared memory
+constexpr int kSlotWords = 28;                   // words per RobotSlot in shared memory
 constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
 
 struct RobotSlot {           // per-warp staged view of one robot of the query
@@ -54,6 +54,7 @@ struct RobotSlot {           // per-warp staged view of one robot of the query
   const uint32_t *self;      // packed pairs x | y << 16, padded to a multiple of 4
   const int4 *rects;         // self pairs as rectangles (rows x0..x1, columns y0..y1)
   const ModelDev *md;        // the model (frame ranges, bounding spheres, groups)
+  const uint32_t *masks;     // self-pair block row masks (null: none)
   int32_t mdl, m, dof, kind, n_self, w0, w1, n_rects;
   int32_t n_links, n_groups;
   int16_t ls[kMaxLinks + 2]; // frame ranges of the sorted spheres (copy of md->link_start)
@@ -62,6 +63,7 @@ static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
 struct TileCtx {
   int q, T, n, M, nb, ffc, check_env, exhaustive, broad;
+  int self_blk;              // every robot's self pairs come as blocks
   int split, spt, nslices;
   int env_ns, env_nb;
   const float4 *env_s;
@@ -1147,7 +1149,8 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
           if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
             const int i = atomicAdd(&cl.ns, 1);
             if (i < kCand) {
-              cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)G.z;
+              // blocks: robot << 16 | group; pair list: robot << 16 | first pair
+              cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)(C.self_blk ? g : G.z);
               cl.scn[i] = (uint16_t)G.w;
             } else {
               cl.overflow = 1;
@@ -1165,7 +1168,49 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
         hit |= env_broad(C, S, P, lane, t, bx);
         acc.tests += (uint32_t)t;
         acc.boxes += (uint32_t)bx;
+      } else if (cl.ns && C.self_blk) {
+        // self pairs as blocks: lane = one row sphere of an overlapping
+        // group's block, tested against the columns its mask lists (lanes of
+        // one block read the same column spheres)
+        place_needed(C, S, xf, jj, lane, acc);
+        const int ns = cl.ns;
+        int base = 0;
+        for (int i0 = 0; i0 < ns; i0 += kWarp) {
+          const int i = i0 + lane;
+          int c = 0;
+          if (i < ns) {
+            const uint32_t v = cl.sc[i];
+            const int r = (int)(v >> 16);
+            const int4 Bk = __ldg(&S.rs[r].md->self_blocks[v & 0xffffu]);
+            const int o = S.off[r];
+            c = Bk.z & 0xffff;
+            cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 9) | ((uint32_t)r << 24);
+            cl.scn[i] = (uint16_t)Bk.w;
+          }
+          base = scan_chunk(cl.pf, i, ns, c, base, lane);
+        }
+        if (lane == 0) cl.pf[ns] = base;
+        __syncwarp();
+        int it = 0;
+        uint32_t nt = 0;
+        for (int f = lane; f < base; f += kWarp) {
+          while (cl.pf[it + 1] <= f) ++it;
+          const uint32_t v = cl.sc[it];
+          const int row = f - cl.pf[it];
+          const float4 pa = P[(int)(v & 511u) + row];
+          const float4 *Pc = P + ((v >> 9) & 511u);
+          uint32_t mk = __ldg(&S.rs[v >> 24].masks[cl.scn[it] + row]);
+          nt += (uint32_t)__popc(mk);
+          while (mk) {
+            const int c = __ffs(mk) - 1;
+            mk &= mk - 1;
+            hit |= sph_hit(pa, Pc[c]);
+          }
+        }
+        acc.tests += nt;
+        __syncwarp();
       } else if (cl.ns) {
+        // self pairs from the pair list, one contiguous run per lane
         place_needed(C, S, xf, jj, lane, acc);
         const int ns = cl.ns;
         int base = 0;
@@ -1177,7 +1222,6 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
         }
         if (lane == 0) cl.pf[ns] = base;
         __syncwarp();
-        // lane l takes a contiguous run of the flat pair range
         const int per = (base + kWarp - 1) / kWarp;
         int f = lane * per;
         const int fe = min(f + per, base);
@@ -1496,6 +1540,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     const ModelDev &m = B.models[id];
     RobotSlot rs;
     rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects; rs.md = &m;
+    rs.masks = m.self_masks;
     rs.mdl = id; rs.m = m.n_spheres; rs.dof = m.dof; rs.kind = m.kind; rs.n_self = m.n_self;
     rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.n_rects = m.n_rects;
     rs.n_links = m.n_links; rs.n_groups = m.n_groups;
@@ -1509,6 +1554,9 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     int acc = 0;
     S.off[0] = 0;
     for (int r = 0; r < C.n; ++r) { acc += S.rs[r].m; S.off[r + 1] = acc; }
+    int blk = 1;
+    for (int r = 0; r < C.n; ++r) blk &= (S.rs[r].n_groups == 0 || S.rs[r].masks != nullptr);
+    C.self_blk = blk;
     int p = 0, f = 0;
     for (int i = 0; i < C.n; ++i)
       for (int j = i + 1; j < C.n; ++j) {

@@ -28,6 +28,8 @@ int main() {
   printf("bs"); for (float v : P.link_bs) printf(" %.9g", v); printf("\n");
   printf("self"); for (auto &e : P.self) printf(" %d %d", e.first, e.second); printf("\n");
   printf("groups"); for (int v : P.self_groups) printf(" %d", v); printf("\n");
+  printf("blocks"); for (int v : P.self_blocks) printf(" %d", v); printf("\n");
+  printf("masks"); for (unsigned v : P.self_masks) printf(" %u", v); printf("\n");
   return 0;
 }
 '''
@@ -92,3 +94,43 @@ def test_prepare_model(exe, seed):
             assert slink[a] == u and slink[b] == v
         covered += cnt
     assert covered == len(got)
+    check_blocks(d, g, got, start)
+
+
+def check_blocks(d, g, got, start):
+    """Every group's block (rows = the frame with more spheres, columns = the
+    other, at most 32) lists exactly the group's pairs, each once."""
+    blocks = np.array(d.get("blocks", []), int).reshape(-1, 4)
+    masks = [int(v) for v in d.get("masks", [])]
+    counts = np.diff(start)
+    if len(blocks) == 0:
+        # only when some group's smaller frame has more than 32 spheres
+        assert len(g) == 0 or any(min(counts[u], counts[v]) > 32 for u, v, _, _ in g)
+        return
+    assert len(blocks) == len(g)
+    for (u, v, s0, cnt), (r0, c0, rc, m0) in zip(g, blocks):
+        nr, nc = rc & 0xffff, rc >> 16
+        assert nc <= 32 and nr >= nc
+        assert {(r0, nr), (c0, nc)} == {(start[u], counts[u]), (start[v], counts[v])}
+        listed = set()
+        for row in range(nr):
+            for c in range(nc):
+                if masks[m0 + row] >> c & 1:
+                    listed.add(tuple(sorted((r0 + row, c0 + c))))
+        want = {tuple(sorted(p)) for p in got[s0:s0 + cnt]}
+        assert listed == want and sum(bin(masks[m0 + row]).count("1") for row in range(nr)) == len(want)
+
+
+def test_blocks_wide_frames(exe):
+    """A model whose frames both exceed 32 spheres keeps the pair list only;
+    one with a 32-sphere frame against a large one uses blocks."""
+    rng = np.random.default_rng(9)
+    for n0, n1, expect in ((40, 40, False), (60, 32, True)):
+        link = np.array([0] * n0 + [1] * n1)
+        xyzr = np.column_stack([rng.uniform(-0.5, 0.5, (len(link), 3)), np.full(len(link), 0.05)]).astype(np.float32)
+        pairs = [(a, n0 + b) for a in range(0, n0, 3) for b in range(0, n1, 2)]
+        d = run(exe, 2, link, xyzr, pairs)
+        got = [tuple(map(int, d["self"][k:k + 2])) for k in range(0, len(d["self"]), 2)]
+        g = np.array(d["groups"], int).reshape(-1, 4)
+        assert (len(d.get("blocks", [])) > 0) == expect
+        check_blocks(d, g, got, np.array(d["start"], int))
