@@ -64,6 +64,19 @@ def work_flops(st):
             + FLOPS_PER_CHAIN * st["fk_chains"] + FLOPS_PER_SPHERE * st["spheres_placed"])
 MAKERS = None
 
+# DRAM bytes of one k_main launch of the benchmark step, from an ncu capture
+# (profiles/k_main_cage_mv_traffic.md), valid for the kernel source it was
+# taken on; any other source reports null
+TRAFFIC = {"kernel_sha256": "1df4a2785b5a7758c44093ff6fe870e1d1e127ea810f92628ffaa9f6f3f1687e",
+           "bytes": 4209664 + 1024}
+
+
+def traffic_per_launch():
+    import hashlib
+    src = ROOT / "paper_2604_23960_gb300" / "csrc" / "mrv_kernels.cu"
+    h = hashlib.sha256(src.read_bytes()).hexdigest()
+    return TRAFFIC["bytes"] if h == TRAFFIC["kernel_sha256"] else None
+
 
 def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
@@ -281,6 +294,36 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
     return out
 
 
+def order_study(ctx, ba, flush, reps=3):
+    """Effort of the four state-visiting orders of MV (combined or
+    hierarchical env/self-then-pairs order x rake or linear state map) on the
+    benchmark batch, early exit: fraction of states checked, fraction of the
+    method's sphere tests executed (dense kernel, the effort of Fig. 4) and
+    kernel time with and without the frame-level broadphase.  All four give
+    the same verdicts."""
+    from paper_2604_23960_gb300 import mrv
+    out = {}
+    for name, fl in (("combined_rake", 0), ("hierarchical_rake", mrv.MRV_HIERARCHICAL),
+                     ("combined_linear", mrv.MRV_LINEAR),
+                     ("hierarchical_linear", mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR)):
+        row = {}
+        for tag, extra in (("", 0), ("_dense", mrv.MRV_NO_BROADPHASE)):
+            ctx.mv_validate(ba, flags=fl | extra)
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                ctx.mv_validate(ba, flags=fl | extra)
+                ms.append(ctx.stats()["device_ms"])
+            st = ctx.stats()
+            row["kernel_ms" + tag] = statistics.median(ms)
+            if not extra:
+                row["effort_states"] = st["states_checked"] / max(1, st["states_available"])
+            else:
+                row["effort_tests"] = st["sphere_tests"] / max(1, st["sphere_tests_available"])
+        out[name] = row
+    return out
+
+
 def cpu_baseline(w, seconds_hint: float = 20.0):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
     from oracle import oracle as O
@@ -449,6 +492,7 @@ def run(args):
             ms.append(ctx.stats()["device_ms"])
         ex[name] = (statistics.median(ms), ctx.stats())
     torch.cuda.nvtx.range_pop()
+    orders = order_study(ctx, ba, flush)
 
     peaks, src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -472,7 +516,7 @@ def run(args):
                    "launch": "CUDA graph: reset + prepare + persistent work-stealing kernel + results",
                    "tuning": mrv.mrv_get_tuning(ctx.h)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": traffic_per_launch(),
                      "kernel": "k_main (persistent MV kernel), early exit, frame-level broadphase",
                      "work": f"states checked x {per_state} FP32 flops per composite state (every sphere pair, "
                              "obstacle and self pair tested, 4 FK chains, 256 spheres placed)",
@@ -482,6 +526,7 @@ def run(args):
                                            "exact), FK chains and spheres placed, counted by the kernel"},
                      "peak_source": f"SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} sm_max_mhz)"},
         "roofline_exhaustive": ex_out,
+        "order_study": orders,
         "e2e": {"value": e2e_val, "unit": "motion-checks/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(nq),
                 "api": "mv_validate with pinned host buffers", "ms_median": statistics.median(e2e_ms)},
         "per_query_launch": {"value": pq_rate, "unit": "motion-checks/s", "queries": pq_n,

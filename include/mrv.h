@@ -67,6 +67,11 @@ extern "C" {
                                       launch per query                      */
 #define MRV_NO_BROADPHASE 0x40u   /* test every sphere pair (no frame-level
                                      bounding-sphere culling); same results */
+#define MRV_LINEAR 0x80u          /* MV visits the states of a tile in the
+                                     linear order t = 32 b + l (the map FFC
+                                     uses, Sec. IV-B) instead of the rake
+                                     order t = b + nb l of Alg. 1 / Fig. 2;
+                                     same verdicts, different effort        */
 
 /* ---- query kinds (mrv_run) ---------------------------------------------- */
 #define MRV_KIND_MV 0

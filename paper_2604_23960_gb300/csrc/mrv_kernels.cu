@@ -63,6 +63,7 @@ static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
 struct TileCtx {
   int q, T, n, M, nb, ffc, check_env, exhaustive, broad;
+  int lin;                   // linear state order (FFC, or MV with MRV_LINEAR)
   int self_blk;              // every robot's self pairs come as blocks
   int split, spt, nslices;
   int env_ns, env_nb;
@@ -423,7 +424,7 @@ __device__ __forceinline__ float uval(const float4 A, const float4 b, float kb) 
 
 // state of position j of slice k (monotone in j for both packings)
 __device__ __forceinline__ int slice_state(const TileCtx &C, int k, int j) {
-  if (C.ffc) return k * C.spt + j;
+  if (C.lin) return k * C.spt + j;
   const int b = k / C.split, p = k - b * C.split;
   return b + C.nb * (p + C.split * j);
 }
@@ -462,7 +463,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
   __syncwarp();
   if (lane == 0) {
-    C.states += nvalid;
+    if (do_env) C.states += nvalid;   // hierarchical order: a state counts in its first phase
     C.chains += (unsigned long long)nvalid * C.n;
     C.placed += (unsigned long long)nvalid * C.M;
   }
@@ -1400,7 +1401,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
     for (int j = j0; j < j0 + CS && j < C.spt; ++j) {
       const int t = slice_state(C, k, j);
       if (t > C.T) break;
-      if (lane == 0) C.states += 1;
+      if (lane == 0 && do_env) C.states += 1;   // hierarchical order: counted in the first phase
       if (!CLR && C.broad) {
         // frame-level broadphase; spheres are placed only for the frames whose
         // bounding spheres overlap something, then resolved exactly
@@ -1522,6 +1523,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
   C.exhaustive = (B.flags & MRV_EXHAUSTIVE) ? 1 : 0;
   C.split = Q.split; C.spt = Q.spt; C.nslices = Q.nslices;
   C.broad = (B.flags & MRV_NO_BROADPHASE) ? 0 : 1;
+  C.lin = (C.ffc || (B.flags & MRV_LINEAR)) ? 1 : 0;
   C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
   C.env = nullptr;
   C.env_c2 = 0.f; C.env_r2 = 0.f; C.rho2 = Q.rho2;

@@ -31,6 +31,7 @@ MRV_PTRS_ON_DEVICE = 0x8
 MRV_ASYNC = 0x10
 MRV_PER_QUERY_LAUNCH = 0x20
 MRV_NO_BROADPHASE = 0x40
+MRV_LINEAR = 0x80
 MRV_KIND_MV = 0
 MRV_KIND_FFC = 1
 MRV_MAX_ROBOTS = 8

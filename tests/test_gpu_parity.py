@@ -54,8 +54,10 @@ def test_tiny_mv_ffc(ctx, seed, timed):
     bd = ba.to("cuda")
     np.testing.assert_array_equal(_np(ctx.mv_validate(bd)), ctx.mv_validate(ba))
     np.testing.assert_array_equal(_np(ctx.ffc_find(bd)), c)
-    # hierarchical order (Alg. 1): same verdicts
-    np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_HIERARCHICAL), ctx.mv_validate(ba))
+    # hierarchical order (Alg. 1) and the linear state map: same verdicts
+    for fl in (mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_LINEAR | mrv.MRV_HIERARCHICAL):
+        np.testing.assert_array_equal(ctx.mv_validate(ba, flags=fl), ctx.mv_validate(ba))
+    np.testing.assert_array_equal(ctx.ffc_find(ba, flags=mrv.MRV_LINEAR), c)   # FFC is linear already
     # every sphere pair tested (no frame-level broadphase): same verdicts
     for ce in (True, False):
         np.testing.assert_array_equal(ctx.mv_validate(ba, check_env=ce, flags=mrv.MRV_NO_BROADPHASE),
@@ -129,6 +131,18 @@ def test_cage_mv_small_exhaustive(ctx):
     PA.check_mv(o, v)
     np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=mrv.MRV_HIERARCHICAL)), v)
     np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=mrv.MRV_NO_BROADPHASE)), v)
+    # the four visiting orders (combined / hierarchical x rake / linear): same
+    # verdicts; early exit checks a subset of the states, exhaustive all
+    for fl in (0, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR):
+        for bp in (0, mrv.MRV_NO_BROADPHASE):
+            np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=fl | bp)), v)
+            st = ctx.stats()
+            assert 0 < st["states_checked"] <= st["states_available"]
+            np.testing.assert_array_equal(_np(ctx.mv_validate(ba, exhaustive=True, flags=fl | bp)), v)
+            st = ctx.stats()
+            assert st["states_checked"] == st["states_available"]
+            if bp:
+                assert st["sphere_tests"] == st["sphere_tests_available"]
     v2, mc = ctx.mv_validate(ba, exhaustive=True, min_clearance=True)
     np.testing.assert_array_equal(_np(v2), v)
     ref = o.mv_min_clearance(threads=PA.THREADS)
