@@ -426,6 +426,67 @@ int orc_mv_min_clearance(const orc_batch *b, const orc_robot *robots, const orc_
 }
 
 /* ------------------------------------------------------------------------ */
+/* MV of prioritized planning (PP-ST-RRT, Sec. IV-C) — plain definition      */
+/* ------------------------------------------------------------------------ */
+
+/* The planner validates one robot at a time against the paths of the robots
+ * planned before it, which act as moving obstacles (Sec. IV-C, PP-ST-RRT):
+ * Alg. 1's loop over robots for the obstacle and self checks keeps only the
+ * current robot, and its robot-robot loop keeps only the pairs of the current
+ * robot with the higher-priority ones.  Slot 0 of the query is the current
+ * robot, slots 1..n-1 the higher-priority robots.  valid_out = 1 iff no state
+ * has a collision of robot 0 with the obstacles or itself (check_env) or with
+ * any robot j >= 1.  Collisions among the higher-priority robots, and theirs
+ * with the obstacles, are not part of the check. */
+int orc_mv_prio(const orc_batch *b, const orc_robot *robots, const orc_env *env, int check_env, int q,
+                int *valid_out) {
+  int64_t T;
+  if (orc_query_T(b, robots, q, &T)) return -1;
+  qstate qs;
+  if (qstate_init(&qs, b, robots, q)) return -1;
+  for (int i = 0; i < qs.n; ++i)
+    if (check_self_pairs(qs.r[i])) { qstate_free(&qs); return -1; }
+  int valid = 1, rc = 0;
+  for (int64_t t = 0; valid && t <= T; ++t) {
+    if ((rc = qstate_fk(&qs, b, robots, q, T, t))) break;
+    if (check_env && env_self_min(&qs, env, 0) < 0.0) valid = 0;
+    for (int j = 1; j < qs.n && valid; ++j)
+      if (pair_min(&qs, 0, j) < 0.0) valid = 0;
+  }
+  qstate_free(&qs);
+  *valid_out = valid;
+  return rc;
+}
+
+/* Signed minimum clearance over the checks of orc_mv_prio (scan stops once
+ * the running minimum falls below stop_below). */
+int orc_mv_prio_min_clearance(const orc_batch *b, const orc_robot *robots, const orc_env *env,
+                              int check_env, int q, double stop_below, double *out) {
+  int64_t T;
+  if (orc_query_T(b, robots, q, &T)) return -1;
+  qstate qs;
+  if (qstate_init(&qs, b, robots, q)) return -1;
+  for (int i = 0; i < qs.n; ++i)
+    if (check_self_pairs(qs.r[i])) { qstate_free(&qs); return -1; }
+  double m = INFINITY;
+  int rc = 0;
+  for (int64_t t = 0; t <= T && !(m < stop_below); ++t) {
+    if ((rc = qstate_fk(&qs, b, robots, q, T, t))) break;
+    if (check_env) {
+      double v = env_self_min(&qs, env, 0);
+      if (v < m) m = v;
+    }
+    for (int j = 1; j < qs.n; ++j) {
+      double v = pair_min(&qs, 0, j);
+      if (v < m) m = v;
+    }
+  }
+  qstate_free(&qs);
+  *out = m;
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FFC (Alg. 2) — plain definition                                           */
 /* ------------------------------------------------------------------------ */
 
@@ -563,7 +624,7 @@ int orc_clearance(const orc_batch *b, const orc_robot *robots, const orc_env *en
 /* batch drivers (independent queries, static interleaved partition)         */
 /* ------------------------------------------------------------------------ */
 
-enum { JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T };
+enum { JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T, JOB_MV_PRIO, JOB_MINCLR_PRIO };
 
 typedef struct {
   int job;
@@ -608,6 +669,16 @@ static void *job_run(void *arg) {
       }
       case JOB_T:
         rc = orc_query_T(J->b, J->robots, q, (int64_t *)J->out + k);
+        break;
+      case JOB_MV_PRIO: {
+        int v = 0;
+        rc = orc_mv_prio(J->b, J->robots, e, J->check_env, q, &v);
+        ((uint8_t *)J->out)[k] = (uint8_t)v;
+        break;
+      }
+      case JOB_MINCLR_PRIO:
+        rc = orc_mv_prio_min_clearance(J->b, J->robots, e, J->check_env, q, J->param,
+                                       (double *)J->out + k);
         break;
     }
     if (rc && !J->rc) J->rc = rc;

@@ -26,7 +26,7 @@ LIB = Path(os.environ.get("MRV_ORACLE_LIB", HERE / "liboracle.so"))
 _lock = threading.Lock()
 _lib = None
 
-JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T = range(5)
+JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T, JOB_MV_PRIO, JOB_MINCLR_PRIO = range(7)
 
 
 def build(force: bool = False, src: Path = SRC, out: Path = None) -> Path:
@@ -167,19 +167,23 @@ class Oracle:
         return np.arange(self.w.batch.n_queries) if idx is None else np.asarray(idx)
 
     # -- public -------------------------------------------------------------
-    def mv(self, idx=None, check_env=None, threads=1):
+    def mv(self, idx=None, check_env=None, threads=1, priority=False):
+        # priority: the prioritized planner's MV (Sec. IV-C), slot 0 against
+        # the obstacles, itself and slots 1..n-1
         idx = self._idx(idx)
         ce = self.w.check_env if check_env is None else check_env
-        return self._run(JOB_MV, idx, np.zeros(len(idx), np.uint8), ce, threads=threads)
+        return self._run(JOB_MV_PRIO if priority else JOB_MV, idx, np.zeros(len(idx), np.uint8), ce,
+                         threads=threads)
 
     def ffc(self, idx=None, threads=1):
         idx = self._idx(idx)
         return self._run(JOB_FFC, idx, np.zeros((len(idx), 3), np.int32), threads=threads)
 
-    def mv_min_clearance(self, idx=None, check_env=None, stop_below=-np.inf, threads=1):
+    def mv_min_clearance(self, idx=None, check_env=None, stop_below=-np.inf, threads=1, priority=False):
         idx = self._idx(idx)
         ce = self.w.check_env if check_env is None else check_env
-        return self._run(JOB_MINCLR, idx, np.zeros(len(idx), np.float64), ce, stop_below, threads)
+        return self._run(JOB_MINCLR_PRIO if priority else JOB_MINCLR, idx, np.zeros(len(idx), np.float64), ce,
+                         stop_below, threads)
 
     def ffc_decidable(self, idx=None, margin=1e-4, threads=1):
         idx = self._idx(idx)

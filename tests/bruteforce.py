@@ -131,6 +131,26 @@ def mv_alg1(g: Geometry, W: int, hierarchical: bool, check_env: bool, packing: s
     return True
 
 
+def mv_alg1_prio(g: Geometry, W: int, check_env: bool, packing: str = "rake"):
+    """Alg. 1 as the prioritized planner modifies it (Sec. IV-C, PP-ST-RRT):
+    the robot loop of the obstacle / self step runs over the current robot
+    (slot 0) only, and the robot-robot loop over the pairs of the current
+    robot with each higher-priority robot (slots 1..n-1)."""
+    tt = g.T + 1
+    n = len(g.slots)
+    pack = rake if packing == "rake" else linear
+    for b in range(math.ceil(tt / W)):
+        if check_env:
+            for t in pack(tt, W, b):
+                if g.env_hit(t, 0):
+                    return False
+        for j in range(1, n):
+            for t in pack(tt, W, b):
+                if g.pair_hit(t, 0, j):
+                    return False
+    return True
+
+
 def ffc_alg2(g: Geometry, W: int):
     """Alg. 2: linear batches, return at a conflict on the batch's first
     timestep, otherwise the batch minimum over robot pairs (earliest pair on

@@ -40,6 +40,10 @@ MUTANTS = {
                                 "double v = orc_sphere_sphere(C + 3 * a, ra, co, 0.0);"),
     "base_ignored": ("frame[0] = mat_from34(r->base);", "frame[0] = mat_identity();"),
     "theta_offset_dropped": ("(double)row[3] + q[k - 1]", "q[k - 1]"),
+    "prio_pairs_chained": ("if (pair_min(&qs, 0, j) < 0.0) valid = 0;", "if (pair_min(&qs, j - 1, j) < 0.0) valid = 0;"),
+    "prio_env_other_robot": ("if (check_env && env_self_min(&qs, env, 0) < 0.0) valid = 0;",
+                             "if (check_env && env_self_min(&qs, env, qs.n - 1) < 0.0) valid = 0;"),
+    "prio_clearance_pairs": ("double v = pair_min(&qs, 0, j);", "double v = pair_min(&qs, j - 1, j);"),
 }
 
 PIN_ARGS = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",

@@ -402,3 +402,84 @@ def test_bruteforce_many_robots(seed):
         conf = BF.all_conflicts(g)
         assert tuple(ffc[q]) == (min(conf) if conf else (-1, -1, -1))
         assert BF.ffc_alg2(g, 4) == tuple(ffc[q])
+
+
+# ------------------------------------------- prioritized planner's MV variant
+
+def _discs_timed(paths, T, r=0.25, env=None):
+    """n disc robots, each on a straight timed motion of T steps."""
+    models = [W.disc_robot(r) for _ in paths]
+    bb = W.BatchBuilder(2, True)
+    bb.add(list(range(len(paths))), [np.array([s, g], np.float32) for s, g in paths], [[T]] * len(paths),
+           0, -1 if env is None else 0)
+    return W.Workload("discs", models, [] if env is None else [env], bb.build(0.05),
+                      env=-1 if env is None else 0, check_env=env is not None)
+
+
+def test_prio_closed_form_discs():
+    """Three discs on straight lines: the prioritized MV is invalid exactly
+    when disc 0 meets disc 1 or disc 2 (closed-form time of closest approach);
+    a meeting of discs 1 and 2 alone leaves it valid.  The full MV needs all
+    three pairs apart."""
+    rng = np.random.default_rng(31)
+    checked = seen_12_only = 0
+    for _ in range(300):
+        p = [tuple(rng.uniform(0, 4, 2).astype(np.float32) for _ in range(2)) for _ in range(3)]
+        T = int(rng.integers(5, 80))
+        cf = {}
+        for i, j in ((0, 1), (0, 2), (1, 2)):
+            cf[i, j] = _disc_closed_form(p[i][0], p[i][1], p[j][0], p[j][1], T, 0.5)
+        if min(c[1] for c in cf.values()) < 1e-6:
+            continue
+        w = _discs_timed(p, T)
+        o = O.Oracle(w)
+        prio_valid = cf[0, 1][0] < 0 and cf[0, 2][0] < 0
+        assert bool(o.mv(priority=True)[0]) == prio_valid
+        assert bool(o.mv()[0]) == (prio_valid and cf[1, 2][0] < 0)
+        lo = min(cf[0, 1][2], cf[0, 2][2])
+        hi = min(cf[k][2] + cf[k][3] / (2 * T) for k in ((0, 1), (0, 2)))
+        assert lo - 1e-9 <= o.mv_min_clearance(priority=True)[0] <= hi + 1e-9
+        seen_12_only += prio_valid and cf[1, 2][0] >= 0
+        checked += 1
+    assert checked > 250 and seen_12_only > 5
+
+
+def test_prio_obstacles_of_current_robot_only():
+    """With obstacles, only disc 0's contacts count: a box on disc 1's path
+    leaves the prioritized MV valid, the same box on disc 0's path does not."""
+    box = W.Env(np.zeros((0, 4), np.float32), np.array([[1.8, 1.8, -1.0, 2.2, 2.2, 1.0]], np.float32), "box")
+    through, aside = ((0.5, 2.0), (3.5, 2.0)), ((0.5, 5.0), (3.5, 5.0))
+    far = ((7.0, 8.0), (9.0, 8.0))
+    o = O.Oracle(_discs_timed([aside, through, far], 40, env=box))
+    assert bool(o.mv(priority=True)[0]) and not bool(o.mv()[0])
+    o = O.Oracle(_discs_timed([through, aside, far], 40, env=box))
+    assert not bool(o.mv(priority=True)[0]) and not bool(o.mv()[0])
+    assert bool(o.mv(priority=True, check_env=False)[0])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_prio_bruteforce_tiny(seed):
+    """The prioritized MV against Alg. 1 as Sec. IV-C modifies it, restated in
+    paper order with every lane width and packing, and its invariants: it
+    only drops checks (full valid => prioritized valid), equals the full MV
+    for two robots without obstacles, and does not depend on the order of the
+    higher-priority robots."""
+    w = tiny_workload(700 + seed, n_queries=10, timed=bool(seed % 2), max_robots=4)
+    o = O.Oracle(w)
+    full, full_ne = o.mv(), o.mv(check_env=False)
+    pr, pr_ne = o.mv(priority=True), o.mv(priority=True, check_env=False)
+    rng = np.random.default_rng(seed)
+    for q in range(w.batch.n_queries):
+        g = BF.Geometry(w, q)
+        for Wd in (1, 8, 32):
+            for pack in ("rake", "linear"):
+                assert BF.mv_alg1_prio(g, Wd, True, pack) == bool(pr[q])
+                assert BF.mv_alg1_prio(g, Wd, False, pack) == bool(pr_ne[q])
+        assert pr[q] >= full[q] and pr_ne[q] >= full_ne[q]
+        n = len(g.slots)
+        if n == 2:
+            assert pr_ne[q] == full_ne[q]
+        if n >= 3:
+            perm = [0] + list(rng.permutation(np.arange(1, n)))
+            wp = _permute(w, q, perm)
+            assert O.Oracle(wp).mv(priority=True)[0] == pr[q]
