@@ -272,6 +272,20 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
                             "kernel_ms": st["device_ms"], "tuning": tune}
+    # prioritized planning's edge checks (Sec. IV-C): 10k cage edges, one arm
+    # against the cage, itself and three higher-priority arms' timed paths
+    w = W.make_cage_priority(10000)
+    ba = ctx.bind(w).to("cuda")
+    tune = autotune(ctx, w, mrv.MRV_CHECK_ENV | mrv.MRV_PRIORITY, kind=0)
+    dt = timed(lambda: ctx.mv_validate(ba, flags=mrv.MRV_PRIORITY))
+    st = ctx.stats()
+    nvalid = int(ctx.mv_validate(ba, flags=mrv.MRV_PRIORITY).sum().item())
+    pq = per_query(w, lambda b: ctx.mv_validate(b, flags=mrv.MRV_PRIORITY | mrv.MRV_PER_QUERY_LAUNCH))
+    out["cage_priority_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
+                                "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
+                                "valid_total": f"{nvalid}/{w.batch.n_queries}",
+                                "effort_states": st["states_checked"] / max(1, st["states_available"]),
+                                "kernel_ms": st["device_ms"], "tuning": tune}
     # ragged teams, 1M mixed MV/FFC queries in one persistent graph launch
     w = W.make_ragged_teams(1_000_000)
     ba = ctx.bind(w).to("cuda")

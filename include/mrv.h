@@ -67,6 +67,14 @@ extern "C" {
                                       launch per query                      */
 #define MRV_NO_BROADPHASE 0x40u   /* test every sphere pair (no frame-level
                                      bounding-sphere culling); same results */
+#define MRV_PRIORITY 0x100u       /* MV of prioritized planning (PP-ST-RRT,
+                                     Sec. IV-C): slot 0 of each MV query is
+                                     the robot being planned, slots 1..n-1
+                                     robots of higher priority whose paths
+                                     act as moving obstacles.  The obstacle
+                                     and self checks run for slot 0 only and
+                                     the robot-robot checks for the pairs
+                                     (0, j) only.  FFC queries ignore it.   */
 #define MRV_LINEAR 0x80u          /* MV visits the states of a tile in the
                                      linear order t = 32 b + l (the map FFC
                                      uses, Sec. IV-B) instead of the rake
@@ -215,7 +223,8 @@ int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out
  * query's robots in slot order; each value is the minimum over the checks
  * that involve the sphere (other robots' spheres; obstacles and self pairs
  * when MRV_CHECK_ENV), +inf when none.  Pointer kinds follow the batch
- * flag. */
+ * flag; MRV_PRIORITY does not restrict it (every robot and pair is
+ * reported). */
 int mrv_clearance(mrv_ctx *ctx, const mrv_batch *batch, int32_t q, const int32_t *ts, int32_t nt,
                   float *out);
 

@@ -153,7 +153,8 @@ int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
   if (!b->q_robot_off || !b->slot_robot_id || !b->slot_wp_off || !b->waypoints)
     return fail(MRV_ERR_ARG, "missing batch array");
   if (b->flags & ~(uint32_t)(MRV_CHECK_ENV | MRV_HIERARCHICAL | MRV_EXHAUSTIVE | MRV_PTRS_ON_DEVICE | MRV_ASYNC |
-                             MRV_PER_QUERY_LAUNCH | MRV_NO_BROADPHASE | MRV_LINEAR))
+                             MRV_PER_QUERY_LAUNCH | MRV_NO_BROADPHASE | MRV_LINEAR |
+                             MRV_PRIORITY))
     return fail(MRV_ERR_ARG, "unknown flag bits 0x%x", b->flags);
   if ((b->flags & MRV_ASYNC) && !(b->flags & MRV_PTRS_ON_DEVICE))
     return fail(MRV_ERR_ARG, "MRV_ASYNC requires MRV_PTRS_ON_DEVICE");

@@ -64,6 +64,10 @@ static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 struct TileCtx {
   int q, T, n, M, nb, ffc, check_env, exhaustive, broad;
   int lin;                   // linear state order (FFC, or MV with MRV_LINEAR)
+  int prio;                  // prioritized MV: slot 0 against obstacles, itself and slots 1..n-1
+  int env_rows;              // spheres with obstacle checks: [0, env_rows)
+  int self_robots;           // robots with self checks: [0, self_robots)
+  int pair_robots;           // robots i whose pairs (i, j > i) are checked
   int self_blk;              // every robot's self pairs come as blocks
   int split, spt, nslices;
   int env_ns, env_nb;
@@ -184,7 +188,7 @@ __global__ void k_prep(BatchDev B) {
   int M = 0;
   bool all_point = true;
   int ms[MRV_MAX_ROBOTS];
-  long long self_total = 0;
+  long long self_total = 0, self0 = 0;
   float rho2 = 0.f;
   if (!err) {
     for (int i = 0; i < n; ++i) {
@@ -196,6 +200,7 @@ __global__ void k_prep(BatchDev B) {
       ms[i] = m.n_spheres;
       M += m.n_spheres;
       self_total += m.n_self;
+      if (i == 0) self0 = m.n_self;
       rho2 = fmaxf(rho2, m.r2max);
       if (m.kind != MRV_ROBOT_POINT) all_point = false;
       const int w0 = B.slot_wp_off[s], w1 = B.slot_wp_off[s + 1];
@@ -252,17 +257,21 @@ __global__ void k_prep(BatchDev B) {
     if (cte < need) cte = need;
     Q.cte = cte;
     Q.nchunks = (total + cte - 1) / cte;
+    // the prioritized MV checks slot 0 alone against the obstacles and
+    // itself, and only the pairs (0, j)
+    const bool prio = mv && (B.flags & MRV_PRIORITY);
     long long pt = 0;
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < (prio ? 1 : n); ++i)
       for (int j = i + 1; j < n; ++j) pt += (long long)ms[i] * ms[j];
     Q.pairtests = pt;
     long long et = 0, bt = 0;
     if (check_env) {
+      const int Me = prio ? ms[0] : M;
       if (env >= 0) {
-        et = (long long)M * B.envs[env].n_spheres;
-        bt = (long long)M * B.envs[env].n_aabbs;
+        et = (long long)Me * B.envs[env].n_spheres;
+        bt = (long long)Me * B.envs[env].n_aabbs;
       }
-      et += self_total;
+      et += prio ? self0 : self_total;
     }
     Q.envtests = et;
     Q.boxtests = bt;
@@ -471,7 +480,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   if (!C.ffc) {
     bool hit = false;
     if (valid && do_env && C.check_env) {
-      for (int a = 0; a < C.M; ++a) {
+      for (int a = 0; a < C.env_rows; ++a) {
         const float4 pa = PA[a * kWarp + lane];
         for (int o = 0; o < C.env_ns; ++o) {
           if (CLR) minclr = fminf(minclr, sph_clr(pa, C.env_s[o]));
@@ -483,7 +492,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
           else hit |= d2 < pa.w * pa.w;
         }
       }
-      for (int r = 0; r < C.n; ++r)
+      for (int r = 0; r < C.self_robots; ++r)
         for (int p = 0; p < S.rs[r].n_self; ++p) {
           const uint32_t sp = S.rs[r].self[p];
           const float4 x = PA[(S.off[r] + (int)(sp & 0xffffu)) * kWarp + lane];
@@ -493,7 +502,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
         }
     }
     if (valid && do_pairs)
-      for (int i = 0; i < C.n; ++i)
+      for (int i = 0; i < C.pair_robots; ++i)
         for (int a = S.off[i]; a < S.off[i + 1]; ++a) {
           const float4 pa = PA[a * kWarp + lane];
           for (int bb = S.off[i + 1]; bb < C.M; ++bb) {
@@ -629,9 +638,10 @@ __device__ bool box_rows(const float4 *P, int ra, int rb, const float4 *BL, cons
 
 // MV robot-robot checks at one state: robot i's rows against every sphere of
 // the robots after it
-__device__ bool pairs_mv(const float4 *P, const float *K, const int *off, int n, int M, int lane, float eps) {
+__device__ bool pairs_mv(const float4 *P, const float *K, const int *off, int n, int M, int lane, float eps,
+                         int row_robots) {
   bool hit = false;
-  for (int i = 0; i + 1 < n; ++i)
+  for (int i = 0; i + 1 < n && i < row_robots; ++i)
     hit |= rect_test(P, off[i], off[i + 1], P, K, off[i + 1], M, 0.f, 0.f, 0.f, eps, lane);
   return hit;
 }
@@ -652,7 +662,7 @@ __device__ unsigned pairs_ffc(const float4 *P, const float *K, const int *off, i
 // self-collision pairs (rectangles of the model, or its sparse pair list)
 __device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, const float *K, int lane, float cw2,
                        float eps) {
-  const int M = C.M;
+  const int M = C.env_rows;   // spheres with obstacle checks
   bool hit = false;
   if (C.env_ns) {
     const float epsw = kEpsU * (fmaxf(cw2, C.env_c2) + fmaxf(C.rho2, C.env_r2));
@@ -665,7 +675,7 @@ __device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, con
     hit |= box_rows(P, 0, M, S.BL, S.BH, nb_c, S.ox, S.oy, S.oz, lane);
     if (C.env_nb > nb_c) hit |= box_rows(P, 0, M, C.box_lo + nb_c, C.box_hi + nb_c, C.env_nb - nb_c, S.ox, S.oy, S.oz, lane);
   }
-  for (int r = 0; r < C.n; ++r) {
+  for (int r = 0; r < C.self_robots; ++r) {
     const int o = S.off[r];
     const int nr = S.rs[r].n_rects;
     if (nr > 0) {
@@ -737,7 +747,7 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float
     const int k = k0 + lane;
     const int i = k / kMaxLinks, u = k - i * kMaxLinks;   // constant divisor
     const float4 bu = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
-    if (bu.w >= 0.f) {
+    if (bu.w >= 0.f && i < C.pair_robots) {
       const int a0 = S.off[i] + S.rs[i].ls[u], a1 = S.off[i] + S.rs[i].ls[u + 1];
       for (int k2 = (i + 1) * kMaxLinks; k2 < nk; ++k2) {
         const float4 bv = S.BS[k2];
@@ -765,7 +775,7 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float
 __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, unsigned long long &ntests,
                           unsigned long long &nbox) {
   bool hit = false;
-  const int nk = C.n * kMaxLinks;
+  const int nk = C.self_robots * kMaxLinks;   // frames of the robots with obstacle checks
   const int ns_c = min(C.env_ns, kEnvCache), nb_c = min(C.env_nb, kBoxCache);
   for (int k0 = 0; k0 < nk; k0 += kWarp) {
     const int k = k0 + lane;
@@ -802,7 +812,7 @@ __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, 
   if (!C.exhaustive && __any_sync(0xffffffffu, hit)) return true;
   // self pairs, grouped by frame pair: lanes test the groups' bounding
   // spheres, then the warp walks the overlapping groups' pairs together
-  for (int r = 0; r < C.n; ++r) {
+  for (int r = 0; r < C.self_robots; ++r) {
     const ModelDev &md = *S.rs[r].md;
     const int o = S.off[r];
     const int ng = S.rs[r].n_groups;
@@ -1002,7 +1012,8 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
                                 bool do_pairs, BroadAcc &acc) {
   Cands &cl = S.u.b.cl;
   const float4 *P = S.u.b.P;
-  const int n = C.n, nk = n * kMaxLinks;
+  const int n = C.n;
+  const int nke = C.self_robots * kMaxLinks;   // frames with obstacle checks
   const bool exhaustive = C.exhaustive != 0, ffc = C.ffc != 0;
   if (lane == 0) {
     cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = 0;
@@ -1022,7 +1033,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
       const EnvDev &E = *C.env;
       const float glx = E.g_lo[0], gly = E.g_lo[1], glz = E.g_lo[2], gih = E.g_inv_h;
       const int gdx = E.g_dims[0], gdy = E.g_dims[1], gdz = E.g_dims[2];
-      for (int k = lane; k < nk; k += kWarp) {
+      for (int k = lane; k < nke; k += kWarp) {
         const float4 bl = S.BS[k];
         if (bl.w < 0.f) continue;
         const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
@@ -1086,7 +1097,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
     } else {
       // no grid: frames x obstacles, lane = (frame group lane & 3, obstacle group lane >> 2)
       const int fg = lane & 3, og = lane >> 2;
-      for (int k = fg; k < nk; k += 4) {
+      for (int k = fg; k < nke; k += 4) {
         const float4 bl = S.BS[k];
         if (bl.w < 0.f) continue;
         const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
@@ -1111,7 +1122,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
       }
       const uint32_t ns_l = (uint32_t)max(0, (env_ns - og + 7) >> 3), nb_l = (uint32_t)max(0, (env_nb - og + 7) >> 3);
       int nf = 0;   // bounding spheres of this lane's frame group
-      for (int k = fg; k < nk; k += 4) nf += S.BS[k].w >= 0.f;
+      for (int k = fg; k < nke; k += 4) nf += S.BS[k].w >= 0.f;
       acc.tests += (uint32_t)nf * (ns_l + nb_l);
       acc.boxes += (uint32_t)nf * nb_l;
     }
@@ -1141,7 +1152,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
         if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
       }
       // self-pair groups by their frames' bounding spheres
-      for (int r = 0; r < n; ++r) {
+      for (int r = 0; r < C.self_robots; ++r) {
         const int4 *groups = S.rs[r].md->self_groups;
         const int ng = S.rs[r].n_groups;
         for (int g = lane; g < ng; g += kWarp) {
@@ -1254,7 +1265,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
   }
   __syncwarp();
   const int npair = n * (n - 1) / 2;
-  const int ftot = S.rpf[npair];
+  const int ftot = S.rpf[C.prio ? n - 1 : npair];   // the table lists the pairs (0, j) first
   {
     int it = 0;
     for (int f = lane; f < ftot; f += kWarp) {
@@ -1342,23 +1353,23 @@ __device__ __forceinline__ void flush_acc(TileCtx &C, BroadAcc &acc, int lane) {
 // clearance mode (exhaustive MV with min_clearance_out): direct formulas
 __device__ void clr_state(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, bool do_env, bool do_pairs,
                           float &minclr) {
-  const int M = C.M, n = C.n;
+  const int M = C.M;
   if (do_env && C.check_env) {
-    for (int a = lane; a < M; a += kWarp) {
+    for (int a = lane; a < C.env_rows; a += kWarp) {
       const float4 pa = P[a];
       const float4 w = make_float4(pa.x + S.ox, pa.y + S.oy, pa.z + S.oz, pa.w);
       for (int o = 0; o < C.env_ns; ++o) minclr = fminf(minclr, sph_clr(w, C.env_s[o]));
       for (int o = 0; o < C.env_nb; ++o)
         minclr = fminf(minclr, sqrtf(box_d2(w.x, w.y, w.z, C.box_lo[o], C.box_hi[o])) - w.w);
     }
-    for (int r = 0; r < n; ++r)
+    for (int r = 0; r < C.self_robots; ++r)
       for (int p = lane; p < S.rs[r].n_self; p += kWarp) {
         const uint32_t e = S.rs[r].self[p];
         minclr = fminf(minclr, sph_clr(P[S.off[r] + (e & 0xffffu)], P[S.off[r] + (e >> 16)]));
       }
   }
   if (do_pairs)
-    for (int a = lane; a < S.off[n - 1]; a += kWarp) {
+    for (int a = lane; a < S.off[C.pair_robots]; a += kWarp) {
       int r = 0;
       while (a >= S.off[r + 1]) ++r;
       const float4 pa = P[a];
@@ -1475,7 +1486,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
           C.btests += (unsigned long long)C.boxtests;
         }
         if (do_pairs) {
-          if (!CLR) hit |= pairs_mv(P, K, S.off, n, M, lane, eps);
+          if (!CLR) hit |= pairs_mv(P, K, S.off, n, M, lane, eps, C.pair_robots);
           if (lane == 0) C.tests += (unsigned long long)C.pairtests;
         }
         if (__any_sync(0xffffffffu, hit)) {
@@ -1524,6 +1535,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
   C.split = Q.split; C.spt = Q.spt; C.nslices = Q.nslices;
   C.broad = (B.flags & MRV_NO_BROADPHASE) ? 0 : 1;
   C.lin = (C.ffc || (B.flags & MRV_LINEAR)) ? 1 : 0;
+  C.prio = (!C.ffc && (B.flags & MRV_PRIORITY)) ? 1 : 0;
   C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
   C.env = nullptr;
   C.env_c2 = 0.f; C.env_r2 = 0.f; C.rho2 = Q.rho2;
@@ -1556,6 +1568,9 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     int acc = 0;
     S.off[0] = 0;
     for (int r = 0; r < C.n; ++r) { acc += S.rs[r].m; S.off[r + 1] = acc; }
+    C.env_rows = C.prio ? S.off[1] : C.M;
+    C.self_robots = C.prio ? 1 : C.n;
+    C.pair_robots = C.prio ? 1 : C.n - 1;
     int blk = 1;
     for (int r = 0; r < C.n; ++r) blk &= (S.rs[r].n_groups == 0 || S.rs[r].masks != nullptr);
     C.self_blk = blk;

@@ -406,6 +406,49 @@ def make_cage_ffc(n_queries: int = 100000, query_seed: int = 204, fixtures: Opti
                     meta={"robots": 4})
 
 
+def make_cage_priority(n_queries: int = 10000, query_seed: int = 207, fixtures: Optional[dict] = None,
+                       env_seed: int = 103, seg_range=(1, 3)) -> Workload:
+    """Edge checks of prioritized planning (Sec. IV-C) in the cage: per query
+    one arm (slot 0, drawn uniformly) moves along a start->goal edge between
+    env+self valid configurations at 1/32 rad per step (L steps), and the
+    three other arms (slots 1..3, higher priority) follow timed paths of 1-3
+    segments through valid configurations spanning the same L steps.  To be
+    run with MRV_PRIORITY: slot 0 against the cage, itself and slots 1..3."""
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    models = cage_arms(fx)
+    env = cage_env(env_seed)
+    rng = np.random.default_rng(query_seed)
+    pools = fx["endpoint_pool"]                      # (4, P, 7)
+    P = pools.shape[1]
+    cur = rng.integers(0, 4, n_queries)
+    wps, steps, slot_robot, slot_wp_off = [], [], [], [0]
+    for q in range(n_queries):
+        c = int(cur[q])
+        s, g = pools[c, rng.integers(0, P, 2)]
+        d = float(np.linalg.norm(g.astype(np.float64) - s.astype(np.float64)))
+        L = max(1, math.ceil(d * 32.0))
+        order = [c] + [a for a in range(4) if a != c]
+        for k, a in enumerate(order):
+            if k == 0:
+                path, st = [s, g], [L]
+            else:
+                ns = int(rng.integers(seg_range[0], seg_range[1] + 1))
+                ns = min(ns, L)
+                cuts = np.sort(rng.choice(np.arange(1, L), ns - 1, replace=False)) if ns > 1 else np.zeros(0, int)
+                st = list(np.diff(np.concatenate([[0], cuts, [L]])).astype(int))
+                path = list(pools[a, rng.integers(0, P, ns + 1)])
+            wps.extend(path)
+            steps.extend(st + [0])
+            slot_robot.append(a)
+            slot_wp_off.append(slot_wp_off[-1] + len(path))
+    b = Batch(np.arange(0, n_queries * 4 + 1, 4, dtype=np.int32), np.asarray(slot_robot, np.int32),
+              np.asarray(slot_wp_off, np.int32), np.asarray(wps, np.float32).reshape(-1, 7),
+              np.asarray(steps, np.int32), 0.0, np.full(n_queries, KIND_MV, np.uint8),
+              np.zeros(n_queries, np.int32))
+    return Workload("cage_priority", models, [env], b, env=0, check_env=True,
+                    meta={"robots": 4, "priority": True})
+
+
 TEAM_ARM_BASES = [(4.4, 5.0, 0.0), (5.6, 5.0, math.pi)]
 TEAM_PAD = (3.8, 3.8, 6.2, 6.2)
 

@@ -18,12 +18,13 @@ CLR_TOL = 1e-5       # m: absolute tolerance on clearance values
 THREADS = os.cpu_count() or 1
 
 
-def check_mv(o, gpu_valid, idx=None, check_env=True, margin=MARGIN):
-    """Returns (n_checked, n_undecidable)."""
+def check_mv(o, gpu_valid, idx=None, check_env=True, margin=MARGIN, priority=False):
+    """Returns (n_checked, n_undecidable).  priority: against the prioritized
+    planner's MV (slot 0 against the obstacles, itself and slots 1..n-1)."""
     n = o.w.batch.n_queries
     idx = np.arange(n) if idx is None else np.asarray(idx)
     g = np.asarray(gpu_valid)[idx].astype(bool) if len(gpu_valid) == n else np.asarray(gpu_valid).astype(bool)
-    m = o.mv_min_clearance(idx, check_env=check_env, stop_below=-margin, threads=THREADS)
+    m = o.mv_min_clearance(idx, check_env=check_env, stop_below=-margin, threads=THREADS, priority=priority)
     exp = m >= 0
     dec = np.abs(m) > margin
     bad = np.nonzero(dec & (g != exp))[0]
