@@ -109,9 +109,11 @@ struct WarpSmem {
   float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
   float EK[kEnvCache];       // their |c|^2 - r^2
   float4 BL[kBoxCache], BH[kBoxCache];   // obstacle boxes
-  // robot pairs i < j of the query (i << 4 | j) and the exclusive prefix of
-  // their frame-pair counts n_links_i x n_links_j
-  uint8_t rp[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2];
+  // robot pairs i < j of the query, i | j << 4 | n_links_j << 8 | m << 16
+  // with m = ceil(4096 / n_links_j) (frame pair g of the pair is (g m >> 12,
+  // g mod n_links_j), exact for g < 100), and the exclusive prefix of their
+  // frame-pair counts n_links_i x n_links_j
+  uint32_t rp[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2];
   int16_t rpf[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2 + 2];
   float4 BS[MRV_MAX_ROBOTS * kMaxLinks];  // per (robot, frame) bounding sphere at the
                                           // current state (center relative to o; w < 0: none)
@@ -398,6 +400,45 @@ __device__ __noinline__ void chain_frames(const ModelDev &m, const float *q, flo
     p2[r] = p[r] + R[3 * r + 0] * m.flange[3] + R[3 * r + 1] * m.flange[7] + R[3 * r + 2] * m.flange[11];
   }
   store_frame(X, m.dof + 1, R2, p2);
+}
+
+// One row (r = 0, 1, 2) of every link frame of a chain.  A joint mixes the
+// columns of each row of the 3x4 transform but never its rows, so the rows
+// evolve independently through the base, the joints and the flange, and three
+// lanes can share a chain (the same arithmetic as chain_frames, row by row).
+__device__ __forceinline__ void store_row(float *X, int link, int r, float x, float y, float z, float p) {
+  *reinterpret_cast<float4 *>(X + link * 12 + 4 * r) = make_float4(x, y, z, p);
+}
+
+__device__ __noinline__ void chain_row(const ModelDev &m, const float *q, float *X, int r) {
+  float x = m.base[4 * r + 0], y = m.base[4 * r + 1], z = m.base[4 * r + 2], p = m.base[4 * r + 3];
+  store_row(X, 0, r, x, y, z, p);
+  if (m.kind == MRV_ROBOT_POINT) {
+    const float zz = m.dof == 2 ? m.point_z : q[2];
+    p = fmaf(x, q[0], fmaf(y, q[1], fmaf(z, zz, p)));
+    store_row(X, 1, r, x, y, z, p);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < MRV_MAX_DOF; ++k) {
+    if (k < m.dof) {
+      const float ca = m.dh[k][0], sa = m.dh[k][1], a = m.dh[k][2], d = m.dh[k][3], th0 = m.dh[k][4];
+      float s, c;
+      sincosf(th0 + q[k], &s, &c);
+      const float u = ca * y + sa * z;
+      const float v = ca * z - sa * y;
+      p = fmaf(a, x, fmaf(d, v, p));
+      const float nx = c * x + s * u, ny = c * u - s * x;
+      x = nx;
+      y = ny;
+      z = v;
+      store_row(X, k + 1, r, x, y, z, p);
+    }
+  }
+  // flange frame dof+1 = frame dof * F
+  const float *F = m.flange;
+  store_row(X, m.dof + 1, r, x * F[0] + y * F[4] + z * F[8], x * F[1] + y * F[5] + z * F[9],
+            x * F[2] + y * F[6] + z * F[10], p + x * F[3] + y * F[7] + z * F[11]);
 }
 
 // direct forms: |a - b|^2 < (ra + rb)^2, clearance |a - b| - ra - rb
@@ -1270,10 +1311,10 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
     int it = 0;
     for (int f = lane; f < ftot; f += kWarp) {
       while (S.rpf[it + 1] <= f) ++it;
-      const int i = S.rp[it] >> 4, j = S.rp[it] & 15;
-      const int nj = S.rs[j].n_links, g = f - S.rpf[it];
-      const int u = (int)(((float)g + 0.5f) * __frcp_rn((float)nj));   // g < 100: exact
-      const int v = g - u * nj;
+      const uint32_t e = S.rp[it];
+      const int i = (int)(e & 15u), j = (int)((e >> 4) & 15u), nj = (int)((e >> 8) & 15u);
+      const int g = f - S.rpf[it];
+      const int u = (g * (int)(e >> 16)) >> 12, v = g - u * nj;
       const int k = i * kMaxLinks + u, k2 = j * kMaxLinks + v;
       const float4 bu = S.BS[k], bv = S.BS[k2];
       if (bu.w < 0.f || bv.w < 0.f) continue;
@@ -1390,16 +1431,17 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   BroadAcc acc = {0u, 0u, 0u};
   for (int j0 = 0; j0 < C.spt; j0 += CS) {
     if (slice_state(C, k, j0) > C.T) break;   // states grow with j in both packings
-    // (state, robot) chains
-    if (lane < CS * n) {
-      const int j = j0 + lane / n, r = lane % n;
+    // (state, robot) chains, three lanes per chain (one row of its frames each)
+    if (lane < 3 * CS * n) {
+      const int c = lane / 3, row = lane - 3 * c;
+      const int j = j0 + c / n, r = c % n;
       if (j < C.spt) {
         const int t = slice_state(C, k, j);
         if (t <= C.T) {
           const RobotSlot &rs = S.rs[r];
           float q[MRV_MAX_DOF];
           interp(B, rs.w0, rs.w1, rs.dof, t, q);
-          chain_frames(B.models[rs.mdl], q, xf + lane * (kMaxLinks * 12));
+          chain_row(B.models[rs.mdl], q, xf + c * (kMaxLinks * 12), row);
         }
       }
     }
@@ -1577,7 +1619,8 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     int p = 0, f = 0;
     for (int i = 0; i < C.n; ++i)
       for (int j = i + 1; j < C.n; ++j) {
-        S.rp[p] = (uint8_t)(i << 4 | j);
+        const int nj = S.rs[j].n_links;
+        S.rp[p] = (uint32_t)(i | j << 4 | nj << 8) | ((uint32_t)((4096 + nj - 1) / nj) << 16);
         S.rpf[p] = (int16_t)f;
         f += S.rs[i].n_links * S.rs[j].n_links;
         ++p;
