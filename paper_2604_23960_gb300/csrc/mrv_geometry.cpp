@@ -112,7 +112,7 @@ PreparedModel prepare_model(int n_links, int m, const int32_t *link, const float
       P.self_masks[first_mask + (x - P.link_start[rf])] |= 1u << (y - P.link_start[cf]);
     }
     P.self_blocks.insert(P.self_blocks.end(),
-                         {P.link_start[rf], P.link_start[cf], nr | (nc << 16), first_mask});
+                         {P.link_start[rf], P.link_start[cf], nr | (nc << 16) | (cf << 24) | (rf << 28), first_mask});
   }
   if (!ok) {
     P.self_blocks.clear();

@@ -31,8 +31,9 @@ struct PreparedModel {
   // the same pairs per group as a block: rows = the spheres of the frame with
   // more of them, columns = the other frame's (at most 32), one bit mask of
   // listed partners per row.  n_groups x 4: first row sphere, first column
-  // sphere, rows | columns << 16, first mask.  Empty when a group's smaller
-  // frame holds more than 32 spheres.
+  // sphere, rows | columns << 16 | column frame << 24 | row frame << 28,
+  // first mask.  Empty when a group's smaller frame holds more than 32
+  // spheres (frames are below 16: at most MRV_MAX_DOF + 2 of them).
   std::vector<int32_t> self_blocks;
   std::vector<uint32_t> self_masks;
 };

@@ -90,7 +90,8 @@ struct Cands {
   uint32_t ec[kCand];        // frame slot << 24 | obstacle sphere
   uint32_t bc[kCand];        // frame slot << 24 | obstacle box
   uint32_t sc[kCand];        // self-pair group: robot << 16 | its first pair
-  uint16_t scn[kCand];       // ... and its pair count
+  uint16_t scn[kCand];       // ... and its pair count (blocks: first row mask)
+  uint8_t sck[kCand];        // blocks: frame slot of the column frame
   int32_t pf[kCand + 1];     // exclusive prefix of the tests of the list being resolved
   int32_t np, ne, nb, ns, overflow, pad;
   uint32_t need[3], placed[3];
@@ -104,6 +105,8 @@ struct WarpSmem {
   TileCtx ctx;               // the current work item's query parameters
   RobotSlot rs[MRV_MAX_ROBOTS];
   int32_t off[MRV_MAX_ROBOTS + 1];
+  int32_t seg[MRV_MAX_ROBOTS];   // per robot: waypoint index of the segment of the
+                                 // latest FK round (states grow within a slice)
   float ox, oy, oz;          // origin of the relative frame (world)
   int32_t pad[4];
   float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
@@ -344,6 +347,42 @@ __device__ __forceinline__ void interp(const BatchDev &B, int w0, int w1, int do
     if (j < dof) q[j] = fmaf(g[j] - a[j], f, a[j]);
 }
 
+// interp from a segment hint: states only grow within a slice, so the search
+// starts at the segment of the previous round (a few linear steps, then a
+// binary search if still behind); *lo_out = the segment used (w1 - 1 past the
+// end of the path)
+__device__ __forceinline__ void interp_from(const BatchDev &B, int w0, int w1, int dof, int t, int hint, float *q,
+                                            int *lo_out) {
+  const int last = w1 - 1;
+  const int *tau = B.slot_tau;
+  if (t >= tau[last]) {
+    const float *a = B.waypoints + (size_t)last * B.wp_stride;
+#pragma unroll
+    for (int j = 0; j < MRV_MAX_DOF; ++j)
+      if (j < dof) q[j] = a[j];
+    *lo_out = last;
+    return;
+  }
+  int lo = (hint >= w0 && hint < last && tau[hint] <= t) ? hint : w0;
+  for (int s = 0; s < 4 && tau[lo + 1] <= t; ++s) ++lo;
+  if (tau[lo + 1] <= t) {
+    int hi = last - 1;
+    ++lo;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tau[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+  }
+  *lo_out = lo;
+  const float f = (float)(t - tau[lo]) / (float)(tau[lo + 1] - tau[lo]);
+  const float *a = B.waypoints + (size_t)lo * B.wp_stride;
+  const float *g = a + B.wp_stride;
+#pragma unroll
+  for (int j = 0; j < MRV_MAX_DOF; ++j)
+    if (j < dof) q[j] = fmaf(g[j] - a[j], f, a[j]);
+}
+
 __device__ __forceinline__ void store_frame(float *X, int link, const float *R, const float *p) {
   float *o = X + link * 12;
   o[0] = R[0]; o[1] = R[1]; o[2] = R[2]; o[3] = p[0];
@@ -491,6 +530,26 @@ __device__ __forceinline__ int slice_state(const TileCtx &C, int k, int j) {
   if (C.lin) return k * C.spt + j;
   const int b = k / C.split, p = k - b * C.split;
   return b + C.nb * (p + C.split * j);
+}
+
+// Position jj of a slice's visiting order -> its state index j.  MV in the
+// rake order visits the middle of the slice first (m, m-1, m+1, m-2, ...):
+// the slice's states are spread over the whole motion, and a motion between
+// valid configurations collides inside it rather than at its ends, so the
+// first collision is met after fewer states; the verdict does not depend on
+// the order.  FFC and the linear map keep increasing states.
+__device__ __forceinline__ int slot_j(const TileCtx &C, int jj, int nvalid) {
+  if (C.lin) return jj;
+  const int m = nvalid >> 1;   // a permutation of 0..nvalid-1 for every nvalid >= 1
+  return (jj & 1) ? m - 1 - (jj >> 1) : m + (jj >> 1);
+}
+
+// number of states of slice k that lie in 0..T (its states grow with j)
+__device__ __forceinline__ int slice_valid(const TileCtx &C, int k) {
+  const int t0 = slice_state(C, k, 0);
+  if (t0 > C.T) return 0;
+  const int step = C.lin ? 1 : C.nb * C.split;
+  return min(C.spt, (C.T - t0) / step + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1253,6 +1312,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
             c = Bk.z & 0xffff;
             cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 9) | ((uint32_t)r << 24);
             cl.scn[i] = (uint16_t)Bk.w;
+            cl.sck[i] = (uint8_t)(r * kMaxLinks + ((Bk.z >> 24) & 15));
           }
           base = scan_chunk(cl.pf, i, ns, c, base, lane);
         }
@@ -1265,6 +1325,10 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
           const uint32_t v = cl.sc[it];
           const int row = f - cl.pf[it];
           const float4 pa = P[(int)(v & 511u) + row];
+          // a row sphere clear of the column frame's bounding sphere is clear
+          // of every column sphere
+          nt += 1;
+          if (!sph_hit(pa, S.BS[cl.sck[it]])) continue;
           const float4 *Pc = P + ((v >> 9) & 511u);
           uint32_t mk = __ldg(&S.rs[v >> 24].masks[cl.scn[it] + row]);
           nt += (uint32_t)__popc(mk);
@@ -1443,31 +1507,28 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   const bool need_env = do_env && C.check_env;
   int found = C.ffc ? 0x7fffffff : 0;
   BroadAcc acc = {0u, 0u, 0u};
-  for (int j0 = 0; j0 < C.spt; j0 += CS) {
-    if (slice_state(C, k, j0) > C.T) break;   // states grow with j in both packings
+  const int nv = slice_valid(C, k);   // positions 0..nv-1 of the visiting order
+  for (int j0 = 0; j0 < nv; j0 += CS) {
     // (state, robot) chains, three lanes per chain (one row of its frames each)
     if (lane < 3 * CS * n) {
       const int c = lane / 3, row = lane - 3 * c;
-      const int j = j0 + c / n, r = c % n;
-      if (j < C.spt) {
-        const int t = slice_state(C, k, j);
+      const int jj = j0 + c / n, r = c % n;
+      if (jj < nv) {
+        const int t = slice_state(C, k, slot_j(C, jj, nv));
         if (t <= C.T) {
           const RobotSlot &rs = S.rs[r];
           float q[MRV_MAX_DOF];
-          interp(B, rs.w0, rs.w1, rs.dof, t, q);
+          int lo;
+          interp_from(B, rs.w0, rs.w1, rs.dof, t, S.seg[r], q, &lo);
           chain_row(B.models[rs.mdl], q, xf + c * (kMaxLinks * 12), row);
+          if (row == 0) atomicMax(&S.seg[r], lo);
         }
       }
     }
-    if (lane == 0) {   // FK chains of this round (statistics)
-      int ns = 0;
-      for (int j = j0; j < j0 + CS && j < C.spt && slice_state(C, k, j) <= C.T; ++j) ++ns;
-      C.chains += (unsigned long long)(ns * n);
-    }
+    if (lane == 0) C.chains += (unsigned long long)(min(CS, nv - j0) * n);   // FK chains (statistics)
     __syncwarp();
-    for (int j = j0; j < j0 + CS && j < C.spt; ++j) {
-      const int t = slice_state(C, k, j);
-      if (t > C.T) break;
+    for (int j = j0; j < j0 + CS && j < nv; ++j) {
+      const int t = slice_state(C, k, slot_j(C, j, nv));
       if (lane == 0 && do_env) C.states += 1;   // hierarchical order: counted in the first phase
       if (!CLR && C.broad) {
         // frame-level broadphase; spheres are placed only for the frames whose
@@ -1617,6 +1678,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
 #pragma unroll
     for (int l = 0; l < kMaxLinks + 2; ++l) rs.ls[l] = (int16_t)(l <= m.n_links ? m.link_start[l] : m.n_spheres);
     S.rs[lane] = rs;
+    S.seg[lane] = rs.w0;
     if (lane == 0) { S.ox = m.base[3]; S.oy = m.base[7]; S.oz = m.base[11]; }
   }
   __syncwarp();

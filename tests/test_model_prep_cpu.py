@@ -109,9 +109,11 @@ def check_blocks(d, g, got, start):
         return
     assert len(blocks) == len(g)
     for (u, v, s0, cnt), (r0, c0, rc, m0) in zip(g, blocks):
-        nr, nc = rc & 0xffff, rc >> 16
+        rc &= 0xffffffff
+        nr, nc, cf, rf = rc & 0xffff, (rc >> 16) & 0xff, (rc >> 24) & 0xf, rc >> 28
         assert nc <= 32 and nr >= nc
         assert {(r0, nr), (c0, nc)} == {(start[u], counts[u]), (start[v], counts[v])}
+        assert {rf, cf} == {u, v} and (r0, c0) == (start[rf], start[cf])
         listed = set()
         for row in range(nr):
             for c in range(nc):
