@@ -67,8 +67,8 @@ MAKERS = None
 # DRAM bytes of one k_main launch of the benchmark step, from an ncu capture
 # (profiles/k_main_cage_mv_traffic.md), valid for the kernel source it was
 # taken on; any other source reports null
-TRAFFIC = {"kernel_sha256": "1df4a2785b5a7758c44093ff6fe870e1d1e127ea810f92628ffaa9f6f3f1687e",
-           "bytes": 4209664 + 1024}
+TRAFFIC = {"kernel_sha256": "6794bc9873f3146752d7a9a732ac0bea66b01466ffddc768dfeb67d3287ff469",
+           "bytes": 4119552 + 768}
 
 
 def traffic_per_launch():
