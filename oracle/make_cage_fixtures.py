@@ -12,8 +12,15 @@ Writes ``tests/golden/cage_fixtures.npz`` with
                  float32        joint limits that are env+self valid with at
                                 least 1 mm clearance (the paper samples motions
                                 with valid endpoints, Sec. IV-A1).
+With --cage8 it writes ``tests/golden/cage8_fixtures.npz`` instead:
+  endpoint_pool  (8, 1024, 7)   per arm of the floor- and ceiling-mounted
+                 float32        8-arm team, configurations uniform in the joint
+                                limits that are valid against the cylinder cage
+                                and themselves with at least 1 mm clearance
+                                (self pairs from cage_fixtures.npz).
 Only the FP64 oracle evaluates geometry here.  Seeds: 301 (pair screening),
-302 (endpoint pools).  Usage: python oracle/make_cage_fixtures.py
+302 (endpoint pools), 303 (8-arm endpoint pools).
+Usage: python oracle/make_cage_fixtures.py [--cage8]
 """
 from __future__ import annotations
 
@@ -30,6 +37,7 @@ from oracle import oracle as O  # noqa: E402
 from paper_2604_23960_gb300 import workloads as W  # noqa: E402
 
 OUT = ROOT / "tests" / "golden" / "cage_fixtures.npz"
+OUT8 = ROOT / "tests" / "golden" / "cage8_fixtures.npz"
 POOL = 1024
 
 
@@ -55,14 +63,14 @@ def screen_self_pairs(seed: int = 301, n_cfg: int = 256, max_rate: float = 0.05,
     return cand[keep].astype(np.int32)
 
 
-def endpoint_pools(self_pairs, seed: int = 302, pool: int = POOL, chunk: int = 4096):
+def endpoint_pools(self_pairs, seed: int = 302, pool: int = POOL, chunk: int = 4096, arms=None, env=None):
     fx = {"self_pairs": self_pairs}
-    arms = W.cage_arms(fx)
-    env = W.cage_env()
+    arms = W.cage_arms(fx) if arms is None else arms
+    env = W.cage_env() if env is None else env
     rng = np.random.default_rng(seed)
     pools = []
     threads = os.cpu_count() or 1
-    for k in range(4):
+    for k in range(len(arms)):
         got = []
         while sum(len(g) for g in got) < pool:
             cfg = rng.uniform(W.PANDA_LO, W.PANDA_HI, (chunk, 7)).astype(np.float32)
@@ -83,5 +91,15 @@ def main():
     print(f"wrote {OUT}: {len(sp)} self pairs, endpoint pools {pools.shape}")
 
 
+def main_cage8():
+    sp = W.load_cage_fixtures()["self_pairs"]
+    pools = endpoint_pools(sp, seed=303, arms=W.cage8_arms({"self_pairs": sp}), env=W.cage_env_cyl())
+    np.savez_compressed(OUT8, endpoint_pool=pools)
+    print(f"wrote {OUT8}: endpoint pools {pools.shape}")
+
+
 if __name__ == "__main__":
-    main()
+    if "--cage8" in sys.argv[1:]:
+        main_cage8()
+    else:
+        main()

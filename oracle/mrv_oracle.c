@@ -24,11 +24,13 @@
  *   - SpheresFK: robot configuration -> world sphere centers through the
  *     kinematic chain (Sec. II-B, Sec. III-A); modified (Craig) DH is used:
  *       X_k = X_{k-1} RotX(alpha_k) TransX(a_k) RotZ(theta_k + q_k) TransZ(d_k).
- *   - CC: robot vs obstacle spheres and boxes and robot self-collision
+ *   - CC: robot vs obstacle spheres, boxes and cylinders and robot self-collision
  *     (Alg. 1, robot-obstacle step), robot vs robot sphere sets (Alg. 1,
  *     robot-robot step; Alg. 2).  Collision iff clearance < 0 with
  *       sphere-sphere clearance = |c_a - c_b| - r_a - r_b,
- *       sphere-box clearance    = dist(c, box) - r   (dist = 0 inside).
+ *       sphere-box clearance    = dist(c, box) - r   (dist = 0 inside),
+ *       sphere-cylinder clearance = dist(c, cylinder) - r (solid, flat caps;
+ *       the obstacle kind of the paper's Cage scenario, Sec. V-A).
  *   - MV (Alg. 1): invalid iff some state has an env/self collision (when
  *     check_environment is set) or a robot-robot collision.
  *   - FFC (Alg. 2): the lexicographically smallest (t, i, j), i < j, with
@@ -69,6 +71,8 @@ typedef struct {
   const float *spheres;  /* n x 4 */
   int32_t n_aabbs;
   const float *aabbs;    /* n x 6: lo xyz, hi xyz */
+  int32_t n_cylinders;
+  const float *cylinders; /* n x 7: axis end a xyz, axis end b xyz, radius */
 } orc_env;
 
 typedef struct {
@@ -201,6 +205,33 @@ double orc_sphere_box(const double *c, double r, const float *box) {
   return sqrt(s) - r;
 }
 
+/* Signed clearance between a sphere and a solid finite cylinder with flat
+ * caps, axis from a to b, radius rho: distance from the center to the solid
+ * (0 inside) minus r.  With s the center's coordinate along the unit axis
+ * from a and d its distance from the axis line, the nearest point of the
+ * solid clamps s to [0, L] and d to [0, rho], so the distance is
+ * sqrt(excess(s)^2 + excess(d)^2). */
+double orc_sphere_cylinder(const double *c, double r, const float *cyl) {
+  double u[3], w[3], L = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    u[k] = (double)cyl[3 + k] - (double)cyl[k];
+    w[k] = c[k] - (double)cyl[k];
+    L += u[k] * u[k];
+  }
+  L = sqrt(L);
+  for (int k = 0; k < 3; ++k) u[k] /= L;
+  const double s = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
+  double d2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double p = w[k] - s * u[k];
+    d2 += p * p;
+  }
+  const double d = sqrt(d2), rho = cyl[6];
+  const double es = s < 0.0 ? -s : (s > L ? s - L : 0.0);
+  const double ed = d > rho ? d - rho : 0.0;
+  return sqrt(es * es + ed * ed) - r;
+}
+
 /* ------------------------------------------------------------------------ */
 /* discretisation (Sec. IV-A3) and padding (Sec. III-A)                      */
 /* ------------------------------------------------------------------------ */
@@ -329,6 +360,10 @@ static double env_self_min(const qstate *qs, const orc_env *e, int i) {
       }
       for (int o = 0; o < e->n_aabbs; ++o) {
         double v = orc_sphere_box(C + 3 * a, ra, e->aabbs + 6 * o);
+        if (v < m) m = v;
+      }
+      for (int o = 0; o < e->n_cylinders; ++o) {
+        double v = orc_sphere_cylinder(C + 3 * a, ra, e->cylinders + 7 * o);
         if (v < m) m = v;
       }
     }
@@ -600,6 +635,10 @@ int orc_clearance(const orc_batch *b, const orc_robot *robots, const orc_env *en
             }
             for (int s = 0; s < env->n_aabbs; ++s) {
               double v = orc_sphere_box(ca, ra, env->aabbs + 6 * s);
+              if (v < m) m = v;
+            }
+            for (int s = 0; s < env->n_cylinders; ++s) {
+              double v = orc_sphere_cylinder(ca, ra, env->cylinders + 7 * s);
               if (v < m) m = v;
             }
           }

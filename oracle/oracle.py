@@ -54,7 +54,7 @@ class Robot(C.Structure):
 
 class EnvS(C.Structure):
     _fields_ = [("n_spheres", C.c_int32), ("spheres", C.c_void_p), ("n_aabbs", C.c_int32),
-                ("aabbs", C.c_void_p)]
+                ("aabbs", C.c_void_p), ("n_cylinders", C.c_int32), ("cylinders", C.c_void_p)]
 
 
 class BatchS(C.Structure):
@@ -74,6 +74,8 @@ def lib():
             L.orc_sphere_sphere.restype = C.c_double
             L.orc_sphere_box.argtypes = [P, C.c_double, P]
             L.orc_sphere_box.restype = C.c_double
+            L.orc_sphere_cylinder.argtypes = [P, C.c_double, P]
+            L.orc_sphere_cylinder.restype = C.c_double
             L.orc_query_T.argtypes = [P, P, C.c_int, P]
             L.orc_mv.argtypes = [P, P, P, C.c_int, C.c_int, P]
             L.orc_mv_min_clearance.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P]
@@ -118,7 +120,8 @@ def _robot_struct(m, keep: _Keep) -> Robot:
 def _env_struct(e, keep: _Keep) -> EnvS:
     s = keep.arr(e.spheres.reshape(-1, 4), np.float32)
     b = keep.arr(e.aabbs.reshape(-1, 6), np.float32)
-    return EnvS(s.shape[0], _ptr(s), b.shape[0], _ptr(b))
+    cy = keep.arr(np.asarray(getattr(e, "cylinders", np.zeros((0, 7)))).reshape(-1, 7), np.float32)
+    return EnvS(s.shape[0], _ptr(s), b.shape[0], _ptr(b), cy.shape[0], _ptr(cy))
 
 
 class Oracle:
@@ -239,3 +242,10 @@ def sphere_box(c, r, box) -> float:
     a = np.ascontiguousarray(c, np.float64)
     bx = np.ascontiguousarray(box, np.float32)
     return lib().orc_sphere_box(a.ctypes.data, float(r), bx.ctypes.data)
+
+
+def sphere_cylinder(c, r, cyl) -> float:
+    """Signed clearance of a sphere and a solid cylinder (a xyz, b xyz, radius)."""
+    a = np.ascontiguousarray(c, np.float64)
+    cy = np.ascontiguousarray(cyl, np.float32)
+    return lib().orc_sphere_cylinder(a.ctypes.data, float(r), cy.ctypes.data)

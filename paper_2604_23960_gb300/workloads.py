@@ -76,6 +76,8 @@ class Env:
     spheres: np.ndarray       # (n,4) float32
     aabbs: np.ndarray         # (n,6) float32
     name: str = ""
+    # (n,7) float32: solid cylinders, axis end a xyz, axis end b xyz, radius
+    cylinders: np.ndarray = field(default_factory=lambda: np.zeros((0, 7), np.float32))
 
 
 @dataclass
@@ -234,6 +236,40 @@ def cage_arms(fixtures: Optional[dict] = None) -> List[RobotModel]:
     return [panda_like(b, fx["self_pairs"], name=f"panda{k}") for k, b in enumerate(cage_bases())]
 
 
+CEILING_Z = 2.0
+CAGE8_CEILING = [(0.0, 0.85), (-0.85, 0.0), (0.0, -0.85), (0.85, 0.0)]
+
+
+def _pose_ceiling(x: float, y: float, z: float, yaw: float) -> np.ndarray:
+    """3x4 transform Trans(x,y,z) RotZ(yaw) RotX(pi): a base hanging upside
+    down from a ceiling at height z (input synthesis only)."""
+    c, s = math.cos(yaw), math.sin(yaw)
+    return np.array([[c, s, 0.0, x], [s, -c, 0.0, y], [0.0, 0.0, -1.0, z]], np.float32)
+
+
+def cage8_bases() -> List[np.ndarray]:
+    """Cage team of the paper's Cage scenario, floor and ceiling mounted: the
+    four floor arms of the 4-arm cage plus four arms hanging from the ceiling
+    (z = 2 m) at (0, +-0.85) and (+-0.85, 0), all yawed to face the center."""
+    floor = cage_bases()
+    ceil = [_pose_ceiling(x, y, CEILING_Z, math.atan2(-y, -x)) for x, y in CAGE8_CEILING]
+    return floor + ceil
+
+
+def load_cage8_fixtures(path: Optional[Path] = None) -> dict:
+    path = FIXTURES.parent / "cage8_fixtures.npz" if path is None else path
+    if not path.exists():
+        raise FileNotFoundError(
+            f"{path} missing: run `python oracle/make_cage_fixtures.py --cage8` to draw it")
+    with np.load(path) as z:
+        return {k: z[k] for k in z.files}
+
+
+def cage8_arms(fixtures: Optional[dict] = None) -> List[RobotModel]:
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    return [panda_like(b, fx["self_pairs"], name=f"cage8_arm{k}") for k, b in enumerate(cage8_bases())]
+
+
 # ---------------------------------------------------------------------------
 # environments
 # ---------------------------------------------------------------------------
@@ -278,6 +314,37 @@ def cage_env(seed: int = 103) -> Env:
         sph.append([c[0], c[1], c[2], r])
     return Env(np.array(sph, np.float32), np.array(bars, np.float32), name="cage")
 
+
+
+def cage_env_cyl(seed: int = 104, n_inner: int = 16) -> Env:
+    """Cylinder cage (the paper's Cage obstacles are cylinders): 4 vertical
+    posts and 8 beams of radius 0.02 m on the edges of [-1.1,1.1]^2 x [0,2],
+    plus `n_inner` cylinders of radius U(0.03, 0.08) and length U(0.2, 0.6)
+    with uniformly random axis directions and centers U([-1,1]^2 x [0.2,1.8]),
+    redrawn when within 0.3 m of a floor or ceiling arm base's vertical axis."""
+    rng = np.random.default_rng(seed)
+    h, zt, rb = 1.1, CEILING_Z, 0.02
+    cyl = []
+    for x in (-h, h):
+        for y in (-h, h):
+            cyl.append([x, y, 0.0, x, y, zt, rb])
+    for z in (0.0, zt):
+        for y in (-h, h):
+            cyl.append([-h, y, z, h, y, z, rb])
+        for x in (-h, h):
+            cyl.append([x, -h, z, x, h, z, rb])
+    axes = [(x, y) for x, y in CAGE_BASES] + CAGE8_CEILING
+    while len(cyl) < 12 + n_inner:
+        c = rng.uniform([-1.0, -1.0, 0.2], [1.0, 1.0, 1.8])
+        if min(math.hypot(c[0] - x, c[1] - y) for x, y in axes) < 0.3:
+            continue
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        half = rng.uniform(0.1, 0.3)
+        a, b = c - half * d, c + half * d
+        cyl.append([*a, *b, rng.uniform(0.03, 0.08)])
+    return Env(np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), "cage_cyl",
+               np.asarray(cyl, np.float32))
 
 def empty_env() -> Env:
     return Env(np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), name="empty")
@@ -447,6 +514,26 @@ def make_cage_priority(n_queries: int = 10000, query_seed: int = 207, fixtures: 
               np.zeros(n_queries, np.int32))
     return Workload("cage_priority", models, [env], b, env=0, check_env=True,
                     meta={"robots": 4, "priority": True})
+
+
+def make_cage8_mv(n_queries: int = 10000, query_seed: int = 208, fixtures: Optional[dict] = None,
+                  fixtures8: Optional[dict] = None) -> Workload:
+    """MV for the floor- and ceiling-mounted 8-arm team in the cylinder cage:
+    composite start->goal motions whose endpoints come from per-arm pools of
+    env+self valid configurations; resolution 1/32 rad."""
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    f8 = load_cage8_fixtures() if fixtures8 is None else fixtures8
+    models = cage8_arms(fx)
+    env = cage_env_cyl()
+    rng = np.random.default_rng(query_seed)
+    pools = f8["endpoint_pool"]                      # (8, P, 7)
+    P = pools.shape[1]
+    idx = rng.integers(0, P, (n_queries, 8, 2))
+    cfg = pools[np.arange(8)[None, :, None], idx]    # (Q, 8, 2, 7)
+    b = _fast_batch(n_queries, 8, np.tile(np.arange(8), n_queries), cfg.reshape(-1, 7), None, 1.0 / 32.0,
+                    KIND_MV, 0)
+    return Workload("cage8_mv", models, [env], b, env=0, check_env=True,
+                    meta={"robots": 8, "resolution": 1.0 / 32.0})
 
 
 TEAM_ARM_BASES = [(4.4, 5.0, 0.0), (5.6, 5.0, math.pi)]

@@ -44,6 +44,9 @@ MUTANTS = {
     "prio_env_other_robot": ("if (check_env && env_self_min(&qs, env, 0) < 0.0) valid = 0;",
                              "if (check_env && env_self_min(&qs, env, qs.n - 1) < 0.0) valid = 0;"),
     "prio_clearance_pairs": ("double v = pair_min(&qs, 0, j);", "double v = pair_min(&qs, j - 1, j);"),
+    "cyl_caps_dropped": ("const double es = s < 0.0 ? -s : (s > L ? s - L : 0.0);", "const double es = 0.0;"),
+    "cyl_axis_unnormalised": ("for (int k = 0; k < 3; ++k) u[k] /= L;", "for (int k = 0; k < 3; ++k) u[k] /= 1.0;"),
+    "cyl_radius_dropped": ("const double ed = d > rho ? d - rho : 0.0;", "const double ed = d;"),
 }
 
 PIN_ARGS = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",

@@ -483,3 +483,104 @@ def test_prio_bruteforce_tiny(seed):
             perm = [0] + list(rng.permutation(np.arange(1, n)))
             wp = _permute(w, q, perm)
             assert O.Oracle(wp).mv(priority=True)[0] == pr[q]
+
+
+# ------------------------------------------------------- cylinder obstacles
+
+CYL = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 2.0, 1.0])   # axis z in [0, 2], radius 1
+
+
+@pytest.mark.parametrize("c, dist", [
+    ((0.0, 0.0, 1.0), 0.0),        # on the axis, inside
+    ((0.6, 0.0, 0.3), 0.0),        # inside, off the axis
+    ((3.0, 0.0, 1.0), 2.0),        # beside the side wall
+    ((0.0, 0.0, 5.0), 3.0),        # above the top cap, within the radius
+    ((0.5, 0.0, -2.0), 2.0),       # below the bottom cap, within the radius
+    ((4.0, 0.0, 6.0), 5.0),        # beyond the rim: 3-4-5 to the top edge
+    ((0.0, -2.0, -3.0), math.hypot(1.0, 3.0)),   # beyond the bottom rim
+    ((1.0, 0.0, 1.0), 0.0),        # on the side wall
+])
+def test_sphere_cylinder_cases(c, dist):
+    assert O.sphere_cylinder(c, 0.25, CYL) == pytest.approx(dist - 0.25, abs=1e-12)
+
+
+def _rotation(rng):
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def test_sphere_cylinder_rigid_motion_and_ends():
+    """A rigid motion of sphere and cylinder keeps the clearance; swapping
+    the axis ends keeps it; a longer axis only adds clearance beyond the caps."""
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        Rm, tr = _rotation(rng), rng.normal(size=3)
+        c = rng.uniform(-3, 3, 3)
+        r = rng.uniform(0, 0.5)
+        ref = O.sphere_cylinder(c, r, CYL)
+        a, b = Rm @ CYL[:3] + tr, Rm @ CYL[3:6] + tr
+        moved = np.concatenate([a, b, [CYL[6]]])
+        assert O.sphere_cylinder(Rm @ c + tr, r, moved) == pytest.approx(ref, abs=2e-6)
+        swapped = np.concatenate([b, a, [CYL[6]]])
+        assert O.sphere_cylinder(Rm @ c + tr, r, swapped) == pytest.approx(ref, abs=2e-6)
+
+
+def test_sphere_cylinder_surface_sampling():
+    """Outside the solid, the distance is the minimum over its surface: a dense
+    sampling of the side wall and both caps bounds it from above and, to the
+    sampling step, from below; inside, the distance is 0."""
+    rng = np.random.default_rng(13)
+    for _ in range(20):
+        a = rng.uniform(-1, 1, 3)
+        b = a + rng.normal(size=3)
+        rho = rng.uniform(0.1, 0.8)
+        cyl = np.concatenate([a, b, [rho]]).astype(np.float32).astype(np.float64)
+        a, b, rho = cyl[:3], cyl[3:6], cyl[6]
+        L = np.linalg.norm(b - a)
+        u = (b - a) / L
+        e1 = np.cross(u, [1.0, 0, 0] if abs(u[0]) < 0.9 else [0, 1.0, 0])
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(u, e1)
+        ang = np.linspace(0, 2 * np.pi, 181)[:-1]
+        ring = np.cos(ang)[:, None] * e1 + np.sin(ang)[:, None] * e2
+        side = (a + np.linspace(0, L, 81)[:, None, None] * u + rho * ring[None]).reshape(-1, 3)
+        disc = (np.linspace(0, rho, 21)[:, None, None] * ring[None]).reshape(-1, 3)
+        surf = np.concatenate([side, a + disc, b + disc])
+        step = max(2 * np.pi * rho / 180, L / 80, rho / 20)
+        for _ in range(30):
+            c = a + rng.uniform(-2.5, 2.5, 3)
+            d = O.sphere_cylinder(c, 0.0, cyl)
+            s, w = (c - a) @ u, c - a
+            inside = 0 <= s <= L and np.linalg.norm(w - s * u) <= rho
+            if inside:
+                assert d == 0.0
+                continue
+            m = np.linalg.norm(surf - c, axis=1).min()
+            assert d <= m + 1e-9 and d >= m - step
+
+
+def test_disc_past_vertical_cylinder():
+    """A disc moving in the plane z = 0 past a vertical cylinder through that
+    plane: MV is invalid exactly when some sampled state brings the disc
+    center within r + rho of the cylinder axis (planar distances, no oracle
+    geometry)."""
+    rng = np.random.default_rng(14)
+    seen = [0, 0]
+    for _ in range(300):
+        cx, cy, rho = rng.uniform(2, 8), rng.uniform(2, 8), rng.uniform(0.2, 1.0)
+        cyl = np.array([[cx, cy, -1.0, cx, cy, 1.0, rho]], np.float32)
+        env = W.Env(np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), "cyl", cyl)
+        s, g = rng.uniform(0, 10, 2).astype(np.float32), rng.uniform(0, 10, 2).astype(np.float32)
+        T = int(rng.integers(5, 80))
+        w = _discs_timed([(s, g)], T, env=env)
+        st = np.array([s + (g.astype(np.float64) - s) * (t / T) for t in range(T + 1)])
+        d = np.linalg.norm(st - np.array([cx, cy], np.float32).astype(np.float64), axis=1) - 0.25 - float(cyl[0, 6])
+        if np.abs(d).min() < 1e-6:
+            continue
+        expect = bool((d >= 0).all())
+        assert bool(O.Oracle(w).mv()[0]) == expect
+        # distance to the solid is 0 inside it, so the clearance is at least -r
+        clr = np.maximum(d + 0.25, 0.0) - 0.25
+        assert O.Oracle(w).mv_min_clearance()[0] == pytest.approx(clr.min(), abs=1e-6)
+        seen[expect] += 1
+    assert min(seen) > 20
