@@ -272,6 +272,20 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
                             "kernel_ms": st["device_ms"], "tuning": tune}
+    # the Cage scenario's team (Sec. V-A): 4 floor- and 4 ceiling-mounted arms
+    # among cylinder obstacles, 10k composite motions
+    w = W.make_cage8_mv(10000)
+    ba = ctx.bind(w).to("cuda")
+    tune = autotune(ctx, w, mrv.MRV_CHECK_ENV, kind=0)
+    dt = timed(lambda: ctx.mv_validate(ba))
+    st = ctx.stats()
+    nvalid = int(ctx.mv_validate(ba).sum().item())
+    pq = per_query(w, lambda b: ctx.mv_validate(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
+    out["cage8_cyl_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
+                            "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
+                            "valid_total": f"{nvalid}/{w.batch.n_queries}",
+                            "effort_states": st["states_checked"] / max(1, st["states_available"]),
+                            "kernel_ms": st["device_ms"], "tuning": tune}
     # prioritized planning's edge checks (Sec. IV-C): 10k cage edges, one arm
     # against the cage, itself and three higher-priority arms' timed paths
     w = W.make_cage_priority(10000)

@@ -131,9 +131,18 @@ typedef struct {
   const float *spheres_xyzr;  /* n_spheres x 4, world frame                  */
   int32_t n_aabbs;
   const float *aabb_lohi;     /* n_aabbs x 6: lo x,y,z then hi x,y,z         */
+  int32_t n_cylinders;        /* solid cylinders with flat caps (the Cage
+                                 obstacles of Sec. V-A); may be 0            */
+  const float *cylinders;     /* n_cylinders x 7: axis end a x,y,z, axis end
+                                 b x,y,z, radius; |b - a| > 0, radius >= 0.
+                                 A sphere collides with a cylinder when its
+                                 center is closer to the solid than its
+                                 radius (distance 0 inside)                */
 } mrv_env_desc;
 
-/* Copies an obstacle set (host pointers) to the device. */
+/* Copies an obstacle set (host pointers) to the device.  MRV_ERR_ARG on a
+ * NULL array with a non-zero count, a non-finite value, a negative radius,
+ * a box with lo > hi or a cylinder whose axis ends coincide. */
 int env_upload(mrv_ctx *ctx, const mrv_env_desc *desc, int32_t *env_id_out);
 /* Drops the upload's reference (robots and envs share the id space); the
  * device memory is freed once no call in flight uses it (the context's
@@ -256,6 +265,7 @@ typedef struct {
   uint64_t box_tests;        /* the sphere-box part of sphere_tests           */
   uint64_t fk_chains;        /* (state, robot) kinematic chains evaluated     */
   uint64_t spheres_placed;   /* sphere centers computed (states x spheres)    */
+  uint64_t cylinder_tests;   /* the sphere-cylinder part of sphere_tests      */
 } mrv_stats;
 int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
 

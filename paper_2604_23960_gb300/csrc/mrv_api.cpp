@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <utility>
 
@@ -55,31 +56,51 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
-size_t Scratch::bytes_for(int64_t nq, int64_t ns, int64_t nw, int64_t stride) {
-  size_t b = 0;
-  auto add = [&](size_t n) { b = align_up(b, 256) + n; };
-  add(sizeof(int32_t) * nw);            // slot_tau
-  add(sizeof(QueryDev) * nq);           // q
-  add(sizeof(int32_t) * nq * 3);        // hit, best, minclr
-  add(sizeof(int32_t) * nq);            // sorted
-  add(sizeof(int32_t) * (kMaxLevels + 1) * 3);
-  add(sizeof(int32_t) * 8);             // counters
-  add(sizeof(uint32_t) * 2);            // err
-  add(sizeof(unsigned long long) * 8);  // stats
-  add(sizeof(int32_t) * 4);             // counts
+// The arena's layout, one walk for both sizing (p == nullptr) and carving:
+// every array starts on a 256-byte boundary.  Returns the bytes it spans.
+size_t Scratch::layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char *p) {
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    o = align_up(o, 256);
+    void *r = p ? p + o : nullptr;
+    o += n;
+    return r;
+  };
+  auto set = [&](auto **dst, size_t n) {
+    void *r = take(n);
+    if (p) *dst = static_cast<std::remove_pointer_t<decltype(dst)>>(r);
+  };
+  set(&slot_tau, sizeof(int32_t) * nw);
+  set(&q, sizeof(QueryDev) * nq);
+  set(&q_hit, sizeof(int32_t) * nq);
+  set(&q_best, sizeof(int32_t) * nq);
+  set(&q_minclr, sizeof(float) * nq);
+  set(&sorted, sizeof(int32_t) * nq);
+  set(&hist, sizeof(int32_t) * (kMaxLevels + 1));
+  set(&level_start, sizeof(int32_t) * (kMaxLevels + 1));
+  set(&cursor, sizeof(int32_t) * (kMaxLevels + 1));
+  set(&counters, sizeof(int32_t) * 8);
+  set(&err, sizeof(uint32_t) * 2);
+  set(&stats, sizeof(unsigned long long) * kNumStats);
+  set(&counts, sizeof(int32_t) * 4);
   // staged inputs
-  add(sizeof(int32_t) * (nq + 1));
-  add(sizeof(int32_t) * ns);
-  add(sizeof(int32_t) * (ns + 1));
-  add(sizeof(float) * nw * stride);
-  add(sizeof(int32_t) * nw);
-  add(sizeof(int32_t) * nq);            // q_env
-  add(sizeof(uint8_t) * nq);            // q_kind
+  set(&in_q_off, sizeof(int32_t) * (nq + 1));
+  set(&in_slot_robot, sizeof(int32_t) * ns);
+  set(&in_slot_wp, sizeof(int32_t) * (ns + 1));
+  set(&in_wp, sizeof(float) * nw * stride);
+  set(&in_steps, sizeof(int32_t) * nw);
+  set(&in_q_env, sizeof(int32_t) * nq);
+  set(&in_q_kind, sizeof(uint8_t) * nq);
   // staged outputs
-  add(sizeof(uint8_t) * nq);
-  add(sizeof(float) * nq);
-  add(sizeof(mrv_conflict) * nq);
-  return align_up(b, 256) + 256;
+  set(&out_valid, sizeof(uint8_t) * nq);
+  set(&out_minclr, sizeof(float) * nq);
+  set(&out_conf, sizeof(mrv_conflict) * nq);
+  return align_up(o, 256);
+}
+
+size_t Scratch::bytes_for(int64_t nq, int64_t ns, int64_t nw, int64_t stride) {
+  Scratch probe;
+  return probe.layout(nq, ns, nw, stride, nullptr);
 }
 
 int Scratch::ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStream_t st) {
@@ -100,37 +121,7 @@ int Scratch::ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStre
     }
     cap = want;
   }
-  char *p = static_cast<char *>(base);
-  size_t o = 0;
-  auto take = [&](size_t n) {
-    o = align_up(o, 256);
-    void *r = p + o;
-    o += n;
-    return r;
-  };
-  slot_tau = (int32_t *)take(sizeof(int32_t) * nw);
-  q = (QueryDev *)take(sizeof(QueryDev) * nq);
-  q_hit = (int32_t *)take(sizeof(int32_t) * nq);
-  q_best = (int32_t *)take(sizeof(int32_t) * nq);
-  q_minclr = (float *)take(sizeof(float) * nq);
-  sorted = (int32_t *)take(sizeof(int32_t) * nq);
-  hist = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
-  level_start = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
-  cursor = (int32_t *)take(sizeof(int32_t) * (kMaxLevels + 1));
-  counters = (int32_t *)take(sizeof(int32_t) * 8);
-  err = (uint32_t *)take(sizeof(uint32_t) * 2);
-  stats = (unsigned long long *)take(sizeof(unsigned long long) * 8);
-  counts = (int32_t *)take(sizeof(int32_t) * 4);
-  in_q_off = (int32_t *)take(sizeof(int32_t) * (nq + 1));
-  in_slot_robot = (int32_t *)take(sizeof(int32_t) * ns);
-  in_slot_wp = (int32_t *)take(sizeof(int32_t) * (ns + 1));
-  in_wp = (float *)take(sizeof(float) * nw * stride);
-  in_steps = (int32_t *)take(sizeof(int32_t) * nw);
-  in_q_env = (int32_t *)take(sizeof(int32_t) * nq);
-  in_q_kind = (uint8_t *)take(sizeof(uint8_t) * nq);
-  out_valid = (uint8_t *)take(sizeof(uint8_t) * nq);
-  out_minclr = (float *)take(sizeof(float) * nq);
-  out_conf = (mrv_conflict *)take(sizeof(mrv_conflict) * nq);
+  layout(nq, ns, nw, stride, static_cast<char *>(base));
   return MRV_OK;
 }
 
@@ -258,7 +249,7 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "scratch reset");
   if ((e = launch_prepare(B, st)) != cudaSuccess) return cuda_fail(e, "prepare launch");
@@ -295,7 +286,7 @@ int finish_call(mrv_ctx *ctx, Scratch &S, bool async) {
   cudaStream_t st = ctx->stream;
   cudaError_t e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ctx->h_stats, S.stats, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(ctx->h_stats, S.stats, sizeof(unsigned long long) * kNumStats, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->h_counts, S.counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "status copy");
@@ -323,6 +314,7 @@ int mrv_ctx::sync() {
   stats.box_tests = h_stats[5];
   stats.fk_chains = h_stats[6];
   stats.spheres_placed = h_stats[7];
+  stats.cylinder_tests = h_stats[8];
   stats.n_valid = h_counts[0];
   stats.n_conflicts = h_counts[1];
   float ms = 0.f;
@@ -364,7 +356,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
     cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * 4, st);
     if (e == cudaSuccess) e = launch_prepare(B, st);
     if (e != cudaSuccess) return cuda_fail(e, "prepare");
@@ -629,8 +621,31 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
 
 int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
   if (!c || !d || !id_out) return fail(MRV_ERR_ARG, "NULL argument");
-  if (d->n_spheres < 0 || d->n_aabbs < 0) return fail(MRV_ERR_ARG, "negative obstacle counts");
-  if ((d->n_spheres && !d->spheres_xyzr) || (d->n_aabbs && !d->aabb_lohi)) return fail(MRV_ERR_ARG, "obstacle arrays missing");
+  if (d->n_spheres < 0 || d->n_aabbs < 0 || d->n_cylinders < 0) return fail(MRV_ERR_ARG, "negative obstacle counts");
+  if ((d->n_spheres && !d->spheres_xyzr) || (d->n_aabbs && !d->aabb_lohi) || (d->n_cylinders && !d->cylinders))
+    return fail(MRV_ERR_ARG, "obstacle arrays missing");
+  // cylinders: finite, radius >= 0, distinct axis ends; stored as (a, radius)
+  // and (unit axis, length), computed in double
+  std::vector<float> cyl_a(4 * (size_t)d->n_cylinders), cyl_u(4 * (size_t)d->n_cylinders);
+  for (int i = 0; i < d->n_cylinders; ++i) {
+    const float *x = d->cylinders + 7 * i;
+    for (int k = 0; k < 7; ++k)
+      if (!std::isfinite(x[k])) return fail(MRV_ERR_ARG, "cylinder %d not finite", i);
+    if (!(x[6] >= 0.f)) return fail(MRV_ERR_ARG, "cylinder %d has a negative radius", i);
+    double u[3], L = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      u[k] = (double)x[3 + k] - (double)x[k];
+      L += u[k] * u[k];
+    }
+    L = std::sqrt(L);
+    if (!(L > 0.0)) return fail(MRV_ERR_ARG, "cylinder %d has coinciding axis ends", i);
+    for (int k = 0; k < 3; ++k) {
+      cyl_a[4 * i + k] = x[k];
+      cyl_u[4 * i + k] = (float)(u[k] / L);
+    }
+    cyl_a[4 * i + 3] = x[6];
+    cyl_u[4 * i + 3] = (float)L;
+  }
   for (int i = 0; i < d->n_aabbs; ++i)
     for (int k = 0; k < 3; ++k)
       if (!(d->aabb_lohi[6 * i + k] <= d->aabb_lohi[6 * i + 3 + k]))
@@ -683,11 +698,21 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
     if (m.dev.live)
       for (int l = 0; l < m.dev.n_links; ++l) R = std::max(R, m.dev.link_bs[l][3]);
   if (!(R > 0.f)) R = 0.3f;
-  const ObstacleGrid G = build_obstacle_grid(d->n_spheres, d->spheres_xyzr, d->n_aabbs, d->aabb_lohi, (double)R);
+  const ObstacleGrid G = build_obstacle_grid(d->n_spheres, d->spheres_xyzr, d->n_aabbs, d->aabb_lohi,
+                                             d->n_cylinders, d->cylinders, (double)R);
+  if ((rc = upload(&h.d_cyla, cyl_a.data(), sizeof(float) * cyl_a.size())) ||
+      (rc = upload(&h.d_cylu, cyl_u.data(), sizeof(float) * cyl_u.size()))) {
+    h.free_all();
+    return rc;
+  }
+  h.dev.n_cyl = d->n_cylinders;
+  h.dev.cyl_a = (const float4 *)h.d_cyla;
+  h.dev.cyl_u = (const float4 *)h.d_cylu;
   h.dev.g_R = -1.f;
   if (G.R > 0) {
     if ((rc = upload(&h.d_goff, G.off.data(), sizeof(int32_t) * G.off.size())) ||
         (rc = upload(&h.d_gns, G.ns.data(), sizeof(uint16_t) * G.ns.size())) ||
+        (rc = upload(&h.d_gnb, G.nb.data(), sizeof(uint16_t) * G.nb.size())) ||
         (rc = upload(&h.d_gitems, G.items.data(), sizeof(uint16_t) * std::max<size_t>(1, G.items.size())))) {
       h.free_all();
       return rc;
@@ -701,6 +726,7 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
     h.dev.g_off = (const int32_t *)h.d_goff;
     h.dev.g_ns = (const uint16_t *)h.d_gns;
     h.dev.g_items = (const uint16_t *)h.d_gitems;
+    h.dev.g_nb = (const uint16_t *)h.d_gnb;
   }
   h.refs = 1;
   c->envs.push_back(h);
@@ -817,7 +843,7 @@ int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, 
   cudaStream_t st = c->stream;
   cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
   if (e == cudaSuccess) e = launch_prepare(B, st);
   if (e != cudaSuccess) return cuda_fail(e, "prepare");
   // the query's sphere count bounds the output; read it back
@@ -921,7 +947,8 @@ int mrv_graph_launch(mrv_graph *g) {
   // status of the replay is read by the next mrv_sync
   e = cudaMemcpyAsync(c->h_status, g->scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->h_stats, g->scratch.stats, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, c->stream);
+    e = cudaMemcpyAsync(c->h_stats, g->scratch.stats, sizeof(unsigned long long) * kNumStats, cudaMemcpyDeviceToHost,
+                        c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->h_counts, g->scratch.counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "graph status copy");

@@ -19,6 +19,7 @@ constexpr int kMaxLinks = MRV_MAX_DOF + 2;  // frames 0..dof+1
 constexpr int kMaxLevels = 256;       // work levels (work items per query)
 constexpr int kEnvIdBase = 1 << 20;   // env ids = kEnvIdBase + env slot
 constexpr int kFkChains = 8;          // (state, robot) chains per FK round
+constexpr int kNumStats = 9;          // statistics counters of a call (see mrv_stats)
 
 // device error bits (BatchDev::err)
 enum : uint32_t {
@@ -82,6 +83,12 @@ struct EnvDev {
   const int32_t *g_off;
   const uint16_t *g_ns;
   const uint16_t *g_items;
+  const uint16_t *g_nb;          // boxes per cell (after its spheres; cylinders follow)
+  // solid cylinders with flat caps
+  int32_t n_cyl;
+  int32_t pad2;
+  const float4 *cyl_a;           // axis end a xyz, radius
+  const float4 *cyl_u;           // unit axis (a -> b) xyz, length |b - a|
 };
 
 // per-query derived record (written by the preparation kernel)
@@ -103,6 +110,7 @@ struct QueryDev {
   long long pairtests;  // robot-robot sphere tests per state
   long long envtests;   // robot-obstacle sphere + self tests per state (MV with env)
   long long boxtests;   // robot-box tests per state (MV with env)
+  long long cyltests;   // robot-cylinder tests per state (MV with env)
 };
 
 struct BatchDev {

@@ -141,10 +141,19 @@ static double box_box(const double *alo, const double *ahi, const double *blo, c
   return std::sqrt(d2);
 }
 
-ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, const float *lohi, double R,
-                                 int64_t max_items) {
+ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, const float *lohi, int n_cyl,
+                                 const float *cyl, double R, int64_t max_items) {
   ObstacleGrid G;
-  if (!(R > 0) || n_spheres + n_boxes == 0 || n_spheres > 65535 || n_boxes > 65535) return G;
+  if (!(R > 0) || n_spheres + n_boxes + n_cyl == 0 || n_spheres > 65535 || n_boxes > 65535 || n_cyl > 65535)
+    return G;
+  // a cylinder's bounding box: axis ends +- radius on every axis
+  std::vector<double> cbox(6 * (size_t)n_cyl);
+  for (int i = 0; i < n_cyl; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const double p = cyl[7 * i + a], q = cyl[7 * i + 3 + a], rr = cyl[7 * i + 6];
+      cbox[6 * i + a] = std::min(p, q) - rr;
+      cbox[6 * i + 3 + a] = std::max(p, q) + rr;
+    }
   // bounding box of the obstacles
   double blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int i = 0; i < n_spheres; ++i)
@@ -156,6 +165,11 @@ ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, 
     for (int a = 0; a < 3; ++a) {
       blo[a] = std::min(blo[a], (double)lohi[6 * i + a]);
       bhi[a] = std::max(bhi[a], (double)lohi[6 * i + 3 + a]);
+    }
+  for (int i = 0; i < n_cyl; ++i)
+    for (int a = 0; a < 3; ++a) {
+      blo[a] = std::min(blo[a], cbox[6 * i + a]);
+      bhi[a] = std::max(bhi[a], cbox[6 * i + 3 + a]);
     }
   double scale = 1.0;
   for (int a = 0; a < 3; ++a) scale = std::max(scale, std::max(std::fabs(blo[a]), std::fabs(bhi[a])));
@@ -215,28 +229,48 @@ ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, 
             if (box_box(clo, chi, olo, ohi) < reach) visit(((int64_t)z * ny + y) * nx + x, 1, i);
           }
     }
+    for (int i = 0; i < n_cyl; ++i) {
+      const double reach = R + slack;
+      const double *olo = &cbox[6 * i], *ohi = &cbox[6 * i + 3];
+      const double lo[3] = {olo[0] - reach, olo[1] - reach, olo[2] - reach};
+      const double hi[3] = {ohi[0] + reach, ohi[1] + reach, ohi[2] + reach};
+      int i0[3], i1[3];
+      cell_range(lo, hi, i0, i1);
+      for (int z = i0[2]; z <= i1[2]; ++z)
+        for (int y = i0[1]; y <= i1[1]; ++y)
+          for (int x = i0[0]; x <= i1[0]; ++x) {
+            const double clo[3] = {G.lo[0] + x * h, G.lo[1] + y * h, G.lo[2] + z * h};
+            const double chi[3] = {clo[0] + h, clo[1] + h, clo[2] + h};
+            if (box_box(clo, chi, olo, ohi) < reach) visit(((int64_t)z * ny + y) * nx + x, 2, i);
+          }
+    }
   };
-  std::vector<int64_t> cnt_s(ncells, 0), cnt_b(ncells, 0);
+  std::vector<int64_t> cnt[3] = {std::vector<int64_t>(ncells, 0), std::vector<int64_t>(ncells, 0),
+                                 std::vector<int64_t>(ncells, 0)};
   int64_t total = 0;
   each([&](int64_t c, int kind, int) {
-    (kind ? cnt_b : cnt_s)[c]++;
+    cnt[kind][c]++;
     ++total;
   });
   if (total > max_items) return ObstacleGrid{};
   G.off.assign(ncells + 1, 0);
   G.ns.assign(ncells, 0);
+  G.nb.assign(ncells, 0);
   for (int64_t c = 0; c < ncells; ++c) {
-    G.off[c + 1] = G.off[c] + (int32_t)(cnt_s[c] + cnt_b[c]);
-    G.ns[c] = (uint16_t)std::min<int64_t>(cnt_s[c], 65535);
-    if (cnt_s[c] > 65535) return ObstacleGrid{};
+    if (cnt[0][c] > 65535 || cnt[1][c] > 65535) return ObstacleGrid{};
+    G.off[c + 1] = G.off[c] + (int32_t)(cnt[0][c] + cnt[1][c] + cnt[2][c]);
+    G.ns[c] = (uint16_t)cnt[0][c];
+    G.nb[c] = (uint16_t)cnt[1][c];
   }
   G.items.assign((size_t)total, 0);
-  std::vector<int32_t> fs(ncells), fb(ncells);
+  std::vector<int32_t> fill[3] = {std::vector<int32_t>(ncells), std::vector<int32_t>(ncells),
+                                  std::vector<int32_t>(ncells)};
   for (int64_t c = 0; c < ncells; ++c) {
-    fs[c] = G.off[c];
-    fb[c] = G.off[c] + G.ns[c];
+    fill[0][c] = G.off[c];
+    fill[1][c] = G.off[c] + G.ns[c];
+    fill[2][c] = G.off[c] + G.ns[c] + G.nb[c];
   }
-  each([&](int64_t c, int kind, int id) { G.items[kind ? fb[c]++ : fs[c]++] = (uint16_t)id; });
+  each([&](int64_t c, int kind, int id) { G.items[fill[kind][c]++] = (uint16_t)id; });
   G.R = R;
   return G;
 }

@@ -48,8 +48,9 @@ PreparedModel prepare_model(int n_links, int m, const int32_t *link, const float
 // Uniform grid over a static obstacle set for the frame-level broadphase.
 // A frame bounding sphere of radius <= R whose center lies in cell c can
 // only overlap the obstacles listed for c: cell c lists every obstacle sphere
-// within R + r_o (+ slack) of the cell's box and every box within R
-// (+ slack) of it.  The slack (1e-3 cell + 1e-6 relative) covers the FP32
+// within R + r_o (+ slack) of the cell's box, every box within R (+ slack) of
+// it, and every cylinder whose bounding box (axis ends +- radius per axis)
+// lies within R (+ slack) of it.  The slack (1e-3 cell + 1e-6 relative) covers the FP32
 // computation of a center's cell.  Centers outside the grid overlap no
 // obstacle.  Cell (ix, iy, iz) = [lo + i h, lo + (i + 1) h) per axis, index
 // (iz * dims[1] + iy) * dims[0] + ix.
@@ -60,13 +61,15 @@ struct ObstacleGrid {
   int dims[3] = {0, 0, 0};
   std::vector<int32_t> off;            // ncells + 1: items of cell c are [off[c], off[c+1])
   std::vector<uint16_t> ns;            // obstacle spheres listed first, ns[c] of them
-  std::vector<uint16_t> items;         // obstacle sphere ids, then box ids
+  std::vector<uint16_t> nb;            // then nb[c] boxes, then the cylinders
+  std::vector<uint16_t> items;         // obstacle sphere ids, box ids, cylinder ids
 };
 
 // Builds the grid for frames of radius <= R (at most 64 cells per axis,
 // cells of at least R / 2).  Returns R = -1 (no grid) when R <= 0, there are
-// no obstacles, either kind exceeds 65535, or the lists would pass max_items.
-ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, const float *lohi, double R,
-                                 int64_t max_items = int64_t(1) << 24);
+// no obstacles, any kind exceeds 65535, or the lists would pass max_items.
+// cyl: n_cyl x 7 (axis end a, axis end b, radius).
+ObstacleGrid build_obstacle_grid(int n_spheres, const float *xyzr, int n_boxes, const float *lohi, int n_cyl,
+                                 const float *cyl, double R, int64_t max_items = int64_t(1) << 24);
 
 }  // namespace mrv

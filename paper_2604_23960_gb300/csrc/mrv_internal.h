@@ -39,6 +39,9 @@ struct Scratch {
   mrv_conflict *out_conf = nullptr;
 
   static size_t bytes_for(int64_t nq, int64_t ns, int64_t nw, int64_t stride);
+  // the arena's layout: sets every pointer from p (nothing when p is null)
+  // and returns the bytes spanned; bytes_for and ensure both use it
+  size_t layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char *p);
   int ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStream_t st);
   void release();
 };
@@ -62,10 +65,11 @@ struct HostModel {
 struct HostEnv {
   EnvDev dev{};
   void *d_spheres = nullptr, *d_k = nullptr, *d_lo = nullptr, *d_hi = nullptr;
-  void *d_goff = nullptr, *d_gns = nullptr, *d_gitems = nullptr;   // obstacle grid
+  void *d_goff = nullptr, *d_gns = nullptr, *d_gitems = nullptr, *d_gnb = nullptr;   // obstacle grid
+  void *d_cyla = nullptr, *d_cylu = nullptr;                                          // cylinders
   int refs = 0;
   void free_all() {
-    for (void **p : {&d_spheres, &d_k, &d_lo, &d_hi, &d_goff, &d_gns, &d_gitems}) {
+    for (void **p : {&d_spheres, &d_k, &d_lo, &d_hi, &d_goff, &d_gns, &d_gitems, &d_gnb, &d_cyla, &d_cylu}) {
       if (*p) cudaFree(*p);
       *p = nullptr;
     }

@@ -76,8 +76,10 @@ struct TileCtx {
   const float4 *box_lo, *box_hi;
   const EnvDev *env;         // the query's obstacle set (null: none)
   float env_c2, env_r2, rho2;
-  long long pairtests, envtests, boxtests;
-  unsigned long long tests, btests, states, chains, placed;
+  long long pairtests, envtests, boxtests, cyltests;
+  unsigned long long tests, btests, states, chains, placed, ctests;
+  int env_nc;                // obstacle cylinders of the query's env
+  const float4 *cyl_a, *cyl_u;
 };
 
 constexpr int kCand = 64;        // broadphase candidates per list and state
@@ -93,7 +95,8 @@ struct Cands {
   uint16_t scn[kCand];       // ... and its pair count (blocks: first row mask)
   uint8_t sck[kCand];        // blocks: frame slot of the column frame
   int32_t pf[kCand + 1];     // exclusive prefix of the tests of the list being resolved
-  int32_t np, ne, nb, ns, overflow, pad;
+  uint32_t yc[kCand];        // frame slot << 24 | obstacle cylinder
+  int32_t np, ne, nb, ns, overflow, ny;
   uint32_t need[3], placed[3];
 };
 static_assert(sizeof(Cands) <= sizeof(float) * MRV_MAX_QUERY_SPHERES, "candidate lists fit the K array");
@@ -176,7 +179,7 @@ __global__ void k_prep(BatchDev B) {
   QueryDev Q;
   Q.T = 0; Q.n = 0; Q.M = 0; Q.ntiles = 0; Q.split = 1; Q.spt = kWarp; Q.nslices = 0; Q.nphase = 1;
   Q.nchunks = 0; Q.cte = 1; Q.env = -1; Q.bits = 0; Q.rho2 = 0.f; Q.pad = 0;
-  Q.pairtests = 0; Q.envtests = 0; Q.boxtests = 0;
+  Q.pairtests = 0; Q.envtests = 0; Q.boxtests = 0; Q.cyltests = 0;
   const int s0 = B.q_robot_off[q], s1 = B.q_robot_off[q + 1];
   const int n = s1 - s0;
   if (n < 1 || n > MRV_MAX_ROBOTS || s0 < 0 || s1 > B.n_slots) err |= kErrRobots;
@@ -269,19 +272,21 @@ __global__ void k_prep(BatchDev B) {
     for (int i = 0; i < (prio ? 1 : n); ++i)
       for (int j = i + 1; j < n; ++j) pt += (long long)ms[i] * ms[j];
     Q.pairtests = pt;
-    long long et = 0, bt = 0;
+    long long et = 0, bt = 0, ct = 0;
     if (check_env) {
       const int Me = prio ? ms[0] : M;
       if (env >= 0) {
         et = (long long)Me * B.envs[env].n_spheres;
         bt = (long long)Me * B.envs[env].n_aabbs;
+        ct = (long long)Me * B.envs[env].n_cyl;
       }
       et += prio ? self0 : self_total;
     }
     Q.envtests = et;
     Q.boxtests = bt;
+    Q.cyltests = ct;
     atomicAdd(&B.stats[2], (unsigned long long)(T + 1));
-    atomicAdd(&B.stats[3], (unsigned long long)((T + 1) * (pt + et + bt)));
+    atomicAdd(&B.stats[3], (unsigned long long)((T + 1) * (pt + et + bt + ct)));
   }
   B.q[q] = Q;
   B.q_hit[q] = 0;
@@ -506,6 +511,21 @@ __device__ __forceinline__ float sph_clr(const float4 a, const float4 b) {
   return sqrtf(dx * dx + dy * dy + dz * dz) - (a.w + b.w);
 }
 
+// squared distance from a point to a solid cylinder with flat caps (0
+// inside): A = axis end a, radius; U = unit axis, length.  With s the axial
+// coordinate and d the distance from the axis line, the nearest point of the
+// solid clamps s to [0, L] and d to [0, radius].
+__device__ __forceinline__ float cyl_d2(float x, float y, float z, const float4 A, const float4 U) {
+  const float wx = x - A.x, wy = y - A.y, wz = z - A.z;
+  const float s = fmaf(wx, U.x, fmaf(wy, U.y, wz * U.z));
+  const float px = fmaf(-s, U.x, wx), py = fmaf(-s, U.y, wy), pz = fmaf(-s, U.z, wz);
+  const float d2 = fmaf(px, px, fmaf(py, py, pz * pz));
+  const float es = fmaxf(fmaxf(-s, s - U.w), 0.f);
+  if (d2 <= A.w * A.w) return es * es;
+  const float ed = sqrtf(d2) - A.w;
+  return fmaf(es, es, ed * ed);
+}
+
 // squared distance from a point to a box (0 inside)
 __device__ __forceinline__ float box_d2(float x, float y, float z, const float4 lo, const float4 hi) {
   const float ex = x - fminf(fmaxf(x, lo.x), hi.x);
@@ -605,6 +625,11 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
           if (CLR) minclr = fminf(minclr, sqrtf(d2) - pa.w);
           else hit |= d2 < pa.w * pa.w;
         }
+        for (int o = 0; o < C.env_nc; ++o) {
+          const float d2 = cyl_d2(pa.x, pa.y, pa.z, __ldg(&C.cyl_a[o]), __ldg(&C.cyl_u[o]));
+          if (CLR) minclr = fminf(minclr, sqrtf(d2) - pa.w);
+          else hit |= d2 < pa.w * pa.w;
+        }
       }
       for (int r = 0; r < C.self_robots; ++r)
         for (int p = 0; p < S.rs[r].n_self; ++p) {
@@ -627,8 +652,9 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
         }
     if (lane == 0) {
       if (do_env && C.check_env) {
-        C.tests += (unsigned long long)nvalid * (unsigned long long)(C.envtests + C.boxtests);
+        C.tests += (unsigned long long)nvalid * (unsigned long long)(C.envtests + C.boxtests + C.cyltests);
         C.btests += (unsigned long long)nvalid * (unsigned long long)C.boxtests;
+        C.ctests += (unsigned long long)nvalid * (unsigned long long)C.cyltests;
       }
       if (do_pairs) C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
     }
@@ -789,6 +815,11 @@ __device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, con
     hit |= box_rows(P, 0, M, S.BL, S.BH, nb_c, S.ox, S.oy, S.oz, lane);
     if (C.env_nb > nb_c) hit |= box_rows(P, 0, M, C.box_lo + nb_c, C.box_hi + nb_c, C.env_nb - nb_c, S.ox, S.oy, S.oz, lane);
   }
+  for (int a = lane; a < M && C.env_nc; a += kWarp) {   // cylinders: one row per lane
+    const float4 p = P[a];
+    const float x = p.x + S.ox, y = p.y + S.oy, z = p.z + S.oz, rr = p.w * p.w;
+    for (int o = 0; o < C.env_nc; ++o) hit |= cyl_d2(x, y, z, __ldg(&C.cyl_a[o]), __ldg(&C.cyl_u[o])) < rr;
+  }
   for (int r = 0; r < C.self_robots; ++r) {
     const int o = S.off[r];
     const int nr = S.rs[r].n_rects;
@@ -887,7 +918,7 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float
 // the bounding sphere of (robot r, frame l) and scans the obstacle spheres and
 // boxes (broadcast reads); overlaps are resolved sphere by sphere in the lane.
 __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, unsigned long long &ntests,
-                          unsigned long long &nbox) {
+                          unsigned long long &nbox, unsigned long long &ncyl) {
   bool hit = false;
   const int nk = C.self_robots * kMaxLinks;   // frames of the robots with obstacle checks
   const int ns_c = min(C.env_ns, kEnvCache), nb_c = min(C.env_nb, kBoxCache);
@@ -920,6 +951,18 @@ __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, 
         hit |= box_d2(p.x + S.ox, p.y + S.oy, p.z + S.oz, lo, hi) < p.w * p.w;
         ntests += 1;
         nbox += 1;
+      }
+    }
+    for (int y = 0; y < C.env_nc; ++y) {
+      const float4 A = __ldg(&C.cyl_a[y]), U = __ldg(&C.cyl_u[y]);
+      ntests += 1;
+      ncyl += 1;
+      if (!(cyl_d2(bw.x, bw.y, bw.z, A, U) < rr)) continue;
+      for (int a = a0; a < a1; ++a) {
+        const float4 p = P[a];
+        hit |= cyl_d2(p.x + S.ox, p.y + S.oy, p.z + S.oz, A, U) < p.w * p.w;
+        ntests += 1;
+        ncyl += 1;
       }
     }
   }
@@ -965,7 +1008,7 @@ __device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, 
 // sends its phase to the in-lane path with every sphere placed.
 
 struct BroadAcc {            // per-lane statistics of a slice
-  uint32_t tests, boxes, placed;
+  uint32_t tests, boxes, placed, cyls;
 };
 
 __device__ __forceinline__ void push_cand(uint32_t *list, int32_t *count, int32_t *overflow, uint32_t v) {
@@ -1078,7 +1121,7 @@ __device__ __forceinline__ int list_find(const int32_t *pf, int n, int f) {
 // Exact tests of a frame x obstacle list (cl.pf holds its sphere prefix):
 // lane l takes a contiguous run of the flat (candidate, sphere) range, so a
 // candidate's data stays in registers over its spheres.
-template <bool BOX>
+template <int KIND>   // 0: obstacle spheres, 1: boxes, 2: cylinders
 __device__ bool resolve_obstacles(const TileCtx &C, const WarpSmem &S, const uint32_t *list, int n, int tot,
                                   int lane, BroadAcc &acc) {
   const Cands &cl = S.u.b.cl;
@@ -1089,19 +1132,26 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WarpSmem &S, const uin
   bool hit = false;
   if (f < fe) {
     acc.tests += (uint32_t)(fe - f);
-    if (BOX) acc.boxes += (uint32_t)(fe - f);
+    if (KIND == 1) acc.boxes += (uint32_t)(fe - f);
+    if (KIND == 2) acc.cyls += (uint32_t)(fe - f);
     const float ox = S.ox, oy = S.oy, oz = S.oz;
     for (int it = list_find(cl.pf, n, f); f < fe; ++it) {
       const uint32_t v = list[it];
       const int o = (int)(v & 0xffffffu);
       const int ge = min(fe, cl.pf[it + 1]);
       const float4 *Pk = P + frame_first(S, (int)(v >> 24)) - cl.pf[it];
-      if (!BOX) {
+      if (KIND == 0) {
         const float4 es = o < kEnvCache ? S.ES[o] : __ldg(&C.env_s[o]);
 #pragma unroll 4
         for (; f < ge; ++f) {
           const float4 p = Pk[f];
           hit |= sph_hit(make_float4(p.x + ox, p.y + oy, p.z + oz, p.w), es);
+        }
+      } else if (KIND == 2) {
+        const float4 A = __ldg(&C.cyl_a[o]), U = __ldg(&C.cyl_u[o]);
+        for (; f < ge; ++f) {
+          const float4 p = Pk[f];
+          hit |= cyl_d2(p.x + ox, p.y + oy, p.z + oz, A, U) < p.w * p.w;
         }
       } else {
         const float4 lo = o < kBoxCache ? S.BL[o] : __ldg(&C.box_lo[o]);
@@ -1130,7 +1180,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
   const int nke = C.self_robots * kMaxLinks;   // frames with obstacle checks
   const bool exhaustive = C.exhaustive != 0, ffc = C.ffc != 0;
   if (lane == 0) {
-    cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = 0;
+    cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = cl.ny = 0;
     cl.need[0] = cl.need[1] = cl.need[2] = 0;
     cl.placed[0] = cl.placed[1] = cl.placed[2] = 0;
   }
@@ -1151,7 +1201,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
         const float4 bl = S.BS[k];
         if (bl.w < 0.f) continue;
         const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
-        int i0 = 0, is = 0, i1 = 0;   // spheres [i0, is), boxes [is, i1) of g_items
+        int i0 = 0, is = 0, ib = 0, i1 = 0;   // spheres [i0, is), boxes [is, ib), cylinders [ib, i1)
         bool full = false;
         if (bw.w <= gR) {
           const float fx = (bw.x - glx) * gih, fy = (bw.y - gly) * gih, fz = (bw.z - glz) * gih;
@@ -1160,6 +1210,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
             i0 = __ldg(&E.g_off[c]);
             i1 = __ldg(&E.g_off[c + 1]);
             is = i0 + (int)__ldg(&E.g_ns[c]);
+            ib = is + (int)__ldg(&E.g_nb[c]);
           }
         } else {
           full = true;
@@ -1167,7 +1218,8 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
         bool nd = false;
         if (!full) {
           acc.tests += (uint32_t)(i1 - i0);
-          acc.boxes += (uint32_t)(i1 - is);
+          acc.boxes += (uint32_t)(ib - is);
+          acc.cyls += (uint32_t)(i1 - ib);
           for (int i = i0; i < is; ++i) {
             const int e = __ldg(&E.g_items[i]);
             const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
@@ -1177,7 +1229,7 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
             }
           }
           const float rr = bw.w * bw.w;
-          for (int i = is; i < i1; ++i) {
+          for (int i = is; i < ib; ++i) {
             const int b = __ldg(&E.g_items[i]);
             const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
             const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
@@ -1186,9 +1238,17 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
               nd = true;
             }
           }
+          for (int i = ib; i < i1; ++i) {
+            const int y = __ldg(&E.g_items[i]);
+            if (cyl_d2(bw.x, bw.y, bw.z, __ldg(&C.cyl_a[y]), __ldg(&C.cyl_u[y])) < rr) {
+              push_obst(cl.yc, &cl.ny, &cl.overflow, k, y);
+              nd = true;
+            }
+          }
         } else {
-          acc.tests += (uint32_t)(env_ns + env_nb);
+          acc.tests += (uint32_t)(env_ns + env_nb + C.env_nc);
           acc.boxes += (uint32_t)env_nb;
+          acc.cyls += (uint32_t)C.env_nc;
           for (int e = 0; e < env_ns; ++e) {
             const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
             if (sph_hit(bw, es)) {
@@ -1205,6 +1265,11 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
               nd = true;
             }
           }
+          for (int y = 0; y < C.env_nc; ++y)
+            if (cyl_d2(bw.x, bw.y, bw.z, __ldg(&C.cyl_a[y]), __ldg(&C.cyl_u[y])) < rr) {
+              push_obst(cl.yc, &cl.ny, &cl.overflow, k, y);
+              nd = true;
+            }
         }
         if (nd) need_frame(cl, k);
       }
@@ -1232,35 +1297,48 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
             nd = true;
           }
         }
+        for (int y = og; y < C.env_nc; y += 8)
+          if (cyl_d2(bw.x, bw.y, bw.z, __ldg(&C.cyl_a[y]), __ldg(&C.cyl_u[y])) < rr) {
+            push_obst(cl.yc, &cl.ny, &cl.overflow, k, y);
+            nd = true;
+          }
         if (nd) need_frame(cl, k);
       }
       const uint32_t ns_l = (uint32_t)max(0, (env_ns - og + 7) >> 3), nb_l = (uint32_t)max(0, (env_nb - og + 7) >> 3);
+      const uint32_t nc_l = (uint32_t)max(0, (C.env_nc - og + 7) >> 3);
       int nf = 0;   // bounding spheres of this lane's frame group
       for (int k = fg; k < nke; k += 4) nf += S.BS[k].w >= 0.f;
-      acc.tests += (uint32_t)nf * (ns_l + nb_l);
+      acc.tests += (uint32_t)nf * (ns_l + nb_l + nc_l);
       acc.boxes += (uint32_t)nf * nb_l;
+      acc.cyls += (uint32_t)nf * nc_l;
     }
     __syncwarp();
     if (cl.overflow) {   // too many candidates: resolve env and self in the lanes
       need_all(cl, lane);
       place_needed(C, S, xf, jj, lane, acc);
-      unsigned long long t = 0, bx = 0;
-      hit = env_broad(C, S, P, lane, t, bx);
+      unsigned long long t = 0, bx = 0, cy = 0;
+      hit = env_broad(C, S, P, lane, t, bx, cy);
       acc.tests += (uint32_t)t;
       acc.boxes += (uint32_t)bx;
+      acc.cyls += (uint32_t)cy;
       if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
     } else {
-      if (cl.ne | cl.nb) {
+      if (cl.ne | cl.nb | cl.ny) {
         place_needed(C, S, xf, jj, lane, acc);
-        const int ne = cl.ne, nbx = cl.nb;
+        const int ne = cl.ne, nbx = cl.nb, ny = cl.ny;
         if (ne) {
           const int tot = scan_frames(cl, cl.ec, ne, S, lane);
-          hit |= resolve_obstacles<false>(C, S, cl.ec, ne, tot, lane, acc);
+          hit |= resolve_obstacles<0>(C, S, cl.ec, ne, tot, lane, acc);
           __syncwarp();
         }
         if (nbx) {
           const int tot = scan_frames(cl, cl.bc, nbx, S, lane);
-          hit |= resolve_obstacles<true>(C, S, cl.bc, nbx, tot, lane, acc);
+          hit |= resolve_obstacles<1>(C, S, cl.bc, nbx, tot, lane, acc);
+          __syncwarp();
+        }
+        if (ny) {
+          const int tot = scan_frames(cl, cl.yc, ny, S, lane);
+          hit |= resolve_obstacles<2>(C, S, cl.yc, ny, tot, lane, acc);
           __syncwarp();
         }
         if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
@@ -1290,10 +1368,11 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
       if (cl.overflow) {
         need_all(cl, lane);
         place_needed(C, S, xf, jj, lane, acc);
-        unsigned long long t = 0, bx = 0;
-        hit |= env_broad(C, S, P, lane, t, bx);
+        unsigned long long t = 0, bx = 0, cy = 0;
+        hit |= env_broad(C, S, P, lane, t, bx, cy);
         acc.tests += (uint32_t)t;
         acc.boxes += (uint32_t)bx;
+        acc.cyls += (uint32_t)cy;
       } else if (cl.ns && C.self_blk) {
         // self pairs as blocks: lane = one row sphere of an overlapping
         // group's block, tested against the columns its mask lists (lanes of
@@ -1459,14 +1538,16 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 __device__ __forceinline__ void flush_acc(TileCtx &C, BroadAcc &acc, int lane) {
   const unsigned long long t = warp_sum((unsigned long long)acc.tests);
   const unsigned long long b = warp_sum((unsigned long long)acc.boxes);
+  const unsigned long long cy = warp_sum((unsigned long long)acc.cyls);
   const unsigned long long p = warp_sum((unsigned long long)acc.placed);
   if (lane == 0) {
     C.tests += t;
     C.btests += b;
+    C.ctests += cy;
     C.placed += p;
   }
   __syncwarp();
-  acc.tests = acc.boxes = acc.placed = 0u;
+  acc.tests = acc.boxes = acc.placed = acc.cyls = 0u;
 }
 
 // clearance mode (exhaustive MV with min_clearance_out): direct formulas
@@ -1480,6 +1561,8 @@ __device__ void clr_state(const TileCtx &C, const WarpSmem &S, const float4 *P, 
       for (int o = 0; o < C.env_ns; ++o) minclr = fminf(minclr, sph_clr(w, C.env_s[o]));
       for (int o = 0; o < C.env_nb; ++o)
         minclr = fminf(minclr, sqrtf(box_d2(w.x, w.y, w.z, C.box_lo[o], C.box_hi[o])) - w.w);
+      for (int o = 0; o < C.env_nc; ++o)
+        minclr = fminf(minclr, sqrtf(cyl_d2(w.x, w.y, w.z, __ldg(&C.cyl_a[o]), __ldg(&C.cyl_u[o]))) - w.w);
     }
     for (int r = 0; r < C.self_robots; ++r)
       for (int p = lane; p < S.rs[r].n_self; p += kWarp) {
@@ -1506,7 +1589,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   float *K = S.u.b.K;
   const bool need_env = do_env && C.check_env;
   int found = C.ffc ? 0x7fffffff : 0;
-  BroadAcc acc = {0u, 0u, 0u};
+  BroadAcc acc = {0u, 0u, 0u, 0u};
   const int nv = slice_valid(C, k);   // positions 0..nv-1 of the visiting order
   for (int j0 = 0; j0 < nv; j0 += CS) {
     // (state, robot) chains, three lanes per chain (one row of its frames each)
@@ -1592,15 +1675,17 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
           hit = env_mv(C, S, P, K, lane, cw2, eps);
           if (!C.exhaustive && __any_sync(0xffffffffu, hit)) {
             if (lane == 0) {
-              C.tests += (unsigned long long)(C.envtests + C.boxtests);
+              C.tests += (unsigned long long)(C.envtests + C.boxtests + C.cyltests);
               C.btests += (unsigned long long)C.boxtests;
+              C.ctests += (unsigned long long)C.cyltests;
             }
             return 1;
           }
         }
         if (need_env && lane == 0) {
-          C.tests += (unsigned long long)(C.envtests + C.boxtests);
+          C.tests += (unsigned long long)(C.envtests + C.boxtests + C.cyltests);
           C.btests += (unsigned long long)C.boxtests;
+          C.ctests += (unsigned long long)C.cyltests;
         }
         if (do_pairs) {
           if (!CLR) hit |= pairs_mv(P, K, S.off, n, M, lane, eps, C.pair_robots);
@@ -1655,15 +1740,17 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
   C.prio = (!C.ffc && (B.flags & MRV_PRIORITY)) ? 1 : 0;
   C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
   C.env = nullptr;
+  C.env_nc = 0; C.cyl_a = nullptr; C.cyl_u = nullptr;
   C.env_c2 = 0.f; C.env_r2 = 0.f; C.rho2 = Q.rho2;
   if (C.check_env && Q.env >= 0) {
     const EnvDev &E = B.envs[Q.env];
     C.env = &E;
+    C.env_nc = E.n_cyl; C.cyl_a = E.cyl_a; C.cyl_u = E.cyl_u;
     C.env_ns = E.n_spheres; C.env_nb = E.n_aabbs; C.env_s = E.spheres; C.env_k = E.sphere_k;
     C.box_lo = E.box_lo; C.box_hi = E.box_hi; C.env_c2 = E.c2max; C.env_r2 = E.r2max;
   }
-  C.pairtests = Q.pairtests; C.envtests = Q.envtests; C.boxtests = Q.boxtests;
-  C.tests = 0; C.btests = 0; C.states = 0; C.chains = 0; C.placed = 0;
+  C.pairtests = Q.pairtests; C.envtests = Q.envtests; C.boxtests = Q.boxtests; C.cyltests = Q.cyltests;
+  C.tests = 0; C.btests = 0; C.states = 0; C.chains = 0; C.placed = 0; C.ctests = 0;
   // stage the query's robots; origin of the relative frame = robot 0's base
   const int s0 = B.q_robot_off[q];
   if (lane < C.n) {
@@ -1752,6 +1839,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
     atomicAdd(&B.stats[0], C.states);
     atomicAdd(&B.stats[1], C.tests);
     atomicAdd(&B.stats[5], C.btests);
+    atomicAdd(&B.stats[8], C.ctests);
     atomicAdd(&B.stats[6], C.chains);
     atomicAdd(&B.stats[7], C.placed);
   }
@@ -1914,6 +2002,7 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
         for (int o = 0; o < E->n_spheres; ++o) m = fminf(m, sph_clr(pa, E->spheres[o]));
         for (int o = 0; o < E->n_aabbs; ++o)
           m = fminf(m, sqrtf(box_d2(pa.x, pa.y, pa.z, E->box_lo[o], E->box_hi[o])) - pa.w);
+        for (int o = 0; o < E->n_cyl; ++o) m = fminf(m, sqrtf(cyl_d2(pa.x, pa.y, pa.z, E->cyl_a[o], E->cyl_u[o])) - pa.w);
       }
       const int li = a - off[r];
       for (int p = 0; p < rs[r].n_self; ++p) {

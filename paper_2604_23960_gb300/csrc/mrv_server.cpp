@@ -192,14 +192,34 @@ void mrv_server::launch(Slot &s) {
                         s.ev1);
   }
   if (!rc) {
+    int which = 0;
     cudaError_t e = cudaMemcpyAsync(valid_h, s.scratch.out_valid, nq, cudaMemcpyDeviceToHost, s.stream);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+      which = 1;
       e = cudaMemcpyAsync(conf_h, s.scratch.out_conf, sizeof(mrv_conflict) * nq, cudaMemcpyDeviceToHost, s.stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(err_h, s.scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream);
+    }
+    if (e == cudaSuccess) {
+      which = 2;
+      e = cudaMemcpyAsync(err_h, s.scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream);
+    }
     if (e != cudaSuccess) {
-      char what[160];
-      std::snprintf(what, sizeof what, "server result copy (%d queries, host %p, device %p %p %p)", nq, s.pin_out,
-                    (void *)s.scratch.out_valid, (void *)s.scratch.out_conf, (void *)s.scratch.err);
+      // what the runtime knows about the buffers, for the error report
+      auto kind = [](const void *p) {
+        cudaPointerAttributes a{};
+        const cudaError_t pe = cudaPointerGetAttributes(&a, p);
+        cudaGetLastError();
+        return pe == cudaSuccess ? (int)a.type : -1 - (int)pe;
+      };
+      const cudaError_t sq = cudaStreamQuery(s.stream);
+      cudaGetLastError();
+      char what[320];
+      std::snprintf(what, sizeof what,
+                    "server result copy %d (%d queries; host %p cap %zu type %d, conf %d..%d; device %p %p %p types "
+                    "%d %d %d; stream %d)",
+                    which, nq, s.pin_out, s.pin_out_cap, kind(s.pin_out), kind(conf_h),
+                    kind((char *)conf_h + sizeof(mrv_conflict) * nq - 1), (void *)s.scratch.out_valid,
+                    (void *)s.scratch.out_conf, (void *)s.scratch.err, kind(s.scratch.out_valid),
+                    kind(s.scratch.out_conf), kind(s.scratch.err), (int)sq);
       rc = cuda_fail(e, what);
     }
   }

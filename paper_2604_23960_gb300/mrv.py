@@ -52,7 +52,8 @@ class RobotDesc(C.Structure):
 
 
 class EnvDesc(C.Structure):
-    _fields_ = [("n_spheres", C.c_int32), ("spheres_xyzr", P), ("n_aabbs", C.c_int32), ("aabb_lohi", P)]
+    _fields_ = [("n_spheres", C.c_int32), ("spheres_xyzr", P), ("n_aabbs", C.c_int32), ("aabb_lohi", P),
+                ("n_cylinders", C.c_int32), ("cylinders", P)]
 
 
 class BatchS(C.Structure):
@@ -70,7 +71,7 @@ class Stats(C.Structure):
     _fields_ = [("states_available", C.c_uint64), ("states_checked", C.c_uint64), ("sphere_tests", C.c_uint64),
                 ("sphere_tests_available", C.c_uint64), ("work_items", C.c_uint64), ("n_valid", C.c_int32),
                 ("n_conflicts", C.c_int32), ("device_ms", C.c_float), ("box_tests", C.c_uint64),
-                ("fk_chains", C.c_uint64), ("spheres_placed", C.c_uint64)]
+                ("fk_chains", C.c_uint64), ("spheres_placed", C.c_uint64), ("cylinder_tests", C.c_uint64)]
 
 
 class Tuning(C.Structure):
@@ -290,8 +291,10 @@ def robot_desc(m: W.RobotModel, keep: list) -> RobotDesc:
 
 def env_desc(e: W.Env, keep: list) -> EnvDesc:
     s, b = _f32(e.spheres.reshape(-1, 4)), _f32(e.aabbs.reshape(-1, 6))
-    keep.extend([s, b])
-    return EnvDesc(s.shape[0], _ptr(s) if s.shape[0] else None, b.shape[0], _ptr(b) if b.shape[0] else None)
+    cy = _f32(np.asarray(getattr(e, "cylinders", np.zeros((0, 7)))).reshape(-1, 7))
+    keep.extend([s, b, cy])
+    return EnvDesc(s.shape[0], _ptr(s) if s.shape[0] else None, b.shape[0], _ptr(b) if b.shape[0] else None,
+                   cy.shape[0], _ptr(cy) if cy.shape[0] else None)
 
 
 class BatchArrays:

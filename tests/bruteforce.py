@@ -99,6 +99,15 @@ class Geometry:
                 e = np.maximum(np.maximum(bx[:3] - c, c - bx[3:]), 0.0)
                 if ((np.linalg.norm(e, axis=1) - r) < 0).any():
                     return True
+            for cy in np.asarray(getattr(self.env, "cylinders", np.zeros((0, 7)))).astype(np.float64):
+                a, b, rho = cy[:3], cy[3:6], cy[6]
+                L = np.linalg.norm(b - a)
+                u = (b - a) / L
+                s = (c - a) @ u
+                d = np.linalg.norm(c - a - s[:, None] * u, axis=1)
+                gap = np.hypot(np.maximum(np.maximum(-s, s - L), 0.0), np.maximum(d - rho, 0.0))
+                if ((gap - r) < 0).any():
+                    return True
         for a, bb in m.self_pairs.reshape(-1, 2):
             if np.linalg.norm(c[a] - c[bb]) - r[a] - r[bb] < 0:
                 return True

@@ -47,6 +47,7 @@ MUTANTS = {
     "cyl_caps_dropped": ("const double es = s < 0.0 ? -s : (s > L ? s - L : 0.0);", "const double es = 0.0;"),
     "cyl_axis_unnormalised": ("for (int k = 0; k < 3; ++k) u[k] /= L;", "for (int k = 0; k < 3; ++k) u[k] /= 1.0;"),
     "cyl_radius_dropped": ("const double ed = d > rho ? d - rho : 0.0;", "const double ed = d;"),
+    "cyl_ignored_in_mv": ("      for (int o = 0; o < e->n_cylinders; ++o) {", "      for (int o = 0; o < 0; ++o) {"),
 }
 
 PIN_ARGS = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",

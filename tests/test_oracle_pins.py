@@ -584,3 +584,24 @@ def test_disc_past_vertical_cylinder():
         assert O.Oracle(w).mv_min_clearance()[0] == pytest.approx(clr.min(), abs=1e-6)
         seen[expect] += 1
     assert min(seen) > 20
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bruteforce_tiny_cylinders(seed):
+    """Random scenes with obstacle cylinders: the oracle's MV against a numpy
+    restatement of the definition (its own cylinder distance), with and
+    without the other obstacles' share of collisions."""
+    w = tiny_workload(1300 + seed, n_queries=12, timed=bool(seed % 2), cylinders=5)
+    only = copy.deepcopy(w)   # the same scene with the cylinders as the only obstacles
+    only.envs[0].spheres = np.zeros((0, 4), np.float32)
+    only.envs[0].aabbs = np.zeros((0, 6), np.float32)
+    for ww, need in ((w, 2), (only, 2)):
+        mv = O.Oracle(ww).mv()
+        n_env = 0
+        for q in range(ww.batch.n_queries):
+            g = BF.Geometry(ww, q)
+            conf = BF.all_conflicts(g)
+            env = BF.any_env(g)
+            assert bool(mv[q]) == (not conf and not env)
+            n_env += env
+        assert n_env >= need

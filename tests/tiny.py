@@ -49,13 +49,19 @@ def random_robot(rng, kind=None):
                         np.array(pairs, np.int32).reshape(-1, 2))
 
 
-def random_env(rng, n_s=3, n_b=3):
+def random_env(rng, n_s=3, n_b=3, n_c=0):
     sph = np.zeros((n_s, 4), np.float32)
     sph[:, :3] = rng.uniform(-1.5, 1.5, (n_s, 3))
     sph[:, 3] = rng.uniform(0.05, 0.3, n_s)
     c = rng.uniform(-1.5, 1.5, (n_b, 3))
     h = rng.uniform(0.05, 0.3, (n_b, 3))
-    return W.Env(sph, np.concatenate([c - h, c + h], axis=1).astype(np.float32))
+    env = W.Env(sph, np.concatenate([c - h, c + h], axis=1).astype(np.float32))
+    if n_c:
+        a = rng.uniform(-1.5, 1.5, (n_c, 3))
+        d = rng.normal(size=(n_c, 3))
+        d *= rng.uniform(0.2, 1.0, (n_c, 1)) / np.linalg.norm(d, axis=1, keepdims=True)
+        env.cylinders = np.concatenate([a, a + d, rng.uniform(0.03, 0.25, (n_c, 1))], axis=1).astype(np.float32)
+    return env
 
 
 def random_config(rng, m: W.RobotModel):
@@ -65,10 +71,11 @@ def random_config(rng, m: W.RobotModel):
 
 
 def tiny_workload(seed: int, n_queries: int = 12, timed: bool = True, max_robots: int = 3,
-                  n_models: int = 5, max_steps: int = 6, resolution: float = 0.4, env: bool = True):
+                  n_models: int = 5, max_steps: int = 6, resolution: float = 0.4, env: bool = True,
+                  cylinders: int = 0):
     rng = np.random.default_rng(seed)
     models = [random_robot(rng) for _ in range(n_models)]
-    envs = [random_env(rng)] if env else []
+    envs = [random_env(rng, n_c=cylinders)] if env else []
     bb = W.BatchBuilder(3, timed)
     for _ in range(n_queries):
         n = int(rng.integers(1, max_robots + 1))
