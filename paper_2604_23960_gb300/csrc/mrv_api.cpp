@@ -710,9 +710,10 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
   h.dev.cyl_u = (const float4 *)h.d_cylu;
   h.dev.g_R = -1.f;
   if (G.R > 0) {
+    std::vector<uint32_t> cnt(G.ns.size());
+    for (size_t c = 0; c < cnt.size(); ++c) cnt[c] = (uint32_t)G.ns[c] | ((uint32_t)G.nb[c] << 16);
     if ((rc = upload(&h.d_goff, G.off.data(), sizeof(int32_t) * G.off.size())) ||
-        (rc = upload(&h.d_gns, G.ns.data(), sizeof(uint16_t) * G.ns.size())) ||
-        (rc = upload(&h.d_gnb, G.nb.data(), sizeof(uint16_t) * G.nb.size())) ||
+        (rc = upload(&h.d_gcnt, cnt.data(), sizeof(uint32_t) * cnt.size())) ||
         (rc = upload(&h.d_gitems, G.items.data(), sizeof(uint16_t) * std::max<size_t>(1, G.items.size())))) {
       h.free_all();
       return rc;
@@ -724,9 +725,8 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
     h.dev.g_inv_h = (float)(1.0 / G.h);
     h.dev.g_R = R;
     h.dev.g_off = (const int32_t *)h.d_goff;
-    h.dev.g_ns = (const uint16_t *)h.d_gns;
+    h.dev.g_cnt = (const uint32_t *)h.d_gcnt;
     h.dev.g_items = (const uint16_t *)h.d_gitems;
-    h.dev.g_nb = (const uint16_t *)h.d_gnb;
   }
   h.refs = 1;
   c->envs.push_back(h);

@@ -76,14 +76,14 @@ struct EnvDev {
   // uniform grid over the obstacles for frame bounding spheres of radius
   // <= g_R (g_R < 0: none): cell (ix, iy, iz) of a center x is
   // floor((x - g_lo) * g_inv_h) per axis; outside 0..g_dims-1 it overlaps no
-  // obstacle.  Cell c = (iz * g_dims[1] + iy) * g_dims[0] + ix lists
-  // g_ns[c] obstacle spheres, then boxes, at g_items[g_off[c] .. g_off[c+1]).
+  // obstacle.  Cell c = (iz * g_dims[1] + iy) * g_dims[0] + ix lists its
+  // obstacle spheres, boxes and cylinders (counts in g_cnt) at
+  // g_items[g_off[c] .. g_off[c+1]).
   float g_lo[3], g_inv_h, g_R;
   int32_t g_dims[3];
   const int32_t *g_off;
-  const uint16_t *g_ns;
+  const uint32_t *g_cnt;         // per cell: spheres | boxes << 16 (cylinders follow)
   const uint16_t *g_items;
-  const uint16_t *g_nb;          // boxes per cell (after its spheres; cylinders follow)
   // solid cylinders with flat caps
   int32_t n_cyl;
   int32_t pad2;

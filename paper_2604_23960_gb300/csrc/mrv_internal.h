@@ -65,11 +65,11 @@ struct HostModel {
 struct HostEnv {
   EnvDev dev{};
   void *d_spheres = nullptr, *d_k = nullptr, *d_lo = nullptr, *d_hi = nullptr;
-  void *d_goff = nullptr, *d_gns = nullptr, *d_gitems = nullptr, *d_gnb = nullptr;   // obstacle grid
+  void *d_goff = nullptr, *d_gcnt = nullptr, *d_gitems = nullptr;   // obstacle grid
   void *d_cyla = nullptr, *d_cylu = nullptr;                                          // cylinders
   int refs = 0;
   void free_all() {
-    for (void **p : {&d_spheres, &d_k, &d_lo, &d_hi, &d_goff, &d_gns, &d_gitems, &d_gnb, &d_cyla, &d_cylu}) {
+    for (void **p : {&d_spheres, &d_k, &d_lo, &d_hi, &d_goff, &d_gcnt, &d_gitems, &d_cyla, &d_cylu}) {
       if (*p) cudaFree(*p);
       *p = nullptr;
     }

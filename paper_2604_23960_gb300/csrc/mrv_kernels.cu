@@ -1209,8 +1209,9 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
             const int c = ((int)fz * gdy + (int)fy) * gdx + (int)fx;
             i0 = __ldg(&E.g_off[c]);
             i1 = __ldg(&E.g_off[c + 1]);
-            is = i0 + (int)__ldg(&E.g_ns[c]);
-            ib = is + (int)__ldg(&E.g_nb[c]);
+            const uint32_t cnt = __ldg(&E.g_cnt[c]);
+            is = i0 + (int)(cnt & 0xffffu);
+            ib = is + (int)(cnt >> 16);
           }
         } else {
           full = true;
