@@ -339,3 +339,35 @@ def test_full_ragged_1m(ctx):
     o = O.Oracle(w)
     PA.check_mv(o, v[idx[kind == 0]], idx[kind == 0])
     PA.check_ffc(o, c[idx[kind == 1]], idx[kind == 1])
+
+
+def test_longest_motions(ctx):
+    """T = MRV_MAX_STEPS (2^24 states): disc 0 drifts slowly far from a
+    stationary disc 1, then jumps onto it in a one-step segment, so the only
+    conflict is the last state (decidable); a second query jumps to a clear
+    spot instead (valid, compared on its exhaustive minimum clearance); one
+    step more than the limit is rejected."""
+    T = 1 << 24
+    disc = W.disc_robot(0.25)
+    bb = W.BatchBuilder(2, True)
+    for end in ((5.0, 5.0), (3.0, 3.0)):
+        bb.add([0, 0], [np.array([(1.0, 1.0), (1.0, 2.0), end], np.float32),
+                        np.array([(5.0, 5.0), (5.0, 5.0)], np.float32)], [[T - 1, 1], [T]])
+    w = W.Workload("long", [disc], [], bb.build(0.05), env=-1, check_env=False)
+    o = O.Oracle(w)
+    ba = ctx.bind(w)
+    assert list(o.query_T()) == [T, T]
+    c = ctx.ffc_find(ba)
+    np.testing.assert_array_equal(c, o.ffc(threads=2))
+    assert tuple(c[0]) == (T, 0, 1) and tuple(c[1]) == (-1, -1, -1)
+    v = ctx.mv_validate(ba, check_env=False)
+    assert list(v) == [0, 1]
+    v2, mc = ctx.mv_validate(ba, check_env=False, exhaustive=True, min_clearance=True)
+    np.testing.assert_allclose(mc, o.mv_min_clearance(check_env=False, threads=2), atol=PA.CLR_TOL, rtol=0)
+    st = ctx.stats()
+    assert st["states_checked"] == st["states_available"] == 2 * (T + 1)
+    bb = W.BatchBuilder(2, True)
+    bb.add([0, 0], [np.array([(1.0, 1.0), (2.0, 2.0)], np.float32), np.array([(5.0, 5.0), (5.0, 5.0)], np.float32)],
+           [[T + 1], [1]])
+    with pytest.raises(mrv.MrvError):
+        ctx.ffc_find(ctx.bind(W.Workload("toolong", [disc], [], bb.build(0.05), env=-1, check_env=False)))
