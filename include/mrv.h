@@ -7,10 +7,12 @@
  *   FindFirstConflict (FFC, Alg. 2): the earliest robot-robot conflict
  *                     (timestep, robot i, robot j).
  * Robots are kinematic chains (modified DH) or point robots, approximated by
- * spheres (Sec. II-B); obstacles are spheres and axis-aligned boxes ("simple
- * geometries", Sec. III-A); motions are start/goal pairs discretised at a
- * C-space resolution (Sec. IV-A3) or timed waypoint paths; shorter paths are
- * padded with their last configuration (Sec. III-A).
+ * spheres (Sec. II-B); obstacles are spheres, axis-aligned boxes ("simple
+ * geometries", Sec. III-A) and solid cylinders (the Cage obstacles, Sec. V-A);
+ * motions are start/goal pairs discretised at a C-space resolution
+ * (Sec. IV-A3) or timed waypoint paths; shorter paths are padded with their
+ * last configuration (Sec. III-A).  MV also comes in the prioritized
+ * planner's form (one robot against higher-priority paths, Sec. IV-C).
  *
  * Conventions for every entry point:
  *   - return value: MRV_OK (0) or a negative MRV_ERR_* code; no call aborts

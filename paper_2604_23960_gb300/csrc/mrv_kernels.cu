@@ -4,38 +4,43 @@
 // Work decomposition
 //   tile   32 states of one query, the GPU's batch of W = 32 timesteps
 //          (PackCfgBatch, Sec. III-A): MV packs them with the rake order
-//          t = b + nb*l (nb = ceil((T+1)/32)), FFC with the linear order
-//          t = 32b + l.
+//          t = b + nb*l (nb = ceil((T+1)/32)), FFC (and MV with MRV_LINEAR)
+//          with the linear order t = 32b + l.
 //   slice  a tile cut into `split` parts: MV slice p takes the rake lanes
-//          l = p, p+split, ... (still spread over the whole motion), FFC
-//          slice p takes consecutive states.  Point-robot queries keep whole
-//          tiles (split 1, one lane per state).
+//          l = p, p+split, ... (still spread over the whole motion) and visits
+//          them from the middle outwards; FFC slice p takes consecutive states
+//          in order.  Point-robot queries keep whole tiles (split 1, one lane
+//          per state).
 //   item   `cte` consecutive slices of one query, walked in order by one warp
 //          that stops once the query is decided (MV: any collision; FFC: a
-//          conflict at an earlier state).  Items are handed out by a global
-//          atomic counter in level order: every query's first item, then
-//          every query's second item, ... (queries sorted by item count), so
-//          coarse rake slices and early FFC states of all queries run first.
+//          conflict at an earlier state).  Items are claimed 1..32 at a time
+//          from a global counter in level order (every query's first item,
+//          then every query's second item, ...); a claim's lanes check the
+//          claimed items' verdicts in parallel, and only undecided ones run.
 //   phase  hierarchical MV (Alg. 1, hierarchical branch) runs every slice
 //          twice: first the robot-obstacle + self checks, then the pairs.
 // Two per-query flavors:
 //   A  (point robots, <= 16 spheres): lane l owns state t(l) of the tile and
 //      runs every check of that state; a ballot finds the first conflicting
 //      lane.
-//   B  (kinematic chains): the warp walks a slice's states; per FK round up
-//      to 8 lanes run the (state, robot) chains into shared-memory link
-//      frames, then per state the lanes place the spheres and split the
-//      sphere rows two at a time; __any_sync / __reduce_or_sync reduce.
+//   B  (kinematic chains): the warp walks a slice's states; per FK round 8
+//      (state, robot) chains run on three lanes each (one row of the link
+//      frames per lane) into shared memory.  Per state (broadphase path, the
+//      default): frame bounding spheres; obstacles from the grid cell of each
+//      frame, self-pair groups and frame pairs of other robots go to
+//      candidate lists; only the named frames' spheres are placed; the lists
+//      are resolved over all lanes (self pairs as row-mask blocks).  With
+//      MRV_NO_BROADPHASE every sphere pair is tested (dense path, below).
 //
-// Sphere-pair test of flavor B.  With centers p relative to an origin near
-// the query and k = |p|^2 - r^2, two spheres overlap iff
+// Sphere-pair test of the dense path.  With centers p relative to an origin
+// near the query and k = |p|^2 - r^2, two spheres overlap iff
 //     u = k_b - 2 p_a.p_b - 2 r_a r_b  <  -k_a
 // (the expanded |p_a - p_b|^2 < (r_a + r_b)^2): four FMAs per test and one
 // running minimum per row.  The rounding error of u and k is below
 // 24 u (C^2 + rho^2) (C: largest |p|, rho: largest radius, u = 2^-24);
 // a row whose minimum falls within twice that band of -k_a is decided again
 // by the direct formula, so decisions are those of the direct FP32 formula
-// wherever the two could differ.
+// wherever the two could differ.  The broadphase path uses the direct formula.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <stdint.h>
