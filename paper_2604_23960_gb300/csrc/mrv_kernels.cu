@@ -45,6 +45,8 @@
 #include <float.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "mrv_dev.h"
 
 namespace mrv {
@@ -2041,11 +2043,25 @@ cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The dynamic shared memory limit of k_main is a process-wide attribute (per
+// device): it is raised once to what the largest block (12 warps) needs, so
+// launches with fewer warps on other threads never see it shrink under them.
 cudaError_t set_main_attrs(int warps) {
-  const int bytes = (int)main_smem_bytes(warps);
-  cudaError_t e = cudaFuncSetAttribute(k_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  (void)warps;
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static bool done[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
+  const int bytes = (int)main_smem_bytes(12);
+  e = cudaFuncSetAttribute(k_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
 }
 
 cudaError_t max_blocks_per_sm(int warps, bool clr, int *out) {
