@@ -308,6 +308,30 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
                             "valid_total": f"{nvalid}/{w.batch.n_queries}",
                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
                             "kernel_ms": st["device_ms"], "tuning": tune}
+    # the 16-arm Cage team (8 floor- and 8 ceiling-mounted arms, 1024 spheres
+    # and 120 robot pairs per state: the large-team kernel): MV on 10k
+    # planner-like edges of at most 0.5 rad, FFC on 10k whole motions
+    w = W.make_cage16_mv(10000)
+    ba = ctx.bind(w).to("cuda")
+    tune = autotune(ctx, w, mrv.MRV_CHECK_ENV, kind=0)
+    dt = timed(lambda: ctx.mv_validate(ba))
+    st = ctx.stats()
+    nvalid = int(ctx.mv_validate(ba).sum().item())
+    pq = per_query(w, lambda b: ctx.mv_validate(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
+    out["cage16_cyl_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
+                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
+                             "valid_total": f"{nvalid}/{w.batch.n_queries}",
+                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
+                             "kernel_ms": st["device_ms"], "tuning": tune}
+    w = W.make_cage16_ffc(10000)
+    ba = ctx.bind(w).to("cuda")
+    dt = timed(lambda: ctx.ffc_find(ba))
+    st = ctx.stats()
+    pq = per_query(w, lambda b: ctx.ffc_find(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
+    out["cage16_ffc_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
+                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
+                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
+                             "kernel_ms": st["device_ms"]}
     # prioritized planning's edge checks (Sec. IV-C): 10k cage edges, one arm
     # against the cage, itself and three higher-priority arms' timed paths
     w = W.make_cage_priority(10000)

@@ -49,11 +49,15 @@ extern "C" {
 #define MRV_ERR_LIMIT (-7)     /* a size beyond a documented maximum        */
 
 /* ---- limits ------------------------------------------------------------ */
-#define MRV_MAX_ROBOTS 8          /* robots per query (28 pairs)            */
-#define MRV_MAX_DOF 8             /* joints per robot                       */
-#define MRV_MAX_SPHERES 256       /* spheres per robot model                */
-#define MRV_MAX_QUERY_SPHERES 512 /* spheres summed over a query's robots   */
-#define MRV_MAX_STEPS (1 << 24)   /* composite step count T of a query      */
+/* Queries of up to 8 robots and 512 spheres run on the team kernel layout;
+ * larger ones (the 16-arm Cage team of Sec. V-A) on a second kernel instance
+ * with a larger per-warp layout, launched after the first when a batch may
+ * hold such queries (always for MRV_PTRS_ON_DEVICE batches). */
+#define MRV_MAX_ROBOTS 16          /* robots per query (120 pairs)          */
+#define MRV_MAX_DOF 8              /* joints per robot                      */
+#define MRV_MAX_SPHERES 256        /* spheres per robot model               */
+#define MRV_MAX_QUERY_SPHERES 1024 /* spheres summed over a query's robots  */
+#define MRV_MAX_STEPS ((1 << 24) - 1) /* composite step count T of a query  */
 
 /* ---- robot kinds ------------------------------------------------------- */
 #define MRV_ROBOT_DH_CHAIN 0

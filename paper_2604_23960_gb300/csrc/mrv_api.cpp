@@ -76,9 +76,9 @@ size_t Scratch::layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char 
   set(&q_best, sizeof(int32_t) * nq);
   set(&q_minclr, sizeof(float) * nq);
   set(&sorted, sizeof(int32_t) * nq);
-  set(&hist, sizeof(int32_t) * (kMaxLevels + 1));
-  set(&level_start, sizeof(int32_t) * (kMaxLevels + 1));
-  set(&cursor, sizeof(int32_t) * (kMaxLevels + 1));
+  set(&hist, sizeof(int32_t) * kLevelBins);
+  set(&level_start, sizeof(int32_t) * kLevelBins);
+  set(&cursor, sizeof(int32_t) * kLevelBins);
   set(&counters, sizeof(int32_t) * 8);
   set(&err, sizeof(uint32_t) * 2);
   set(&stats, sizeof(unsigned long long) * kNumStats);
@@ -167,6 +167,30 @@ int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
   return MRV_OK;
 }
 
+// Whether a batch may hold queries of work class 1 (more than kTeamRobots
+// robots or kTeamSpheres spheres), whose kernel instance is then launched too.
+// Host batches are scanned (robots per query first; sphere sums only when the
+// largest model could exceed the bound); device batches may hold any.
+static int maybe_large(const mrv_ctx *ctx, const mrv_batch *b) {
+  if (b->flags & MRV_PTRS_ON_DEVICE) return 1;
+  int n_max = 0;
+  for (int q = 0; q < b->n_queries; ++q) n_max = std::max(n_max, b->q_robot_off[q + 1] - b->q_robot_off[q]);
+  if (n_max > kTeamRobots) return 1;
+  int m_max = 0;
+  for (const auto &m : ctx->models) m_max = std::max(m_max, m.dev.n_spheres);
+  if (n_max * m_max <= kTeamSpheres) return 0;
+  const int n_models = (int)ctx->models.size();
+  for (int q = 0; q < b->n_queries; ++q) {
+    int M = 0;
+    for (int s = b->q_robot_off[q]; s < b->q_robot_off[q + 1]; ++s) {
+      const int id = b->slot_robot_id[s];
+      if (id >= 0 && id < n_models) M += ctx->models[id].dev.n_spheres;
+    }
+    if (M > kTeamSpheres) return 1;
+  }
+  return 0;
+}
+
 BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int slices_per_item) {
   BatchDev B;
   std::memset(&B, 0, sizeof B);
@@ -205,6 +229,7 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
   B.envs = ctx->d_envs;
   B.n_envs = (int32_t)ctx->envs.size();
   B.clock_budget = ctx->clock_budget;
+  B.maybe_large = b->n_queries > 0 ? maybe_large(ctx, b) : 0;
   return B;
 }
 
@@ -226,9 +251,9 @@ int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st) {
   return MRV_OK;
 }
 
-int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm) {
+int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
   int occ = 0;
-  if (max_blocks_per_sm(warps, clr, &occ) != cudaSuccess || occ < 1) {
+  if (max_blocks_per_sm(warps, clr, cls, &occ) != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
   }
@@ -246,7 +271,7 @@ int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *
 int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
                    mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
   cudaGetLastError();   // the launch checks below report this sequence's errors only
-  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
@@ -261,8 +286,14 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return cuda_fail(e, "capture status");
   const unsigned rec_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev0 && (e = cudaEventRecordWithFlags(ev0, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
-  e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm), warps, clr, -1, st);
+  e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm, 0), warps, clr, 0, -1, st);
   if (e != cudaSuccess) return cuda_fail(e, "main launch");
+  // queries beyond the team layout: the large-team instance, after the first
+  if (B.maybe_large) {
+    const int lw = large_warps();
+    e = launch_main(B, grid_for(ctx, lw, clr, 0, 1), lw, clr, 1, -1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "large-team launch");
+  }
   if (ev1 && (e = cudaEventRecordWithFlags(ev1, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
   if ((e = launch_finish(B, valid, minclr, conf, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish launch");
   return MRV_OK;
@@ -353,7 +384,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
     if ((rc = enqueue_run(ctx, B, S, clr, v_dst, m_dst, c_dst, true))) return rc;
   } else {
     // baseline: one synchronous launch per query (grid = the query's chunks)
-    cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+    cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
@@ -368,7 +399,8 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
     cudaEventRecord(ctx->ev0, st);
     for (int q = 0; q < b->n_queries; ++q) {
       if (hq[q].bits & 4u || hq[q].nchunks == 0) continue;
-      if ((e = launch_main(B, hq[q].nchunks, 1, clr, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
+      const int cls = (hq[q].bits & 8u) ? 1 : 0;
+      if ((e = launch_main(B, hq[q].nchunks, 1, clr, cls, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "query synchronize");
     }
     cudaEventRecord(ctx->ev1, st);
@@ -841,7 +873,7 @@ int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, 
   const bool dev = b->flags & MRV_PTRS_ON_DEVICE;
   BatchDev B = make_batchdev(c, b, S, MRV_KIND_MV, 1);
   cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * (kMaxLevels + 1), st);
+  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
   if (e == cudaSuccess) e = launch_prepare(B, st);
@@ -902,7 +934,8 @@ int mrv_graph_create(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_con
   BatchDev B = make_batchdev(c, b, g->scratch, -1, c->tuning.slices_per_item);
   // attributes are set outside the capture
   set_main_attrs(c->tuning.warps_per_block);
-  grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm);
+  grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm, 0);
+  grid_for(c, large_warps(), false, 0, 1);
   cudaStream_t cap = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {

@@ -19,6 +19,14 @@ constexpr int kMaxLinks = MRV_MAX_DOF + 2;  // frames 0..dof+1
 constexpr int kMaxLevels = 256;       // work levels (work items per query)
 constexpr int kEnvIdBase = 1 << 20;   // env ids = kEnvIdBase + env slot
 constexpr int kFkChains = 8;          // (state, robot) chains per FK round
+// Queries of up to kTeamRobots robots and kTeamSpheres spheres form work
+// class 0 (the team kernel layout); larger ones, up to MRV_MAX_ROBOTS and
+// MRV_MAX_QUERY_SPHERES, work class 1 (the large-team layout).  Each class has
+// its own work levels: kLevelBins = 2 x (kMaxLevels + 1) histogram, cursor
+// and level-start bins.
+constexpr int kTeamRobots = 8;
+constexpr int kTeamSpheres = 512;
+constexpr int kLevelBins = 2 * (kMaxLevels + 1);
 constexpr int kNumStats = 9;          // statistics counters of a call (see mrv_stats)
 
 // device error bits (BatchDev::err)
@@ -104,7 +112,8 @@ struct QueryDev {
   int32_t nchunks;    // work items of this query
   int32_t cte;        // slices per work item
   int32_t env;        // env slot or -1
-  uint32_t bits;      // bit 0: FFC, bit 1: flavor A (lane = state), bit 2: invalid
+  uint32_t bits;      // bit 0: FFC, bit 1: flavor A (lane = state), bit 2: invalid,
+                      // bit 3: work class 1 (more than kTeamRobots robots or kTeamSpheres spheres)
   float rho2;         // largest squared sphere radius of the query's robots
   int32_t pad;
   long long pairtests;  // robot-robot sphere tests per state
@@ -133,13 +142,15 @@ struct BatchDev {
   int32_t *slot_tau;                 // n_waypoints: time of each waypoint
   QueryDev *q;                       // n_queries
   int32_t *q_hit;                    // MV: 1 once a collision is found
-  int32_t *q_best;                   // FFC: min key t*32 + pair index
+  int32_t *q_best;                   // FFC: min key t << 7 | pair index
   float *q_minclr;                   // exhaustive MV: min clearance (as ordered int)
   int32_t *sorted;                   // queries sorted by nchunks (desc)
-  int32_t *hist;                     // kMaxLevels + 1 bins
-  int32_t *level_start;              // kMaxLevels + 1
-  int32_t *cursor;                   // kMaxLevels + 1
-  int32_t *counters;                 // [0] work counter, [1] n_items, [2] abort flag
+  int32_t *hist;                     // kLevelBins bins (class 0, then class 1)
+  int32_t *level_start;              // kLevelBins
+  int32_t *cursor;                   // kLevelBins
+  int32_t *counters;                 // [0] class-0 work counter, [1] class-0 items, [2] abort flag,
+                                     // [3] class-1 items, [4] class-1 work counter,
+                                     // [5] class-0 queries (first sorted position of class 1)
   uint32_t *err;
   unsigned long long *stats;         // [0] states checked, [1] tests executed,
                                      // [2] states available, [3] tests available,
@@ -151,6 +162,8 @@ struct BatchDev {
   const EnvDev *envs;
   int32_t n_envs;
   long long clock_budget;            // persistent kernel: clock64 ticks (0 = none)
+  int32_t maybe_large;               // host: the batch may hold class-1 queries (launch their kernel)
+  int32_t pad1;
 };
 
 }  // namespace mrv

@@ -77,11 +77,12 @@ struct HostEnv {
 };
 
 // kernel launch wrappers (mrv_kernels.cu)
-size_t main_smem_bytes(int warps);
+size_t main_smem_bytes(int warps, int cls);   // cls: work class (0 team, 1 large team)
+int large_warps();                             // warps per block of the large-team instance
 cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st);
 cudaError_t set_main_attrs(int warps);
-cudaError_t max_blocks_per_sm(int warps, bool clr, int *out);
-cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int q_single, cudaStream_t st);
+cudaError_t max_blocks_per_sm(int warps, bool clr, int cls, int *out);
+cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int cls, int q_single, cudaStream_t st);
 cudaError_t launch_finish(const BatchDev &B, uint8_t *valid, float *minclr, mrv_conflict *conf, int *counts,
                           cudaStream_t st);
 cudaError_t launch_clearance(const BatchDev &B, int q, const int32_t *ts, int nt, int check_env, float *out,
@@ -130,6 +131,6 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
                    mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
 int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st);
 int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr, mrv_conflict *conf);
-int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm);
+int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls);
 int check_device_err(uint32_t err);
 }  // namespace mrv

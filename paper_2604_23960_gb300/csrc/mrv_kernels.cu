@@ -19,13 +19,19 @@
 //          claimed items' verdicts in parallel, and only undecided ones run.
 //   phase  hierarchical MV (Alg. 1, hierarchical branch) runs every slice
 //          twice: first the robot-obstacle + self checks, then the pairs.
+//   class  queries of up to 8 robots and 512 spheres (class 0) run on the
+//          team layout of per-warp shared memory, 12 warps per SM; larger
+//          ones, up to 16 robots and 1024 spheres (the 16-arm Cage team),
+//          on the large-team layout; k_main is instantiated per layout and
+//          each instance takes its class's items (own levels and counter).
 // Two per-query flavors:
 //   A  (point robots, <= 16 spheres): lane l owns state t(l) of the tile and
 //      runs every check of that state; a ballot finds the first conflicting
 //      lane.
-//   B  (kinematic chains): the warp walks a slice's states; per FK round 8
-//      (state, robot) chains run on three lanes each (one row of the link
-//      frames per lane) into shared memory.  Per state (broadphase path, the
+//   B  (kinematic chains): the warp walks a slice's states; per FK round up
+//      to 8 (state, robot) chains (16 for a 16-robot team) run on three lanes
+//      each (one row of the link frames per lane, ten chains at a time) into
+//      shared memory.  Per state (broadphase path, the
 //      default): frame bounding spheres; obstacles from the grid cell of each
 //      frame, self-pair groups and frame pairs of other robots go to
 //      candidate lists; only the named frames' spheres are placed; the lists
@@ -93,8 +99,11 @@ constexpr int kCand = 64;        // broadphase candidates per list and state
 
 // Candidates of one state found by the bounding-sphere tests, and the frames
 // whose spheres must be placed to resolve them (bit k of need/placed = frame
-// slot k = robot k / kMaxLinks, frame k % kMaxLinks).
+// slot k = robot k / kMaxLinks, frame k % kMaxLinks), for queries of up to NR
+// robots (frame slots < 256).
+template <int NR>
 struct Cands {
+  static constexpr int kWords = (NR * kMaxLinks + 31) / 32;   // frame-slot mask words
   uint32_t pc[kCand];        // robot-robot: frame slot k << 8 | frame slot k2
   uint32_t ec[kCand];        // frame slot << 24 | obstacle sphere
   uint32_t bc[kCand];        // frame slot << 24 | obstacle box
@@ -104,19 +113,27 @@ struct Cands {
   int32_t pf[kCand + 1];     // exclusive prefix of the tests of the list being resolved
   uint32_t yc[kCand];        // frame slot << 24 | obstacle cylinder
   int32_t np, ne, nb, ns, overflow, ny;
-  uint32_t need[3], placed[3];
+  uint32_t need[kWords], placed[kWords];
 };
-static_assert(sizeof(Cands) <= sizeof(float) * MRV_MAX_QUERY_SPHERES, "candidate lists fit the K array");
 
 constexpr int kEnvCache = 64;    // obstacle spheres staged per warp (more: read from L1)
 constexpr int kBoxCache = 32;    // obstacle boxes staged per warp
 
-struct WarpSmem {
+// Per-warp shared memory of the persistent kernel for queries of up to NR
+// robots and MQ spheres.  Two layouts are instantiated: the team layout (8
+// robots, 512 spheres), sized so that 12 warps share an SM, and the
+// large-team layout (16 robots, 1024 spheres) of a second kernel instance
+// that takes the queries beyond the first (work class 1).
+template <int NR, int MQ>
+struct WarpSmemT {
+  static constexpr int kRobots = NR, kSpheres = MQ, kClass = NR > kTeamRobots ? 1 : 0;
+  static constexpr int kChains = NR > kFkChains ? NR : kFkChains;   // FK chains held at once
+  using Cl = Cands<NR>;
   TileCtx ctx;               // the current work item's query parameters
-  RobotSlot rs[MRV_MAX_ROBOTS];
-  int32_t off[MRV_MAX_ROBOTS + 1];
-  int32_t seg[MRV_MAX_ROBOTS];   // per robot: waypoint index of the segment of the
-                                 // latest FK round (states grow within a slice)
+  RobotSlot rs[NR];
+  int32_t off[NR + 1];
+  int32_t seg[NR];           // per robot: waypoint index of the segment of the
+                             // latest FK round (states grow within a slice)
   float ox, oy, oz;          // origin of the relative frame (world)
   int32_t pad[4];
   float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
@@ -126,28 +143,45 @@ struct WarpSmem {
   // with m = ceil(4096 / n_links_j) (frame pair g of the pair is (g m >> 12,
   // g mod n_links_j), exact for g < 100), and the exclusive prefix of their
   // frame-pair counts n_links_i x n_links_j
-  uint32_t rp[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2];
-  int16_t rpf[MRV_MAX_ROBOTS * (MRV_MAX_ROBOTS - 1) / 2 + 2];
-  float4 BS[MRV_MAX_ROBOTS * kMaxLinks];  // per (robot, frame) bounding sphere at the
-                                          // current state (center relative to o; w < 0: none)
+  uint32_t rp[NR * (NR - 1) / 2];
+  int16_t rpf[NR * (NR - 1) / 2 + 2];
+  float4 BS[NR * kMaxLinks];  // per (robot, frame) bounding sphere at the
+                              // current state (center relative to o; w < 0: none)
   union {
     struct {
-      float xf[kFkChains * kMaxLinks * 12];   // link frames of one FK round
-      float4 P[MRV_MAX_QUERY_SPHERES];         // centers relative to o, radius
+      float xf[kChains * kMaxLinks * 12];   // link frames of one FK round
+      float4 P[MQ];                         // centers relative to o, radius
       union {
-        float K[MRV_MAX_QUERY_SPHERES];        // dense path: |p|^2 - r^2
-        Cands cl;                              // broadphase: candidate lists
+        float K[MQ];                        // dense path: |p|^2 - r^2
+        Cl cl;                              // broadphase: candidate lists
       };
     } b;
-    float4 PA[kFlavorAMaxSpheres * kWarp];     // flavor A: world centers per lane
+    float4 PA[kFlavorAMaxSpheres * kWarp];  // flavor A: world centers per lane
   } u;
+  static_assert(sizeof(Cl) <= sizeof(float) * MQ, "candidate lists fit the K array");
+  static_assert(NR <= 16 && NR * kMaxLinks < 256, "robot and frame-slot indices fit their fields");
 };
+using WarpSmemTeam = WarpSmemT<kTeamRobots, kTeamSpheres>;
+using WarpSmemLarge = WarpSmemT<MRV_MAX_ROBOTS, MRV_MAX_QUERY_SPHERES>;
 
-__host__ __device__ constexpr size_t warp_smem_bytes() { return (sizeof(WarpSmem) + 15) & ~size_t(15); }
-// 12 warps (3 blocks of 4) must fit the SM's 228 KB with 1 KB reserved per block
-static_assert(12 * ((sizeof(WarpSmem) + 15) & ~size_t(15)) + 3 * 1024 <= 233472, "shared memory per warp");
+template <class WS>
+__host__ __device__ constexpr size_t warp_smem_bytes() { return (sizeof(WS) + 15) & ~size_t(15); }
+// team layout: 12 warps (3 blocks of 4) must fit the SM's 228 KB with 1 KB reserved per block
+static_assert(12 * warp_smem_bytes<WarpSmemTeam>() + 3 * 1024 <= 233472, "shared memory per warp");
+// large-team layout: blocks of kLargeWarps warps, one per SM
+constexpr int kLargeWarps = (int)((233472 - 1024) / warp_smem_bytes<WarpSmemLarge>()) > 8
+                                ? 8 : (int)((233472 - 1024) / warp_smem_bytes<WarpSmemLarge>());
+static_assert(kLargeWarps >= 4, "large-team layout fits 4 warps per SM");
 
 __device__ __forceinline__ int pair_index(int i, int j, int n) { return i * n - i * (i + 1) / 2 + (j - i - 1); }
+
+// FFC keys order the conflicts of a query lexicographically by (t, i, j):
+// key = t << kKeyShift | pair index (pairs in (i, j) order, fewer than 128).
+// Per state, the colliding pairs are reduced to one code, 128 - pair index
+// of the first, so the largest code names the first pair and 0 means none.
+constexpr int kKeyShift = 7;
+__device__ __forceinline__ unsigned pair_code(int p) { return (unsigned)(128 - p); }
+__device__ __forceinline__ int code_key(int t, unsigned code) { return (t << kKeyShift) | (128 - (int)code); }
 
 // ordered-int encoding of floats so that atomicMin on int orders like floats
 __device__ __forceinline__ int f2ord(float f) {
@@ -257,6 +291,7 @@ __global__ void k_prep(BatchDev B) {
     Q.rho2 = rho2;
     const bool flavor_a = all_point && M <= kFlavorAMaxSpheres;
     if (flavor_a) Q.bits |= 2u;
+    if (n > kTeamRobots || M > kTeamSpheres) Q.bits |= 8u;   // large-team kernel
     const bool mv = !(Q.bits & 1u);
     const bool check_env = mv && (B.flags & MRV_CHECK_ENV);
     Q.ntiles = (int)((T + 1 + kWarp - 1) / kWarp);
@@ -299,33 +334,42 @@ __global__ void k_prep(BatchDev B) {
   B.q_hit[q] = 0;
   B.q_best[q] = 0x7fffffff;
   B.q_minclr[q] = __int_as_float(f2ord(INFINITY));
-  atomicAdd(&B.hist[Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks], 1);
+  atomicAdd(&B.hist[((Q.bits & 8u) ? kMaxLevels + 1 : 0) + (Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks)], 1);
 }
 
-// level layout: queries sorted by item count (descending); level c holds the
-// queries with more than c items, which are the first cnt_c sorted queries.
+// level layout, per work class: the class's queries sorted by item count
+// (descending), class 0 first; level c holds the class's queries with more
+// than c items, which are its first cnt_c sorted queries.
 __global__ void k_levels(BatchDev B) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int start = 0;
-  for (int k = kMaxLevels; k >= 0; --k) {
-    B.cursor[k] = start;           // first sorted position of item count k
-    start += B.hist[k];
+  for (int cls = 0; cls < 2; ++cls) {
+    const int *hist = B.hist + cls * (kMaxLevels + 1);
+    int *cursor = B.cursor + cls * (kMaxLevels + 1);
+    int *level_start = B.level_start + cls * (kMaxLevels + 1);
+    const int qbase = start;         // first sorted position of the class
+    for (int k = kMaxLevels; k >= 0; --k) {
+      cursor[k] = start;             // first sorted position of item count k
+      start += hist[k];
+    }
+    int acc = 0;
+    level_start[0] = 0;
+    for (int c = 0; c < kMaxLevels; ++c) {
+      acc += cursor[c] - qbase;      // the class's queries with more than c items
+      level_start[c + 1] = acc;
+    }
+    B.counters[cls ? 3 : 1] = acc;   // the class's work items
+    if (cls == 0) B.counters[5] = start;
   }
-  int acc = 0;
-  B.level_start[0] = 0;
-  for (int c = 0; c < kMaxLevels; ++c) {
-    acc += B.cursor[c];            // queries with more than c items
-    B.level_start[c + 1] = acc;
-  }
-  B.counters[1] = acc;             // number of work items
 }
 
 __global__ void k_scatter(BatchDev B) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= B.n_queries) return;
-  int c = B.q[q].nchunks;
+  const QueryDev &Q = B.q[q];
+  int c = Q.nchunks;
   if (c > kMaxLevels) c = kMaxLevels;
-  const int pos = atomicAdd(&B.cursor[c], 1);
+  const int pos = atomicAdd(&B.cursor[((Q.bits & 8u) ? kMaxLevels + 1 : 0) + c], 1);
   B.sorted[pos] = q;
 }
 
@@ -583,9 +627,9 @@ __device__ __forceinline__ int slice_valid(const TileCtx &C, int k) {
 // flavor A: one lane per state (point robots)
 // ---------------------------------------------------------------------------
 
-// MV -> 1 if a collision was found; FFC -> smallest key t*32 + pair or INT_MAX
-template <bool CLR>
-__device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int lane, float &minclr, bool do_env,
+// MV -> 1 if a collision was found; FFC -> smallest key (t << kKeyShift | pair) or INT_MAX
+template <bool CLR, class WS>
+__device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, float &minclr, bool do_env,
                        bool do_pairs) {
   const int t = slice_state(C, k, lane);
   const bool valid = t <= C.T;
@@ -683,7 +727,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   if (!m) return 0x7fffffff;
   const int l0 = __ffs(m) - 1;
   const int p0 = __shfl_sync(0xffffffffu, first, l0);
-  return slice_state(C, k, l0) * 32 + p0;
+  return (slice_state(C, k, l0) << kKeyShift) | p0;
 }
 
 // ---------------------------------------------------------------------------
@@ -793,13 +837,13 @@ __device__ bool pairs_mv(const float4 *P, const float *K, const int *off, int n,
   return hit;
 }
 
-// FFC robot-robot checks at one state: bitmask of colliding pairs
+// FFC robot-robot checks at one state: code of the first colliding pair (0: none)
 __device__ unsigned pairs_ffc(const float4 *P, const float *K, const int *off, int n, int lane, float eps) {
   unsigned pm = 0;
   for (int i = 0; i + 1 < n; ++i)
     for (int j = i + 1; j < n; ++j) {
       const bool h = rect_test(P, off[i], off[i + 1], P, K, off[j], off[j + 1], 0.f, 0.f, 0.f, eps, lane);
-      if (__any_sync(0xffffffffu, h)) pm |= 1u << pair_index(i, j, n);
+      if (__any_sync(0xffffffffu, h)) pm = max(pm, pair_code(pair_index(i, j, n)));
     }
   return pm;
 }
@@ -807,7 +851,8 @@ __device__ unsigned pairs_ffc(const float4 *P, const float *K, const int *off, i
 // MV robot-obstacle checks (obstacle spheres staged in shared memory up to
 // the cache size, the rest read through L1; boxes by the clamp distance) and
 // self-collision pairs (rectangles of the model, or its sparse pair list)
-__device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, const float *K, int lane, float cw2,
+template <class WS>
+__device__ bool env_mv(const TileCtx &C, const WS &S, const float4 *P, const float *K, int lane, float cw2,
                        float eps) {
   const int M = C.env_rows;   // spheres with obstacle checks
   bool hit = false;
@@ -869,7 +914,8 @@ __device__ bool env_mv(const TileCtx &C, const WarpSmem &S, const float4 *P, con
 
 // bounding spheres of every (robot, frame) at the state whose frames sit in
 // FK slot jj of xf
-__device__ void link_spheres(const TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane) {
+template <class WS>
+__device__ void link_spheres(const TileCtx &C, WS &S, const float *xf, int jj, int lane) {
   const int n = C.n;
   for (int k = lane; k < n * kMaxLinks; k += kWarp) {
     const int r = k / kMaxLinks, l = k - r * kMaxLinks;
@@ -887,11 +933,12 @@ __device__ void link_spheres(const TileCtx &C, WarpSmem &S, const float *xf, int
   }
 }
 
-// robot-robot checks: MV -> 1 on a collision; FFC -> bitmask of colliding
-// pairs.  Lane k owns the bounding sphere of (robot i, frame u) and scans the
+// robot-robot checks: MV -> 1 on a collision; FFC -> code of the first
+// colliding pair (0: none).  Lane k owns the bounding sphere of (robot i, frame u) and scans the
 // frame spheres of every later robot (broadcast reads); where two overlap
 // the lane tests their spheres itself (overlaps are rare).
-__device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, bool ffc,
+template <class WS>
+__device__ unsigned pairs_broad(const TileCtx &C, const WS &S, const float4 *P, int lane, bool ffc,
                                 unsigned long long &ntests) {
   unsigned pm = 0;
   const int nk = C.n * kMaxLinks;
@@ -914,7 +961,7 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float
           for (int b = b0; b < b1; ++b) h |= sph_hit(pa, P[b]);
           ntests += (unsigned long long)(b1 - b0);
         }
-        if (h) pm |= ffc ? (1u << pair_index(i, j, C.n)) : 1u;
+        if (h) pm = ffc ? max(pm, pair_code(pair_index(i, j, C.n))) : 1u;
       }
     }
   }
@@ -924,7 +971,8 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WarpSmem &S, const float
 // robot-obstacle and self checks (MV with the environment).  Lane k owns
 // the bounding sphere of (robot r, frame l) and scans the obstacle spheres and
 // boxes (broadcast reads); overlaps are resolved sphere by sphere in the lane.
-__device__ bool env_broad(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, unsigned long long &ntests,
+template <class WS>
+__device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int lane, unsigned long long &ntests,
                           unsigned long long &nbox, unsigned long long &ncyl) {
   bool hit = false;
   const int nk = C.self_robots * kMaxLinks;   // frames of the robots with obstacle checks
@@ -1031,7 +1079,8 @@ __device__ __forceinline__ void push_obst(uint32_t *list, int32_t *count, int32_
   else push_cand(list, count, overflow, ((uint32_t)k << 24) | (uint32_t)e);
 }
 
-__device__ __forceinline__ void need_frame(Cands &cl, int k) { atomicOr(&cl.need[k >> 5], 1u << (k & 31)); }
+template <class CL>
+__device__ __forceinline__ void need_frame(CL &cl, int k) { atomicOr(&cl.need[k >> 5], 1u << (k & 31)); }
 
 // Exclusive prefix of the per-item test counts c (lane i0 + lane holds item
 // i0 + lane's) into pf, called for i0 = 0, 32, ...; returns the new base.
@@ -1046,18 +1095,21 @@ __device__ __forceinline__ int scan_chunk(int32_t *pf, int i, int n, int c, int 
   return base + __shfl_sync(0xffffffffu, x, kWarp - 1);
 }
 
-__device__ __forceinline__ int frame_count(const WarpSmem &S, int k) {
+template <class WS>
+__device__ __forceinline__ int frame_count(const WS &S, int k) {
   const int r = k / kMaxLinks, l = k - r * kMaxLinks;
   return S.rs[r].ls[l + 1] - S.rs[r].ls[l];
 }
 
-__device__ __forceinline__ int frame_first(const WarpSmem &S, int k) {
+template <class WS>
+__device__ __forceinline__ int frame_first(const WS &S, int k) {
   const int r = k / kMaxLinks, l = k - r * kMaxLinks;
   return S.off[r] + S.rs[r].ls[l];
 }
 
 // prefix of spheres-per-frame over a list of frame-slot << 24 entries
-__device__ int scan_frames(Cands &cl, const uint32_t *list, int n, const WarpSmem &S, int lane) {
+template <class CL, class WS>
+__device__ int scan_frames(CL &cl, const uint32_t *list, int n, const WS &S, int lane) {
   int base = 0;
   for (int i0 = 0; i0 < n; i0 += kWarp) {
     const int i = i0 + lane;
@@ -1070,16 +1122,20 @@ __device__ int scan_frames(Cands &cl, const uint32_t *list, int n, const WarpSme
 }
 
 // places the spheres of the frames marked in cl.need and not placed yet
-__device__ void place_needed(const TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane, BroadAcc &acc) {
-  Cands &cl = S.u.b.cl;
-  const uint32_t w0 = cl.need[0] & ~cl.placed[0], w1 = cl.need[1] & ~cl.placed[1], w2 = cl.need[2] & ~cl.placed[2];
-  if (!(w0 | w1 | w2)) return;
+template <class WS>
+__device__ void place_needed(const TileCtx &C, WS &S, const float *xf, int jj, int lane, BroadAcc &acc) {
+  auto &cl = S.u.b.cl;
+  constexpr int NW = WS::Cl::kWords;
+  uint32_t any = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) any |= cl.need[w] & ~cl.placed[w];
+  if (!any) return;
   float4 *P = S.u.b.P;
   const int n = C.n;
   for (int r = 0; r < n; ++r) {
     const int k0 = r * kMaxLinks, wd = k0 >> 5, sh = k0 & 31;
-    const uint32_t lo = wd == 0 ? w0 : (wd == 1 ? w1 : w2);
-    const uint32_t hi = wd == 0 ? w1 : (wd == 1 ? w2 : 0u);
+    const uint32_t lo = cl.need[wd] & ~cl.placed[wd];
+    const uint32_t hi = wd + 1 < NW ? cl.need[wd + 1] & ~cl.placed[wd + 1] : 0u;
     const uint32_t mr = (uint32_t)((((unsigned long long)hi << 32) | lo) >> sh) & ((1u << kMaxLinks) - 1u);
     if (!mr) continue;
     const float *Xr = xf + (jj * n + r) * (kMaxLinks * 12);
@@ -1102,15 +1158,17 @@ __device__ void place_needed(const TileCtx &C, WarpSmem &S, const float *xf, int
   }
   __syncwarp();
   if (lane == 0) {
-    cl.placed[0] |= w0;
-    cl.placed[1] |= w1;
-    cl.placed[2] |= w2;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cl.placed[w] |= cl.need[w];
   }
   __syncwarp();
 }
 
-__device__ __forceinline__ void need_all(Cands &cl, int lane) {
-  if (lane == 0) cl.need[0] = cl.need[1] = cl.need[2] = 0xffffffffu;
+template <class CL>
+__device__ __forceinline__ void need_all(CL &cl, int lane) {
+  if (lane == 0)
+#pragma unroll
+    for (int w = 0; w < CL::kWords; ++w) cl.need[w] = 0xffffffffu;
   __syncwarp();
 }
 
@@ -1128,10 +1186,10 @@ __device__ __forceinline__ int list_find(const int32_t *pf, int n, int f) {
 // Exact tests of a frame x obstacle list (cl.pf holds its sphere prefix):
 // lane l takes a contiguous run of the flat (candidate, sphere) range, so a
 // candidate's data stays in registers over its spheres.
-template <int KIND>   // 0: obstacle spheres, 1: boxes, 2: cylinders
-__device__ bool resolve_obstacles(const TileCtx &C, const WarpSmem &S, const uint32_t *list, int n, int tot,
+template <int KIND, class WS>   // KIND 0: obstacle spheres, 1: boxes, 2: cylinders
+__device__ bool resolve_obstacles(const TileCtx &C, const WS &S, const uint32_t *list, int n, int tot,
                                   int lane, BroadAcc &acc) {
-  const Cands &cl = S.u.b.cl;
+  const auto &cl = S.u.b.cl;
   const float4 *P = S.u.b.P;
   const int per = (tot + kWarp - 1) / kWarp;
   int f = lane * per;
@@ -1175,21 +1233,22 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WarpSmem &S, const uin
 }
 
 // One state of the broadphase path: MV -> 1 on a collision, FFC -> the
-// bitmask of colliding robot pairs.  MV checks the obstacles, then the self
+// code of the first colliding robot pair (0: none).  MV checks the obstacles, then the self
 // pairs, then the other robots, with a warp vote after each (all three
 // belong to one state, so the verdict is the same in any order; the env and
 // self checks still come before the robot-robot ones, as in Alg. 1).
-__device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj, int lane, bool need_env,
+template <class WS>
+__device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int lane, bool need_env,
                                 bool do_pairs, BroadAcc &acc) {
-  Cands &cl = S.u.b.cl;
+  auto &cl = S.u.b.cl;
   const float4 *P = S.u.b.P;
   const int n = C.n;
   const int nke = C.self_robots * kMaxLinks;   // frames with obstacle checks
   const bool exhaustive = C.exhaustive != 0, ffc = C.ffc != 0;
   if (lane == 0) {
     cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = cl.ny = 0;
-    cl.need[0] = cl.need[1] = cl.need[2] = 0;
-    cl.placed[0] = cl.placed[1] = cl.placed[2] = 0;
+#pragma unroll
+    for (int w = 0; w < WS::Cl::kWords; ++w) cl.need[w] = cl.placed[w] = 0u;
   }
   __syncwarp();
   bool hit = false;
@@ -1528,11 +1587,11 @@ __device__ unsigned broad_state(TileCtx &C, WarpSmem &S, const float *xf, int jj
 #pragma unroll 4
           for (int b = b0; b < b1; ++b) h |= sph_hit(pa, P[b]);
         }
-        if (h) pm |= ffc ? (1u << pair_index(k / kMaxLinks, k2 / kMaxLinks, n)) : 1u;
+        if (h) pm = ffc ? max(pm, pair_code(pair_index(k / kMaxLinks, k2 / kMaxLinks, n))) : 1u;
       }
     }
   }
-  if (ffc) return __reduce_or_sync(0xffffffffu, pm);
+  if (ffc) return __reduce_max_sync(0xffffffffu, pm);
   return __any_sync(0xffffffffu, hit || pm != 0) ? 1u : 0u;
 }
 
@@ -1559,7 +1618,8 @@ __device__ __forceinline__ void flush_acc(TileCtx &C, BroadAcc &acc, int lane) {
 }
 
 // clearance mode (exhaustive MV with min_clearance_out): direct formulas
-__device__ void clr_state(const TileCtx &C, const WarpSmem &S, const float4 *P, int lane, bool do_env, bool do_pairs,
+template <class WS>
+__device__ void clr_state(const TileCtx &C, const WS &S, const float4 *P, int lane, bool do_env, bool do_pairs,
                           float &minclr) {
   const int M = C.M;
   if (do_env && C.check_env) {
@@ -1587,11 +1647,11 @@ __device__ void clr_state(const TileCtx &C, const WarpSmem &S, const float4 *P, 
     }
 }
 
-template <bool CLR>
-__device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int lane, float &minclr, bool do_env,
+template <bool CLR, class WS>
+__device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, float &minclr, bool do_env,
                        bool do_pairs) {
   const int n = C.n, M = C.M;
-  const int CS = (kFkChains / n) < 1 ? 1 : (kFkChains / n);   // states per FK round
+  const int CS = (kFkChains / n) < 1 ? 1 : (kFkChains / n);   // states per FK round (n chains each)
   float *xf = S.u.b.xf;
   float4 *P = S.u.b.P;
   float *K = S.u.b.K;
@@ -1600,9 +1660,10 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
   BroadAcc acc = {0u, 0u, 0u, 0u};
   const int nv = slice_valid(C, k);   // positions 0..nv-1 of the visiting order
   for (int j0 = 0; j0 < nv; j0 += CS) {
-    // (state, robot) chains, three lanes per chain (one row of its frames each)
-    if (lane < 3 * CS * n) {
-      const int c = lane / 3, row = lane - 3 * c;
+    // (state, robot) chains, three lanes per chain (one row of its frames
+    // each), ten chains at a time
+    for (int c = lane / 3; lane < 30 && c < CS * n; c += 10) {
+      const int row = lane - 3 * (lane / 3);
       const int jj = j0 + c / n, r = c % n;
       if (jj < nv) {
         const int t = slice_state(C, k, slot_j(C, jj, nv));
@@ -1636,7 +1697,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
             }
             found = 1;
           } else {
-            const int key = t * 32 + (__ffs(res) - 1);
+            const int key = code_key(t, res);
             if (!C.exhaustive) {
               flush_acc(C, acc, lane);
               return key;
@@ -1706,9 +1767,9 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
       } else {
         unsigned pm = pairs_ffc(P, K, S.off, n, lane, eps);
         if (lane == 0) C.tests += (unsigned long long)C.pairtests;
-        pm = __reduce_or_sync(0xffffffffu, pm);
+        pm = __reduce_max_sync(0xffffffffu, pm);
         if (pm) {
-          const int key = t * 32 + (__ffs(pm) - 1);
+          const int key = code_key(t, pm);
           if (!C.exhaustive) return key;
           if (key < found) found = key;   // states run in increasing t
         }
@@ -1725,15 +1786,15 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WarpSmem &S, int k, int la
 // the persistent work-stealing kernel
 // ---------------------------------------------------------------------------
 
-template <bool CLR>
-__device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane) {
+template <bool CLR, class WS>
+__device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   const QueryDev Q = B.q[q];
   if (!(B.flags & MRV_EXHAUSTIVE)) {
     // a verdict reached since the item was claimed: skip the staging too
     int stop = 0;
     if (lane == 0)
       stop = !(Q.bits & 1u) ? *(volatile int *)&B.q_hit[q] != 0
-                            : *(volatile int *)&B.q_best[q] < c * Q.cte * Q.spt * 32;
+                            : *(volatile int *)&B.q_best[q] < (min(c * Q.cte * Q.spt, Q.T) << kKeyShift);
     if (__shfl_sync(0xffffffffu, stop, 0)) return;
   }
   TileCtx &C = S.ctx;   // kept in shared memory: read where used, not held in registers
@@ -1822,7 +1883,7 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
       int stop = 0;
       if (lane == 0)
         stop = !C.ffc ? *(volatile int *)&B.q_hit[q] != 0
-                      : *(volatile int *)&B.q_best[q] < slice_state(C, k, 0) * 32;
+                      : *(volatile int *)&B.q_best[q] < (min(slice_state(C, k, 0), C.T) << kKeyShift);
       if (__shfl_sync(0xffffffffu, stop, 0)) break;
     }
     const int res = (Q.bits & 2u) ? slice_a<CLR>(B, C, S, k, lane, minclr, do_env, do_pairs)
@@ -1855,13 +1916,15 @@ __device__ void run_chunk(const BatchDev &B, WarpSmem &S, int q, int c, int lane
 }
 
 // up to 12 warps per block; the register cap (168) lets 12 warps share an SM,
-// which is also what the shared memory of 3 blocks of 4 warps allows
-template <bool CLR>
+// which is also what the shared memory of 3 blocks of 4 warps of the team
+// layout allows.  The instance of layout WS takes the work items of its class.
+template <bool CLR, class WS>
 __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
   extern __shared__ float4 smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  WarpSmem &S = *reinterpret_cast<WarpSmem *>(reinterpret_cast<char *>(smem_raw) + warp * warp_smem_bytes());
+  WS &S = *reinterpret_cast<WS *>(reinterpret_cast<char *>(smem_raw) + warp * warp_smem_bytes<WS>());
+  constexpr int cls = WS::kClass;
   const long long t_start = clock64();
   if (q_single >= 0) {
     // one launch per query: warp w of block x takes items x*warps + w, ...
@@ -1871,7 +1934,9 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
       run_chunk<CLR>(B, S, q_single, c, lane);
     return;
   }
-  const int n_items = B.counters[1];
+  const int n_items = B.counters[cls ? 3 : 1];
+  const int *level_start = B.level_start + cls * (kMaxLevels + 1);
+  const int qbase = cls ? B.counters[5] : 0;   // first sorted position of the class
   const bool skip_dead = !(B.flags & MRV_EXHAUSTIVE);
   unsigned long long items = 0;
   // Items are claimed g at a time.  Lane l < g resolves item base + l (level,
@@ -1883,7 +1948,7 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
   int g = 1;
   for (;;) {
     int base = 0;
-    if (lane == 0) base = atomicAdd(&B.counters[0], g);
+    if (lane == 0) base = atomicAdd(&B.counters[cls ? 4 : 0], g);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_items) break;
     int halt = 0;
@@ -1900,11 +1965,11 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
       int lo = 0, hi = kMaxLevels - 1;   // level: last c with level_start[c] <= idx
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&B.level_start[mid]) <= idx) lo = mid;
+        if (__ldg(&level_start[mid]) <= idx) lo = mid;
         else hi = mid - 1;
       }
       lvl = lo;
-      q = __ldg(&B.sorted[idx - __ldg(&B.level_start[lo])]);
+      q = __ldg(&B.sorted[qbase + idx - __ldg(&level_start[lo])]);
       live = !skip_dead ||
              (*(volatile int *)&B.q_hit[q] == 0 && *(volatile int *)&B.q_best[q] == 0x7fffffff);
     }
@@ -1935,8 +2000,8 @@ __global__ void k_finish(BatchDev B, uint8_t *valid_out, float *minclr_out, mrv_
     mrv_conflict c = {-1, -1, -1};
     const int key = B.q_best[q];
     if (key != 0x7fffffff && !(Q.bits & 4u)) {
-      c.t = key >> 5;
-      int p = key & 31, i = 0;
+      c.t = key >> kKeyShift;
+      int p = key & ((1 << kKeyShift) - 1), i = 0;
       while (p >= Q.n - 1 - i) { p -= Q.n - 1 - i; ++i; }
       c.i = i;
       c.j = i + 1 + p;
@@ -2028,7 +2093,11 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
 // host-side launch wrappers
 // ---------------------------------------------------------------------------
 
-size_t main_smem_bytes(int warps) { return warp_smem_bytes() * (size_t)warps; }
+size_t main_smem_bytes(int warps, int cls) {
+  return (cls ? warp_smem_bytes<WarpSmemLarge>() : warp_smem_bytes<WarpSmemTeam>()) * (size_t)warps;
+}
+
+int large_warps() { return kLargeWarps; }
 
 cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st) {
   if (B.n_queries > 0) {
@@ -2044,8 +2113,9 @@ cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st) {
 }
 
 // The dynamic shared memory limit of k_main is a process-wide attribute (per
-// device): it is raised once to what the largest block (12 warps) needs, so
-// launches with fewer warps on other threads never see it shrink under them.
+// device): it is raised once to what the largest block (12 warps of the team
+// layout, kLargeWarps of the large-team layout) needs, so launches with fewer
+// warps on other threads never see it shrink under them.
 cudaError_t set_main_attrs(int warps) {
   (void)warps;
   constexpr int kMaxDevices = 64;
@@ -2057,24 +2127,35 @@ cudaError_t set_main_attrs(int warps) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return cudaSuccess;
-  const int bytes = (int)main_smem_bytes(12);
-  e = cudaFuncSetAttribute(k_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const int team = (int)main_smem_bytes(12, 0), large = (int)main_smem_bytes(kLargeWarps, 1);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  e = cudaFuncSetAttribute(k_main<false, WarpSmemTeam>, a, team);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true, WarpSmemTeam>, a, team);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<false, WarpSmemLarge>, a, large);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true, WarpSmemLarge>, a, large);
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
 
-cudaError_t max_blocks_per_sm(int warps, bool clr, int *out) {
+cudaError_t max_blocks_per_sm(int warps, bool clr, int cls, int *out) {
   set_main_attrs(warps);
-  if (clr)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true>, warps * 32, main_smem_bytes(warps));
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false>, warps * 32, main_smem_bytes(warps));
+  const size_t smem = main_smem_bytes(warps, cls);
+  if (cls)
+    return clr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WarpSmemLarge>, warps * 32, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WarpSmemLarge>, warps * 32, smem);
+  return clr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WarpSmemTeam>, warps * 32, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WarpSmemTeam>, warps * 32, smem);
 }
 
-cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int q_single, cudaStream_t st) {
-  const size_t smem = main_smem_bytes(warps);
-  if (clr) k_main<true><<<grid, warps * 32, smem, st>>>(B, q_single);
-  else k_main<false><<<grid, warps * 32, smem, st>>>(B, q_single);
+cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int cls, int q_single, cudaStream_t st) {
+  const size_t smem = main_smem_bytes(warps, cls);
+  if (cls) {
+    if (clr) k_main<true, WarpSmemLarge><<<grid, warps * 32, smem, st>>>(B, q_single);
+    else k_main<false, WarpSmemLarge><<<grid, warps * 32, smem, st>>>(B, q_single);
+  } else {
+    if (clr) k_main<true, WarpSmemTeam><<<grid, warps * 32, smem, st>>>(B, q_single);
+    else k_main<false, WarpSmemTeam><<<grid, warps * 32, smem, st>>>(B, q_single);
+  }
   return cudaGetLastError();
 }
 

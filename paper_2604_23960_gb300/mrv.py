@@ -35,8 +35,9 @@ MRV_LINEAR = 0x80
 MRV_PRIORITY = 0x100
 MRV_KIND_MV = 0
 MRV_KIND_FFC = 1
-MRV_MAX_ROBOTS = 8
-MRV_MAX_QUERY_SPHERES = 512
+MRV_MAX_ROBOTS = 16
+MRV_MAX_QUERY_SPHERES = 1024
+MRV_MAX_STEPS = (1 << 24) - 1
 MRV_NOALLOC_MAX_QUERIES = 4096
 MRV_NOALLOC_MAX_WAYPOINTS = 65536
 ERR_NAMES = {-1: "MRV_ERR_ARG", -2: "MRV_ERR_OOM", -3: "MRV_ERR_NOT_FOUND", -4: "MRV_ERR_CUDA",

@@ -256,6 +256,16 @@ def cage8_bases() -> List[np.ndarray]:
     return floor + ceil
 
 
+def cage16_bases() -> List[np.ndarray]:
+    """16-arm Cage team (the paper's largest Cage, floor and ceiling mounted):
+    the 8-arm team, then floor arms under its four ceiling arms and ceiling
+    arms above its four floor arms, so each of the eight positions carries a
+    floor and a ceiling arm, all yawed to face the center."""
+    floor = [_pose(x, y, 0.0, math.atan2(-y, -x)) for x, y in CAGE8_CEILING]
+    ceil = [_pose_ceiling(x, y, CEILING_Z, math.atan2(-y, -x)) for x, y in CAGE_BASES]
+    return cage8_bases() + floor + ceil
+
+
 def load_cage8_fixtures(path: Optional[Path] = None) -> dict:
     path = FIXTURES.parent / "cage8_fixtures.npz" if path is None else path
     if not path.exists():
@@ -268,6 +278,20 @@ def load_cage8_fixtures(path: Optional[Path] = None) -> dict:
 def cage8_arms(fixtures: Optional[dict] = None) -> List[RobotModel]:
     fx = load_cage_fixtures() if fixtures is None else fixtures
     return [panda_like(b, fx["self_pairs"], name=f"cage8_arm{k}") for k, b in enumerate(cage8_bases())]
+
+
+def load_cage16_fixtures(path: Optional[Path] = None) -> dict:
+    path = FIXTURES.parent / "cage16_fixtures.npz" if path is None else path
+    if not path.exists():
+        raise FileNotFoundError(
+            f"{path} missing: run `python oracle/make_cage_fixtures.py --cage16` to draw it")
+    with np.load(path) as z:
+        return {k: z[k] for k in z.files}
+
+
+def cage16_arms(fixtures: Optional[dict] = None) -> List[RobotModel]:
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    return [panda_like(b, fx["self_pairs"], name=f"cage16_arm{k}") for k, b in enumerate(cage16_bases())]
 
 
 # ---------------------------------------------------------------------------
@@ -534,6 +558,49 @@ def make_cage8_mv(n_queries: int = 10000, query_seed: int = 208, fixtures: Optio
                     KIND_MV, 0)
     return Workload("cage8_mv", models, [env], b, env=0, check_env=True,
                     meta={"robots": 8, "resolution": 1.0 / 32.0})
+
+
+def make_cage16_mv(n_queries: int = 10000, query_seed: int = 209, fixtures: Optional[dict] = None,
+                   fixtures16: Optional[dict] = None, edge: Optional[float] = 0.5) -> Workload:
+    """MV for the floor- and ceiling-mounted 16-arm team in the cylinder cage
+    (Sec. V-A, Fig. 3b), on planner-like edges: each motion starts at a
+    whole-team configuration that is valid (every arm env+self valid and clear
+    of the others) and heads for another one, cut to at most `edge` rad of
+    C-space distance for the arm that moves furthest (a tree planner's
+    extension range; None: the whole way); resolution 1/32 rad.  1024 spheres
+    per query: the large-team kernel.  At 0.5 rad about 15% of the edges are
+    valid and T is about 16; whole motions between two team configurations
+    are almost never valid."""
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    f16 = load_cage16_fixtures() if fixtures16 is None else fixtures16
+    models = cage16_arms(fx)
+    env = cage_env_cyl()
+    rng = np.random.default_rng(query_seed)
+    team = f16["team_states"]                        # (K, 16, 7)
+    K = team.shape[0]
+    a = rng.integers(0, K, n_queries)
+    b = (a + rng.integers(1, K, n_queries)) % K      # a different configuration
+    start = team[a].astype(np.float64)
+    d = team[b].astype(np.float64) - start
+    if edge is not None:
+        reach = np.linalg.norm(d, axis=2).max(axis=1)
+        d *= np.minimum(1.0, edge / np.maximum(reach, 1e-12))[:, None, None]
+    cfg = np.stack([team[a], (start + d).astype(np.float32)], axis=2)   # (Q, 16, 2, 7)
+    bt = _fast_batch(n_queries, 16, np.tile(np.arange(16), n_queries), cfg.reshape(-1, 7), None, 1.0 / 32.0,
+                     KIND_MV, 0)
+    return Workload("cage16_mv", models, [env], bt, env=0, check_env=True,
+                    meta={"robots": 16, "resolution": 1.0 / 32.0, "edge": edge})
+
+
+def make_cage16_ffc(n_queries: int = 10000, query_seed: int = 210, fixtures: Optional[dict] = None,
+                    fixtures16: Optional[dict] = None) -> Workload:
+    """FFC on the 16-arm team's whole motions between two valid team
+    configurations (120 robot pairs per state), obstacles ignored (Alg. 2)."""
+    w = make_cage16_mv(n_queries, query_seed, fixtures, fixtures16, edge=None)
+    w.batch.q_kind = np.full(n_queries, KIND_FFC, np.uint8)
+    w.name = "cage16_ffc"
+    w.check_env = False
+    return w
 
 
 TEAM_ARM_BASES = [(4.4, 5.0, 0.0), (5.6, 5.0, math.pi)]

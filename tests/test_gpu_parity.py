@@ -9,6 +9,8 @@ clearance values must agree within 1e-5 m.
 """
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -252,10 +254,21 @@ def test_errors_are_reported(ctx):
             ctx.ffc_find(bt2)
     # too many robots in a query
     d = W.disc_robot(0.1)
-    nine = _one_query([d] * 9, [np.array([[i, 0.0], [i, 1.0]]) for i in range(9)])
+    n = mrv.MRV_MAX_ROBOTS + 1
+    over = _one_query([d] * n, [np.array([[i, 0.0], [i, 1.0]]) for i in range(n)])
     with pytest.raises(mrv.MrvError) as e:
-        ctx.mv_validate(ctx.bind(nine))
+        ctx.mv_validate(ctx.bind(over))
     assert e.value.code == -7
+    # too many spheres in a query (five 256-sphere robots), host and device batch
+    d1 = W.disc_robot(0.05)
+    big = dataclasses.replace(d1, sphere_xyzr=np.tile(d1.sphere_xyzr, (256, 1)),
+                              sphere_link=np.tile(d1.sphere_link, 256), name="big")
+    five = _one_query([big] * 5, [np.array([[i, 0.0], [i, 1.0]]) for i in range(5)])
+    for dev in (False, True):
+        b5 = ctx.bind(five)
+        with pytest.raises(mrv.MrvError) as e:
+            ctx.mv_validate(b5.to("cuda") if dev else b5)
+        assert e.value.code == -7
     # the context stays usable
     PA.check_mv(O.Oracle(w), ctx.mv_validate(ba))
 
@@ -342,12 +355,13 @@ def test_full_ragged_1m(ctx):
 
 
 def test_longest_motions(ctx):
-    """T = MRV_MAX_STEPS (2^24 states): disc 0 drifts slowly far from a
+    """T = MRV_MAX_STEPS (2^24 states, t = 0..2^24 - 1): disc 0 drifts slowly far from a
     stationary disc 1, then jumps onto it in a one-step segment, so the only
     conflict is the last state (decidable); a second query jumps to a clear
     spot instead (valid, compared on its exhaustive minimum clearance); one
     step more than the limit is rejected."""
-    T = 1 << 24
+    T = mrv.MRV_MAX_STEPS
+    assert T == (1 << 24) - 1
     disc = W.disc_robot(0.25)
     bb = W.BatchBuilder(2, True)
     for end in ((5.0, 5.0), (3.0, 3.0)):

@@ -404,6 +404,27 @@ def test_bruteforce_many_robots(seed):
         assert BF.ffc_alg2(g, 4) == tuple(ffc[q])
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_bruteforce_large_teams(seed):
+    """Teams of 9-16 robots (up to 120 pairs, pair indices past 31): the
+    oracle's FFC against every conflict enumerated and against Alg. 2 with
+    lane batches of 4, and its MV against Alg. 1 restated."""
+    w = tiny_workload(520 + seed, n_queries=4, timed=True, min_robots=9, max_robots=16, max_steps=2,
+                      n_models=3)
+    o = O.Oracle(w)
+    ffc = o.ffc()
+    mv = o.mv()
+    seen_high = False
+    for q in range(w.batch.n_queries):
+        g = BF.Geometry(w, q)
+        conf = BF.all_conflicts(g)
+        assert tuple(ffc[q]) == (min(conf) if conf else (-1, -1, -1))
+        assert BF.ffc_alg2(g, 4) == tuple(ffc[q])
+        assert bool(mv[q]) == BF.mv_alg1(g, 4, hierarchical=False, check_env=True)
+        seen_high |= any(j >= 8 for _, _, j in conf)
+    assert seen_high
+
+
 # ------------------------------------------- prioritized planner's MV variant
 
 def _discs_timed(paths, T, r=0.25, env=None):

@@ -72,13 +72,13 @@ def random_config(rng, m: W.RobotModel):
 
 def tiny_workload(seed: int, n_queries: int = 12, timed: bool = True, max_robots: int = 3,
                   n_models: int = 5, max_steps: int = 6, resolution: float = 0.4, env: bool = True,
-                  cylinders: int = 0):
+                  cylinders: int = 0, min_robots: int = 1):
     rng = np.random.default_rng(seed)
     models = [random_robot(rng) for _ in range(n_models)]
     envs = [random_env(rng, n_c=cylinders)] if env else []
     bb = W.BatchBuilder(3, timed)
     for _ in range(n_queries):
-        n = int(rng.integers(1, max_robots + 1))
+        n = int(rng.integers(min_robots, max_robots + 1))
         robots = [int(rng.integers(0, n_models)) for _ in range(n)]
         paths, steps = [], []
         for r in robots:
