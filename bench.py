@@ -322,7 +322,8 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
                              "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
                              "valid_total": f"{nvalid}/{w.batch.n_queries}",
                              "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                             "kernel_ms": st["device_ms"], "tuning": tune}
+                             "kernel_ms": st["device_ms"], "tuning": tune,
+                             "order_study": order_study(ctx, ba, flush, linear=False)}
     w = W.make_cage16_ffc(10000)
     ba = ctx.bind(w).to("cuda")
     dt = timed(lambda: ctx.ffc_find(ba))
@@ -368,18 +369,22 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
     return out
 
 
-def order_study(ctx, ba, flush, reps=3):
-    """Effort of the four state-visiting orders of MV (combined or
-    hierarchical env/self-then-pairs order x rake or linear state map) on the
-    benchmark batch, early exit: fraction of states checked, fraction of the
-    method's sphere tests executed (dense kernel, the effort of Fig. 4) and
-    kernel time with and without the frame-level broadphase.  All four give
-    the same verdicts."""
+def order_study(ctx, ba, flush, reps=3, linear=True):
+    """Effort of the state-visiting orders of MV (combined, hierarchical
+    env/self-then-pairs, or pairs first: the adjacent fixed-base pairs, then
+    the rest; x rake or linear state map) on a batch, early exit: fraction of
+    states checked, fraction of the method's sphere tests executed (dense
+    kernel, the effort of Fig. 4) and kernel time with and without the
+    frame-level broadphase.  All give the same verdicts."""
     from paper_2604_23960_gb300 import mrv
     out = {}
-    for name, fl in (("combined_rake", 0), ("hierarchical_rake", mrv.MRV_HIERARCHICAL),
-                     ("combined_linear", mrv.MRV_LINEAR),
-                     ("hierarchical_linear", mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR)):
+    orders = [("combined_rake", 0), ("hierarchical_rake", mrv.MRV_HIERARCHICAL),
+              ("pairs_first_rake", mrv.MRV_PAIRS_FIRST)]
+    if linear:
+        orders += [("combined_linear", mrv.MRV_LINEAR),
+                   ("hierarchical_linear", mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR),
+                   ("pairs_first_linear", mrv.MRV_PAIRS_FIRST | mrv.MRV_LINEAR)]
+    for name, fl in orders:
         row = {}
         for tag, extra in (("", 0), ("_dense", mrv.MRV_NO_BROADPHASE)):
             ctx.mv_validate(ba, flags=fl | extra)

@@ -86,6 +86,19 @@ extern "C" {
                                      uses, Sec. IV-B) instead of the rake
                                      order t = b + nb l of Alg. 1 / Fig. 2;
                                      same verdicts, different effort        */
+#define MRV_PAIRS_FIRST 0x200u    /* MV checks the robot pairs likely to
+                                     collide first, the mixed strategy of
+                                     Sec. III-A: adjacent fixed-base robots
+                                     (kinematic chains whose bases are within
+                                     1.25x of either one's nearest other
+                                     fixed base).  Each slice runs twice:
+                                     those pairs, then the obstacle and self
+                                     checks and the other pairs.  Same
+                                     verdicts, different effort.  Queries
+                                     without such a pair run the combined
+                                     order; FFC queries and MRV_EXHAUSTIVE
+                                     runs ignore it; not with
+                                     MRV_HIERARCHICAL or MRV_PRIORITY.      */
 
 /* ---- query kinds (mrv_run) ---------------------------------------------- */
 #define MRV_KIND_MV 0

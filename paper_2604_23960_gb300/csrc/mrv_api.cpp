@@ -145,8 +145,10 @@ int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
     return fail(MRV_ERR_ARG, "missing batch array");
   if (b->flags & ~(uint32_t)(MRV_CHECK_ENV | MRV_HIERARCHICAL | MRV_EXHAUSTIVE | MRV_PTRS_ON_DEVICE | MRV_ASYNC |
                              MRV_PER_QUERY_LAUNCH | MRV_NO_BROADPHASE | MRV_LINEAR |
-                             MRV_PRIORITY))
+                             MRV_PRIORITY | MRV_PAIRS_FIRST))
     return fail(MRV_ERR_ARG, "unknown flag bits 0x%x", b->flags);
+  if ((b->flags & MRV_PAIRS_FIRST) && (b->flags & (MRV_HIERARCHICAL | MRV_PRIORITY)))
+    return fail(MRV_ERR_ARG, "MRV_PAIRS_FIRST excludes MRV_HIERARCHICAL and MRV_PRIORITY");
   if ((b->flags & MRV_ASYNC) && !(b->flags & MRV_PTRS_ON_DEVICE))
     return fail(MRV_ERR_ARG, "MRV_ASYNC requires MRV_PTRS_ON_DEVICE");
   if (!b->seg_steps && !(std::isfinite(b->resolution) && b->resolution > 0.f))
@@ -251,6 +253,25 @@ int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st) {
   return MRV_OK;
 }
 
+cudaError_t Scratch::reset(cudaStream_t st) const {
+  const char *a = reinterpret_cast<const char *>(hist);
+  const char *b = reinterpret_cast<const char *>(counts + 4);
+  const bool contiguous = a < reinterpret_cast<const char *>(level_start) &&
+                          reinterpret_cast<const char *>(level_start) < reinterpret_cast<const char *>(cursor) &&
+                          reinterpret_cast<const char *>(cursor) < reinterpret_cast<const char *>(counters) &&
+                          reinterpret_cast<const char *>(counters) < reinterpret_cast<const char *>(err) &&
+                          reinterpret_cast<const char *>(err) < reinterpret_cast<const char *>(stats) &&
+                          reinterpret_cast<const char *>(stats) < reinterpret_cast<const char *>(counts) &&
+                          b - a < (1 << 16);
+  if (contiguous) return cudaMemsetAsync(hist, 0, (size_t)(b - a), st);
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * kLevelBins, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t) * 2, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kNumStats, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 4, st);
+  return e;
+}
+
 int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
   int occ = 0;
   if (max_blocks_per_sm(warps, clr, cls, &occ) != cudaSuccess || occ < 1) {
@@ -271,11 +292,7 @@ int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *
 int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
                    mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
   cudaGetLastError();   // the launch checks below report this sequence's errors only
-  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * 4, st);
+  cudaError_t e = S.reset(st);
   if (e != cudaSuccess) return cuda_fail(e, "scratch reset");
   if ((e = launch_prepare(B, st)) != cudaSuccess) return cuda_fail(e, "prepare launch");
   const int warps = ctx->tuning.warps_per_block;
@@ -384,11 +401,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
     if ((rc = enqueue_run(ctx, B, S, clr, v_dst, m_dst, c_dst, true))) return rc;
   } else {
     // baseline: one synchronous launch per query (grid = the query's chunks)
-    cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.counters, 0, sizeof(int32_t) * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * 4, st);
+    cudaError_t e = S.reset(st);
     if (e == cudaSuccess) e = launch_prepare(B, st);
     if (e != cudaSuccess) return cuda_fail(e, "prepare");
     std::vector<QueryDev> hq(b->n_queries);
@@ -873,9 +886,7 @@ int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, 
   const bool dev = b->flags & MRV_PTRS_ON_DEVICE;
   BatchDev B = make_batchdev(c, b, S, MRV_KIND_MV, 1);
   cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
+  cudaError_t e = S.reset(st);
   if (e == cudaSuccess) e = launch_prepare(B, st);
   if (e != cudaSuccess) return cuda_fail(e, "prepare");
   // the query's sphere count bounds the output; read it back

@@ -108,14 +108,17 @@ struct QueryDev {
   int32_t split;      // slices per tile
   int32_t spt;        // states per slice (32 / split)
   int32_t nslices;    // slices per phase (ntiles * split)
-  int32_t nphase;     // 2 for hierarchical MV (env pass, then pair pass), else 1
+  int32_t nphase;     // 2 for hierarchical MV (env pass, then pair pass) and for
+                      // pairs-first MV (adjacent pairs, then the rest), else 1
   int32_t nchunks;    // work items of this query
   int32_t cte;        // slices per work item
   int32_t env;        // env slot or -1
   uint32_t bits;      // bit 0: FFC, bit 1: flavor A (lane = state), bit 2: invalid,
                       // bit 3: work class 1 (more than kTeamRobots robots or kTeamSpheres spheres)
   float rho2;         // largest squared sphere radius of the query's robots
-  int32_t pad;
+  int32_t nadj;       // pairs-first MV: adjacent robot pairs (0: the order is off)
+  uint32_t adj[4];    // pairs-first MV: bit p = pair p (in (i, j) order) is adjacent
+  long long adjtests;   // pairs-first MV: sphere tests per state of the adjacent pairs
   long long pairtests;  // robot-robot sphere tests per state
   long long envtests;   // robot-obstacle sphere + self tests per state (MV with env)
   long long boxtests;   // robot-box tests per state (MV with env)

@@ -44,6 +44,9 @@ struct Scratch {
   size_t layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char *p);
   int ensure(int64_t nq, int64_t ns, int64_t nw, int64_t stride, cudaStream_t st);
   void release();
+  // zeroes the per-call state (level bins, counters, error word, statistics,
+  // result counts), which every carving lays out back to back: one memset
+  cudaError_t reset(cudaStream_t st) const;
 };
 
 struct HostModel {

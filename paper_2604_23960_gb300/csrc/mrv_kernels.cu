@@ -82,6 +82,9 @@ struct TileCtx {
   int self_robots;           // robots with self checks: [0, self_robots)
   int pair_robots;           // robots i whose pairs (i, j > i) are checked
   int self_blk;              // every robot's self pairs come as blocks
+  int pr0, pr1;              // robot-pair table entries checked in the current phase
+  int first_phase;           // the current phase is the first visit of its states
+  long long rangetests;      // sphere tests per state of the entries pr0..pr1-1
   int split, spt, nslices;
   int env_ns, env_nb;
   const float4 *env_s;
@@ -213,13 +216,49 @@ __device__ long long steps_from_resolution(const float *s, const float *g, int d
   return (long long)ceil(__ddiv_rn(dist, (double)res));
 }
 
+// Robot pairs likely to collide, for the pairs-first MV order (the mixed
+// strategy Sec. III-A suggests: adjacent fixed-base manipulators first).
+// Two fixed-base robots (kinematic chains) are adjacent when the distance of
+// their bases is within 1.25x of either one's distance to its nearest other
+// fixed base.  Sets Q.adj (bit p: pair p in (i, j) order), Q.nadj and
+// Q.adjtests (sphere tests per state of the adjacent pairs).
+__device__ void adjacent_pairs(const BatchDev &B, int s0, int n, QueryDev &Q) {
+  float nn2[MRV_MAX_ROBOTS];
+  for (int i = 0; i < n; ++i) {
+    nn2[i] = INFINITY;
+    const ModelDev &a = B.models[B.slot_robot_id[s0 + i]];
+    if (a.kind == MRV_ROBOT_POINT) continue;
+    for (int j = 0; j < n; ++j) {
+      const ModelDev &b = B.models[B.slot_robot_id[s0 + j]];
+      if (j == i || b.kind == MRV_ROBOT_POINT) continue;
+      const float dx = a.base[3] - b.base[3], dy = a.base[7] - b.base[7], dz = a.base[11] - b.base[11];
+      nn2[i] = fminf(nn2[i], dx * dx + dy * dy + dz * dz);
+    }
+  }
+  int p = 0;
+  for (int i = 0; i < n; ++i) {
+    const ModelDev &a = B.models[B.slot_robot_id[s0 + i]];
+    for (int j = i + 1; j < n; ++j, ++p) {
+      const ModelDev &b = B.models[B.slot_robot_id[s0 + j]];
+      if (a.kind == MRV_ROBOT_POINT || b.kind == MRV_ROBOT_POINT) continue;
+      const float dx = a.base[3] - b.base[3], dy = a.base[7] - b.base[7], dz = a.base[11] - b.base[11];
+      if (dx * dx + dy * dy + dz * dz <= 1.5625f * fmaxf(nn2[i], nn2[j])) {
+        Q.adj[p >> 5] |= 1u << (p & 31);
+        Q.nadj += 1;
+        Q.adjtests += (long long)a.n_spheres * b.n_spheres;
+      }
+    }
+  }
+}
+
 __global__ void k_prep(BatchDev B) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= B.n_queries) return;
   uint32_t err = 0;
   QueryDev Q;
   Q.T = 0; Q.n = 0; Q.M = 0; Q.ntiles = 0; Q.split = 1; Q.spt = kWarp; Q.nslices = 0; Q.nphase = 1;
-  Q.nchunks = 0; Q.cte = 1; Q.env = -1; Q.bits = 0; Q.rho2 = 0.f; Q.pad = 0;
+  Q.nchunks = 0; Q.cte = 1; Q.env = -1; Q.bits = 0; Q.rho2 = 0.f; Q.nadj = 0;
+  Q.adj[0] = Q.adj[1] = Q.adj[2] = Q.adj[3] = 0u; Q.adjtests = 0;
   Q.pairtests = 0; Q.envtests = 0; Q.boxtests = 0; Q.cyltests = 0;
   const int s0 = B.q_robot_off[q], s1 = B.q_robot_off[q + 1];
   const int n = s1 - s0;
@@ -301,6 +340,10 @@ __global__ void k_prep(BatchDev B) {
     Q.spt = kWarp / split;
     Q.nslices = Q.ntiles * split;
     Q.nphase = (check_env && (B.flags & MRV_HIERARCHICAL)) ? 2 : 1;
+    if (mv && (B.flags & MRV_PAIRS_FIRST) && !(B.flags & MRV_EXHAUSTIVE)) {
+      adjacent_pairs(B, s0, n, Q);
+      if (Q.nadj > 0) Q.nphase = 2;
+    }
     const int total = Q.nslices * Q.nphase;
     int cte = B.slices_per_item < 1 ? 1 : B.slices_per_item;
     const int need = (total + kMaxLevels - 1) / kMaxLevels;
@@ -339,27 +382,46 @@ __global__ void k_prep(BatchDev B) {
 
 // level layout, per work class: the class's queries sorted by item count
 // (descending), class 0 first; level c holds the class's queries with more
-// than c items, which are its first cnt_c sorted queries.
-__global__ void k_levels(BatchDev B) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int start = 0;
-  for (int cls = 0; cls < 2; ++cls) {
-    const int *hist = B.hist + cls * (kMaxLevels + 1);
-    int *cursor = B.cursor + cls * (kMaxLevels + 1);
-    int *level_start = B.level_start + cls * (kMaxLevels + 1);
-    const int qbase = start;         // first sorted position of the class
-    for (int k = kMaxLevels; k >= 0; --k) {
-      cursor[k] = start;             // first sorted position of item count k
-      start += hist[k];
-    }
-    int acc = 0;
-    level_start[0] = 0;
-    for (int c = 0; c < kMaxLevels; ++c) {
-      acc += cursor[c] - qbase;      // the class's queries with more than c items
-      level_start[c + 1] = acc;
-    }
-    B.counters[cls ? 3 : 1] = acc;   // the class's work items
-    if (cls == 0) B.counters[5] = start;
+// than c items, which are its first cnt_c sorted queries.  With h the class's
+// histogram of item counts (bin kMaxLevels: that many or more) and
+// S[k] = sum_{k' >= k} h[k'], the first sorted position of item count k is
+// qbase + S[k + 1] and level c starts at item sum_{m <= c} S[m + 1].  One
+// block of kLevelThreads threads, thread (class, k) owning bin k; both sums
+// are segmented scans in shared memory.
+constexpr int kLevelThreads = 1024;
+static_assert(kLevelBins <= kLevelThreads, "one thread per level bin");
+
+__device__ __forceinline__ void seg_scan(int *v, int t, int seg) {
+  // inclusive prefix sums of v within segments of `seg` entries
+  for (int d = 1; d < seg; d <<= 1) {
+    const int add = (t < kLevelBins && t % seg >= d) ? v[t - d] : 0;
+    __syncthreads();
+    if (t < kLevelBins) v[t] += add;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kLevelThreads) k_levels(BatchDev B) {
+  __shared__ int suf[kLevelBins], pre[kLevelBins];
+  const int t = threadIdx.x, L = kMaxLevels + 1;
+  const int cls = t / L, k = t - cls * L;
+  // suffix sums: scan the bins in reverse order within each class
+  if (t < kLevelBins) suf[cls * L + (kMaxLevels - k)] = B.hist[t];
+  __syncthreads();
+  seg_scan(suf, t, L);
+  // S[k] of class c sits at suf[c L + kMaxLevels - k]; S[kMaxLevels + 1] = 0
+  const int S1 = (t < kLevelBins && k < kMaxLevels) ? suf[cls * L + kMaxLevels - k - 1] : 0;   // S[k + 1]
+  if (t < kLevelBins) pre[t] = S1;
+  __syncthreads();
+  seg_scan(pre, t, L);
+  const int n0 = suf[kMaxLevels];   // S[0] of class 0: its queries
+  if (t < kLevelBins) {
+    const int qbase = cls ? n0 : 0;
+    B.cursor[t] = qbase + S1;
+    if (k < kMaxLevels) B.level_start[cls * L + k + 1] = pre[t];
+    if (k == 0) B.level_start[cls * L] = 0;
+    if (k == kMaxLevels - 1) B.counters[cls ? 3 : 1] = pre[t];   // the class's work items
+    if (t == 0) B.counters[5] = n0;
   }
 }
 
@@ -657,7 +719,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
   const int nvalid = __popc(__ballot_sync(0xffffffffu, valid));
   __syncwarp();
   if (lane == 0) {
-    if (do_env) C.states += nvalid;   // hierarchical order: a state counts in its first phase
+    if (C.first_phase) C.states += nvalid;   // two-phase orders: a state counts in its first phase
     C.chains += (unsigned long long)nvalid * C.n;
     C.placed += (unsigned long long)nvalid * C.M;
   }
@@ -834,6 +896,19 @@ __device__ bool pairs_mv(const float4 *P, const float *K, const int *off, int n,
   bool hit = false;
   for (int i = 0; i + 1 < n && i < row_robots; ++i)
     hit |= rect_test(P, off[i], off[i + 1], P, K, off[i + 1], M, 0.f, 0.f, 0.f, eps, lane);
+  return hit;
+}
+
+// MV robot-robot checks at one state for the entries pr0..pr1-1 of the
+// query's pair table
+template <class WS>
+__device__ bool pairs_list_mv(const float4 *P, const float *K, const WS &S, int pr0, int pr1, int lane, float eps) {
+  bool hit = false;
+  for (int p = pr0; p < pr1; ++p) {
+    const uint32_t e = S.rp[p];
+    const int i = (int)(e & 15u), j = (int)((e >> 4) & 15u);
+    hit |= rect_test(P, S.off[i], S.off[i + 1], P, K, S.off[j], S.off[j + 1], 0.f, 0.f, 0.f, eps, lane);
+  }
   return hit;
 }
 
@@ -1529,11 +1604,12 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
     cl.overflow = 0;
   }
   __syncwarp();
-  const int npair = n * (n - 1) / 2;
-  const int ftot = S.rpf[C.prio ? n - 1 : npair];   // the table lists the pairs (0, j) first
+  // the phase's entries of the pair table (prioritized MV: the pairs (0, j),
+  // listed first; pairs first: the adjacent pairs, listed first, or the rest)
+  const int ftot = S.rpf[C.pr1];
   {
-    int it = 0;
-    for (int f = lane; f < ftot; f += kWarp) {
+    int it = C.pr0;
+    for (int f = S.rpf[C.pr0] + lane; f < ftot; f += kWarp) {
       while (S.rpf[it + 1] <= f) ++it;
       const uint32_t e = S.rp[it];
       const int i = (int)(e & 15u), j = (int)((e >> 4) & 15u), nj = (int)((e >> 8) & 15u);
@@ -1554,6 +1630,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   unsigned pm = 0;
   const int np = cl.np;
   if (cl.overflow) {
+    // every pair of the query's checked robots (a superset of the phase's
+    // entries in the pairs-first order: an MV collision found there is one)
     need_all(cl, lane);
     place_needed(C, S, xf, jj, lane, acc);
     unsigned long long t = 0;
@@ -1681,7 +1759,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
     __syncwarp();
     for (int j = j0; j < j0 + CS && j < nv; ++j) {
       const int t = slice_state(C, k, slot_j(C, j, nv));
-      if (lane == 0 && do_env) C.states += 1;   // hierarchical order: counted in the first phase
+      if (lane == 0 && C.first_phase) C.states += 1;   // two-phase orders: counted in the first phase
       if (!CLR && C.broad) {
         // frame-level broadphase; spheres are placed only for the frames whose
         // bounding spheres overlap something, then resolved exactly
@@ -1757,8 +1835,11 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
           C.ctests += (unsigned long long)C.cyltests;
         }
         if (do_pairs) {
-          if (!CLR) hit |= pairs_mv(P, K, S.off, n, M, lane, eps, C.pair_robots);
-          if (lane == 0) C.tests += (unsigned long long)C.pairtests;
+          if (!CLR) {
+            if (C.pr0 == 0 && C.rangetests == C.pairtests) hit |= pairs_mv(P, K, S.off, n, M, lane, eps, C.pair_robots);
+            else hit |= pairs_list_mv(P, K, S, C.pr0, C.pr1, lane, eps);
+          }
+          if (lane == 0) C.tests += (unsigned long long)C.rangetests;
         }
         if (__any_sync(0xffffffffu, hit)) {
           if (!C.exhaustive) return 1;
@@ -1848,15 +1929,20 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     int blk = 1;
     for (int r = 0; r < C.n; ++r) blk &= (S.rs[r].n_groups == 0 || S.rs[r].masks != nullptr);
     C.self_blk = blk;
+    // pairs in (i, j) order; pairs-first MV lists the adjacent pairs first
     int p = 0, f = 0;
-    for (int i = 0; i < C.n; ++i)
-      for (int j = i + 1; j < C.n; ++j) {
-        const int nj = S.rs[j].n_links;
-        S.rp[p] = (uint32_t)(i | j << 4 | nj << 8) | ((uint32_t)((4096 + nj - 1) / nj) << 16);
-        S.rpf[p] = (int16_t)f;
-        f += S.rs[i].n_links * S.rs[j].n_links;
-        ++p;
-      }
+    const bool pf = !C.ffc && Q.nadj > 0;
+    const uint32_t *adj = B.q[q].adj;   // read in place (a copy indexed at run time would live in local memory)
+    for (int pass = pf ? 0 : 1; pass < 2; ++pass)
+      for (int i = 0, pi = 0; i < C.n; ++i)
+        for (int j = i + 1; j < C.n; ++j, ++pi) {
+          if (pf && (((__ldg(&adj[pi >> 5]) >> (pi & 31)) & 1u) != (pass == 0 ? 1u : 0u))) continue;
+          const int nj = S.rs[j].n_links;
+          S.rp[p] = (uint32_t)(i | j << 4 | nj << 8) | ((uint32_t)((4096 + nj - 1) / nj) << 16);
+          S.rpf[p] = (int16_t)f;
+          f += S.rs[i].n_links * S.rs[j].n_links;
+          ++p;
+        }
     S.rpf[p] = (int16_t)f;
   }
   if (C.check_env && !(Q.bits & 2u)) {
@@ -1877,7 +1963,22 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   for (int kt = k0; kt < k1; ++kt) {
     const int phase = Q.nphase == 2 ? kt / Q.nslices : -1;
     const int k = Q.nphase == 2 ? kt - phase * Q.nslices : kt;
-    const bool do_env = phase != 1, do_pairs = phase != 0;
+    // combined: obstacles + self and every pair; hierarchical: obstacles +
+    // self, then the pairs; pairs first: the adjacent pairs, then obstacles +
+    // self and the other pairs
+    const bool pf = Q.nadj > 0;
+    const bool do_env = pf ? phase == 1 : phase != 1;
+    const int npr = C.prio ? C.n - 1 : C.n * (C.n - 1) / 2;
+    const int pr0 = (pf && phase == 1) ? Q.nadj : 0;
+    const int pr1 = pf ? (phase == 0 ? Q.nadj : npr) : (phase == 0 ? 0 : npr);
+    const bool do_pairs = pr1 > pr0;
+    if (lane == 0) {
+      C.pr0 = pr0;
+      C.pr1 = pr1;
+      C.first_phase = phase <= 0;
+      C.rangetests = !pf ? Q.pairtests : (phase == 0 ? Q.adjtests : Q.pairtests - Q.adjtests);
+    }
+    __syncwarp();
     if (!C.exhaustive) {
       // one lane reads the query's shared verdict so the warp decides together
       int stop = 0;
@@ -1935,6 +2036,7 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
     return;
   }
   const int n_items = B.counters[cls ? 3 : 1];
+  if (n_items == 0) return;
   const int *level_start = B.level_start + cls * (kMaxLevels + 1);
   const int qbase = cls ? B.counters[5] : 0;   // first sorted position of the class
   const bool skip_dead = !(B.flags & MRV_EXHAUSTIVE);
@@ -2104,7 +2206,7 @@ cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st) {
     const int th = 128, bl = (B.n_queries + th - 1) / th;
     k_prep<<<bl, th, 0, st>>>(B);
   }
-  k_levels<<<1, 32, 0, st>>>(B);
+  k_levels<<<1, kLevelThreads, 0, st>>>(B);
   if (B.n_queries > 0) {
     const int th = 256, bl = (B.n_queries + th - 1) / th;
     k_scatter<<<bl, th, 0, st>>>(B);

@@ -21,9 +21,7 @@ static int batch_class(mrv_ctx *c, const mrv_batch *b, std::string *key) {
   if (rc) return rc;
   BatchDev B = make_batchdev(c, b, S, -1, 1);
   cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemsetAsync(S.hist, 0, sizeof(int32_t) * kLevelBins, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.err, 0, sizeof(uint32_t) * 2, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(S.stats, 0, sizeof(unsigned long long) * kNumStats, st);
+  cudaError_t e = S.reset(st);
   if (e == cudaSuccess) e = launch_prepare(B, st);
   std::vector<QueryDev> hq(b->n_queries);
   uint32_t err = 0;

@@ -33,6 +33,7 @@ MRV_PER_QUERY_LAUNCH = 0x20
 MRV_NO_BROADPHASE = 0x40
 MRV_LINEAR = 0x80
 MRV_PRIORITY = 0x100
+MRV_PAIRS_FIRST = 0x200
 MRV_KIND_MV = 0
 MRV_KIND_FFC = 1
 MRV_MAX_ROBOTS = 16

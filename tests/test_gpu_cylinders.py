@@ -84,7 +84,8 @@ def test_cage8_small(ctx):
     ba = ctx.bind(w).to("cuda")
     v = _np(ctx.mv_validate(ba))
     PA.check_mv(o, v)
-    for fl in (mrv.MRV_NO_BROADPHASE, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR):
+    for fl in (mrv.MRV_NO_BROADPHASE, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_PAIRS_FIRST,
+               mrv.MRV_PAIRS_FIRST | mrv.MRV_NO_BROADPHASE):
         np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=fl)), v)
     v2, mc = ctx.mv_validate(ba, exhaustive=True, min_clearance=True)
     np.testing.assert_array_equal(_np(v2), v)

@@ -46,7 +46,8 @@ def test_random_large_teams(ctx, seed):
     PA.check_ffc(o, c)
     assert (c[:, 2] >= 8).any(), "pair indices beyond one 32-bit mask are exercised"
     for fl in (mrv.MRV_NO_BROADPHASE, mrv.MRV_PER_QUERY_LAUNCH, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR,
-               mrv.MRV_HIERARCHICAL | mrv.MRV_NO_BROADPHASE):
+               mrv.MRV_HIERARCHICAL | mrv.MRV_NO_BROADPHASE, mrv.MRV_PAIRS_FIRST,
+               mrv.MRV_PAIRS_FIRST | mrv.MRV_NO_BROADPHASE, mrv.MRV_PAIRS_FIRST | mrv.MRV_PER_QUERY_LAUNCH):
         np.testing.assert_array_equal(ctx.mv_validate(ba, flags=fl), v)
     for fl in (mrv.MRV_NO_BROADPHASE, mrv.MRV_PER_QUERY_LAUNCH):
         np.testing.assert_array_equal(ctx.ffc_find(ba, flags=fl), c)
@@ -129,8 +130,11 @@ def test_cage16_small(ctx):
     v = _np(ctx.mv_validate(ba))
     PA.check_mv(o, v)
     assert 0 < v.sum() < len(v)
-    for fl in (mrv.MRV_NO_BROADPHASE, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_PER_QUERY_LAUNCH):
+    for fl in (mrv.MRV_NO_BROADPHASE, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_PER_QUERY_LAUNCH,
+               mrv.MRV_PAIRS_FIRST, mrv.MRV_PAIRS_FIRST | mrv.MRV_NO_BROADPHASE):
         np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=fl)), v)
+        st = ctx.stats()
+        assert 0 < st["states_checked"] <= st["states_available"]
     v2, mc = ctx.mv_validate(ba, exhaustive=True, min_clearance=True)
     np.testing.assert_array_equal(_np(v2), v)
     np.testing.assert_allclose(_np(mc), o.mv_min_clearance(threads=PA.THREADS), atol=PA.CLR_TOL, rtol=0)

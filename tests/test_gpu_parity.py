@@ -56,9 +56,13 @@ def test_tiny_mv_ffc(ctx, seed, timed):
     bd = ba.to("cuda")
     np.testing.assert_array_equal(_np(ctx.mv_validate(bd)), ctx.mv_validate(ba))
     np.testing.assert_array_equal(_np(ctx.ffc_find(bd)), c)
-    # hierarchical order (Alg. 1) and the linear state map: same verdicts
-    for fl in (mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_LINEAR | mrv.MRV_HIERARCHICAL):
-        np.testing.assert_array_equal(ctx.mv_validate(ba, flags=fl), ctx.mv_validate(ba))
+    # hierarchical order (Alg. 1), the linear state map and the pairs-first
+    # order (adjacent fixed-base pairs first): same verdicts
+    for fl in (mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_LINEAR | mrv.MRV_HIERARCHICAL, mrv.MRV_PAIRS_FIRST,
+               mrv.MRV_PAIRS_FIRST | mrv.MRV_LINEAR, mrv.MRV_PAIRS_FIRST | mrv.MRV_NO_BROADPHASE):
+        for ce in (True, False):
+            np.testing.assert_array_equal(ctx.mv_validate(ba, check_env=ce, flags=fl),
+                                          ctx.mv_validate(ba, check_env=ce))
     np.testing.assert_array_equal(ctx.ffc_find(ba, flags=mrv.MRV_LINEAR), c)   # FFC is linear already
     # every sphere pair tested (no frame-level broadphase): same verdicts
     for ce in (True, False):
@@ -135,7 +139,8 @@ def test_cage_mv_small_exhaustive(ctx):
     np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=mrv.MRV_NO_BROADPHASE)), v)
     # the four visiting orders (combined / hierarchical x rake / linear): same
     # verdicts; early exit checks a subset of the states, exhaustive all
-    for fl in (0, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR):
+    for fl in (0, mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR,
+               mrv.MRV_PAIRS_FIRST, mrv.MRV_PAIRS_FIRST | mrv.MRV_LINEAR):
         for bp in (0, mrv.MRV_NO_BROADPHASE):
             np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=fl | bp)), v)
             st = ctx.stats()
@@ -269,6 +274,11 @@ def test_errors_are_reported(ctx):
         with pytest.raises(mrv.MrvError) as e:
             ctx.mv_validate(b5.to("cuda") if dev else b5)
         assert e.value.code == -7
+    # the pairs-first order excludes the hierarchical order and the prioritized MV
+    for fl in (mrv.MRV_PAIRS_FIRST | mrv.MRV_HIERARCHICAL, mrv.MRV_PAIRS_FIRST | mrv.MRV_PRIORITY):
+        with pytest.raises(mrv.MrvError) as e:
+            ctx.mv_validate(ba, flags=fl)
+        assert e.value.code == -1
     # the context stays usable
     PA.check_mv(O.Oracle(w), ctx.mv_validate(ba))
 
