@@ -378,6 +378,8 @@ def order_study(ctx, ba, flush, reps=3, linear=True):
     frame-level broadphase.  All give the same verdicts."""
     from paper_2604_23960_gb300 import mrv
     out = {}
+    saved = mrv.mrv_get_tuning(ctx.h)
+    mrv.mrv_set_tuning(ctx.h, **dict(saved, mv_order=0))   # flags 0: the combined order
     orders = [("combined_rake", 0), ("hierarchical_rake", mrv.MRV_HIERARCHICAL),
               ("pairs_first_rake", mrv.MRV_PAIRS_FIRST)]
     if linear:
@@ -400,6 +402,7 @@ def order_study(ctx, ba, flush, reps=3, linear=True):
             else:
                 row["effort_tests"] = st["sphere_tests"] / max(1, st["sphere_tests_available"])
         out[name] = row
+    mrv.mrv_set_tuning(ctx.h, **saved)
     return out
 
 

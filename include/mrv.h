@@ -299,6 +299,11 @@ typedef struct {
   int32_t tile_split;        /* 1, 2, 4, 8, 16 or 32 slices per 32-state tile for
                                 kinematic-chain queries (point-robot queries
                                 always use whole tiles)                      */
+  int32_t mv_order;          /* order of MV queries with obstacle checks in
+                                batches whose flags name none
+                                (MRV_HIERARCHICAL, MRV_PAIRS_FIRST): 0 the
+                                combined order, 1 the hierarchical order.
+                                Same verdicts; mrv_autotune times both.     */
 } mrv_tuning;
 int mrv_set_tuning(mrv_ctx *ctx, const mrv_tuning *t);
 int mrv_get_tuning(mrv_ctx *ctx, mrv_tuning *t);

@@ -214,6 +214,7 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
   B.forced_kind = forced_kind;
   B.slices_per_item = slices_per_item;
   B.tile_split = ctx->tuning.tile_split;
+  B.mv_order = ctx->tuning.mv_order;
   B.slot_tau = S.slot_tau;
   B.q = S.q;
   B.q_hit = S.q_hit;
@@ -286,11 +287,11 @@ int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
 int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
                 mrv_conflict *conf, bool timed) {
   return enqueue_run_on(ctx, B, S, clr, valid, minclr, conf, ctx->stream, timed ? ctx->ev0 : nullptr,
-                        timed ? ctx->ev1 : nullptr);
+                        timed ? ctx->ev1 : nullptr, &ctx->fork);
 }
 
 int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
-                   mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+                   mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, const Fork *fk) {
   cudaGetLastError();   // the launch checks below report this sequence's errors only
   cudaError_t e = S.reset(st);
   if (e != cudaSuccess) return cuda_fail(e, "scratch reset");
@@ -303,13 +304,20 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return cuda_fail(e, "capture status");
   const unsigned rec_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev0 && (e = cudaEventRecordWithFlags(ev0, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
+  // queries beyond the team layout: the large-team instance, beside the team
+  // one on the fork's stream (after it on this stream without a fork)
+  const bool side = B.maybe_large && fk && fk->aux;
+  if (side && (e = cudaEventRecord(fk->fork, st)) != cudaSuccess) return cuda_fail(e, "fork event");
   e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm, 0), warps, clr, 0, -1, st);
   if (e != cudaSuccess) return cuda_fail(e, "main launch");
-  // queries beyond the team layout: the large-team instance, after the first
   if (B.maybe_large) {
     const int lw = large_warps();
-    e = launch_main(B, grid_for(ctx, lw, clr, 0, 1), lw, clr, 1, -1, st);
+    cudaStream_t ls = side ? fk->aux : st;
+    if (side && (e = cudaStreamWaitEvent(ls, fk->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
+    e = launch_main(B, grid_for(ctx, lw, clr, 0, 1), lw, clr, 1, -1, ls);
     if (e != cudaSuccess) return cuda_fail(e, "large-team launch");
+    if (side && ((e = cudaEventRecord(fk->join, ls)) != cudaSuccess || (e = cudaStreamWaitEvent(st, fk->join, 0)) != cudaSuccess))
+      return cuda_fail(e, "join");
   }
   if (ev1 && (e = cudaEventRecordWithFlags(ev1, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
   if ((e = launch_finish(B, valid, minclr, conf, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish launch");
@@ -521,6 +529,7 @@ int mrv_create(mrv_ctx **out, int device, void *cuda_stream) {
   if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->device_name = prop.name;
   e = cudaEventCreate(&c->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e == cudaSuccess) e = c->fork.create();
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
   if (e != cudaSuccess) {
     delete c;
@@ -544,6 +553,7 @@ int mrv_destroy(mrv_ctx *c) {
   if (c->d_envs) cudaFree(c->d_envs);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  c->fork.destroy();
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   delete c;
   return MRV_OK;
@@ -861,6 +871,7 @@ int mrv_set_tuning(mrv_ctx *c, const mrv_tuning *t) {
   if (t->blocks_per_sm < 0) return fail(MRV_ERR_ARG, "blocks_per_sm < 0");
   if (t->tile_split < 1 || t->tile_split > 32 || (t->tile_split & (t->tile_split - 1)))
     return fail(MRV_ERR_ARG, "tile_split must be 1, 2, 4, 8, 16 or 32");
+  if (t->mv_order < 0 || t->mv_order > 1) return fail(MRV_ERR_ARG, "mv_order must be 0 or 1");
   c->tuning = *t;
   return MRV_OK;
 }

@@ -141,6 +141,7 @@ struct BatchDev {
   int32_t forced_kind;               // -1 = q_kind, else MRV_KIND_*
   int32_t slices_per_item;
   int32_t tile_split;
+  int32_t mv_order;                  // tuning: 1 = hierarchical order for MV batches naming none
   // derived (device scratch)
   int32_t *slot_tau;                 // n_waypoints: time of each waypoint
   QueryDev *q;                       // n_queries

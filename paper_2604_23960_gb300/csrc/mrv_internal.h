@@ -79,6 +79,29 @@ struct HostEnv {
   }
 };
 
+// A second stream beside a work stream for the large-team kernel instance:
+// it runs concurrently with the team instance (its one-per-SM blocks start as
+// the team kernel's blocks leave their SMs, and return at once when the batch
+// holds no such query) and is joined back before the result kernel.
+struct Fork {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    return e;
+  }
+  void destroy() {
+    if (aux) cudaStreamSynchronize(aux);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (aux) cudaStreamDestroy(aux);
+    aux = nullptr;
+    fork = join = nullptr;
+  }
+};
+
 // kernel launch wrappers (mrv_kernels.cu)
 size_t main_smem_bytes(int warps, int cls);   // cls: work class (0 team, 1 large team)
 int large_warps();                             // warps per block of the large-team instance
@@ -104,10 +127,11 @@ struct mrv_ctx {
   mrv::EnvDev *d_envs = nullptr;
   size_t cap_models = 0, cap_envs = 0;
   mrv::Scratch scratch;
-  mrv_tuning tuning{1, 4, 0, 4};
+  mrv_tuning tuning{1, 4, 0, 4, 0};
   mrv_stats stats{};
   long long clock_budget = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  mrv::Fork fork;               // second stream of the large-team instance
   void *h_pinned = nullptr;
   uint32_t *h_status = nullptr;
   unsigned long long *h_stats = nullptr;
@@ -131,7 +155,7 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
 int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
                 mrv_conflict *conf, bool timed);
 int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
-                   mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+                   mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, const Fork *fk);
 int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st);
 int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr, mrv_conflict *conf);
 int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls);

@@ -339,7 +339,9 @@ __global__ void k_prep(BatchDev B) {
     Q.split = split;
     Q.spt = kWarp / split;
     Q.nslices = Q.ntiles * split;
-    Q.nphase = (check_env && (B.flags & MRV_HIERARCHICAL)) ? 2 : 1;
+    // hierarchical order: named by the batch, or the tuned default of batches naming no order
+    const bool hier = (B.flags & MRV_HIERARCHICAL) || (B.mv_order == 1 && !(B.flags & MRV_PAIRS_FIRST));
+    Q.nphase = (check_env && hier) ? 2 : 1;
     if (mv && (B.flags & MRV_PAIRS_FIRST) && !(B.flags & MRV_EXHAUSTIVE)) {
       adjacent_pairs(B, s0, n, Q);
       if (Q.nadj > 0) Q.nphase = 2;

@@ -112,7 +112,8 @@ extern "C" int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *b, uint8_t *va
   Scratch S;   // a view only: it owns nothing (base stays null)
   carve(base, b->n_queries, b->n_waypoints, &S);
   const BatchDev B = make_batchdev(ctx, b, S, MRV_KIND_MV, ctx->tuning.slices_per_item);
-  if ((rc = enqueue_run_on(ctx, B, S, false, valid_out, nullptr, nullptr, ctx->stream, nullptr, nullptr))) return rc;
+  if ((rc = enqueue_run_on(ctx, B, S, false, valid_out, nullptr, nullptr, ctx->stream, nullptr, nullptr, &ctx->fork)))
+    return rc;
   // the error word comes back through the context's pinned status word
   e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

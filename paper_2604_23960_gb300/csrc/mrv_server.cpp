@@ -52,6 +52,7 @@ struct Slot {
   void *pin_out = nullptr;
   size_t pin_out_cap = 0;
   cudaEvent_t done_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
+  Fork fork;   // second stream of the large-team instance
   std::vector<std::shared_ptr<Request>> reqs;
   int32_t nq = 0;
   size_t footprint = 0;
@@ -189,7 +190,7 @@ void mrv_server::launch(Slot &s) {
   if (!rc) {
     BatchDev B = make_batchdev(ctx, &b, s.scratch, -1, ctx->tuning.slices_per_item);
     rc = enqueue_run_on(ctx, B, s.scratch, false, s.scratch.out_valid, nullptr, s.scratch.out_conf, s.stream, s.ev0,
-                        s.ev1);
+                        s.ev1, &s.fork);
   }
   if (!rc) {
     int which = 0;
@@ -328,6 +329,7 @@ int mrv_server_create(mrv_ctx *c, const mrv_server_opts *o, mrv_server **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&sl.ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&sl.ev1);
+    if (e == cudaSuccess) e = sl.fork.create();
     if (e != cudaSuccess) {
       int rc = cuda_fail(e, "server streams");
       mrv_server_destroy(s);
@@ -361,6 +363,7 @@ int mrv_server_destroy(mrv_server *s) {
     if (sl.done_ev) cudaEventDestroy(sl.done_ev);
     if (sl.ev0) cudaEventDestroy(sl.ev0);
     if (sl.ev1) cudaEventDestroy(sl.ev1);
+    sl.fork.destroy();
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }
   delete s;

@@ -62,6 +62,7 @@ static bool cache_lookup(const char *path, const std::string &key, mrv_tuning *t
     std::string k;
     mrv_tuning c{};
     if (in >> k >> c.slices_per_item >> c.warps_per_block >> c.blocks_per_sm >> c.tile_split && k == key) {
+      if (!(in >> c.mv_order) || c.mv_order < 0 || c.mv_order > 1) c.mv_order = 0;
       *t = c;
       found = true;  // the last entry for a key wins
     }
@@ -73,7 +74,7 @@ static void cache_store(const char *path, const std::string &key, const mrv_tuni
   if (!path) return;
   std::ofstream f(path, std::ios::app);
   f << key << ' ' << t.slices_per_item << ' ' << t.warps_per_block << ' ' << t.blocks_per_sm << ' ' << t.tile_split
-    << '\n';
+    << ' ' << t.mv_order << '\n';
 }
 
 }  // namespace mrv
@@ -108,10 +109,13 @@ extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_pa
   static const int chunks[] = {1, 2};
   static const int splits[] = {2, 4, 8, 16};
   static const int warps[] = {4, 8};
+  // the MV order is timed too when the batch names none and has obstacle checks
+  const bool orders = (b->flags & MRV_CHECK_ENV) && !(b->flags & (MRV_HIERARCHICAL | MRV_PAIRS_FIRST));
+  for (int ord = 0; ord < (orders ? 2 : 1); ++ord)
   for (int w : warps)
     for (int sp : splits)
       for (int ch : chunks) {
-      mrv_tuning t{ch, w, 0, sp};
+      mrv_tuning t{ch, w, 0, sp, orders ? ord : saved.mv_order};
       c->tuning = t;
       float total = 0.f;
       for (int rep = 0; rep < 3 && rc == MRV_OK; ++rep) {

@@ -78,7 +78,7 @@ class Stats(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("slices_per_item", C.c_int32), ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("tile_split", C.c_int32)]
+                ("tile_split", C.c_int32), ("mv_order", C.c_int32)]
 
 
 class Limits(C.Structure):
@@ -238,8 +238,8 @@ def mrv_get_stats(ctx) -> dict:
     return {k: getattr(s, k) for k, _ in Stats._fields_}
 
 
-def mrv_set_tuning(ctx, slices_per_item=1, warps_per_block=4, blocks_per_sm=0, tile_split=4):
-    t = Tuning(slices_per_item, warps_per_block, blocks_per_sm, tile_split)
+def mrv_set_tuning(ctx, slices_per_item=1, warps_per_block=4, blocks_per_sm=0, tile_split=4, mv_order=0):
+    t = Tuning(slices_per_item, warps_per_block, blocks_per_sm, tile_split, mv_order)
     _check(lib().mrv_set_tuning(ctx, C.byref(t)), ctx)
 
 

@@ -171,3 +171,38 @@ def test_clearance_diagnostic_sixteen_arms(ctx):
     ts = np.array([0, T // 2, T], np.int32)
     got = ctx.clearance(ba, 2, ts, 1024)
     np.testing.assert_allclose(got, o.clearance(2, ts), atol=PA.CLR_TOL, rtol=0)
+
+
+def test_server_mixes_team_and_large_requests():
+    """16-arm and 8-arm requests through the continuous-batching server from
+    several client threads (micro-batches holding both kernel classes, the
+    large-team instance on each stream's fork): the results of every request
+    equal those of running it alone."""
+    import threading
+    c = mrv.Context(0)
+    reqs = []
+    for w in (W.make_cage16_mv(400), W.make_cage8_mv(400)):
+        rids = [c.upload_model(m) for m in w.models]
+        eids = [c.upload_env(e) for e in w.envs]
+        ba = c.bind(w, rids, eids)
+        reqs += [mrv.slice_batch(ba, q0, q0 + 50) for q0 in range(0, 400, 50)]
+    alone = [c.run(r) for r in reqs]
+    srv = mrv.Server(c, n_streams=3, device_budget_bytes=256 << 20, max_batch_queries=200, max_pending=100)
+    got = [None] * len(reqs)
+
+    def client(ids):
+        for i in ids:
+            t = srv.submit(reqs[i])
+            got[i] = srv.wait(t, reqs[i].n_queries, timeout_ms=60000)
+
+    th = [threading.Thread(target=client, args=(list(range(k, len(reqs), 4)),)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    st = srv.stats()
+    srv.close()
+    for (va, _), (vm, _) in zip(alone, got):
+        np.testing.assert_array_equal(_np(va), _np(vm))
+    assert st["completed"] == len(reqs)
+    c.close()

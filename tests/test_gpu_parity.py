@@ -316,9 +316,23 @@ def test_tunings_do_not_change_results(ctx, tmp_path):
     ref = ctx.run(ba)
     saved = mrv.mrv_get_tuning(ctx.h)
     try:
-        for ch, wp, sp in [(1, 2, 1), (2, 8, 2), (16, 4, 8), (3, 12, 4), (1, 1, 4), (1, 4, 16), (2, 6, 32)]:
-            mrv.mrv_set_tuning(ctx.h, ch, wp, 0, sp)
+        for ch, wp, sp, mo in [(1, 2, 1, 0), (2, 8, 2, 1), (16, 4, 8, 0), (3, 12, 4, 1), (1, 1, 4, 0),
+                               (1, 4, 16, 1), (2, 6, 32, 0)]:
+            mrv.mrv_set_tuning(ctx.h, ch, wp, 0, sp, mo)
             assert same(ctx.run(ba), ref)
+        # the tuned MV order (1: hierarchical) is the order of batches naming
+        # none: exhaustive runs take the hierarchical order's work items
+        # (two phases per slice of an MV query)
+        mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 1)
+        ctx.run(ba, exhaustive=True)
+        items_tuned = ctx.stats()["work_items"]
+        mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 0)
+        ctx.run(ba, exhaustive=True, flags=mrv.MRV_HIERARCHICAL)
+        assert ctx.stats()["work_items"] == items_tuned
+        ctx.run(ba, exhaustive=True)
+        assert ctx.stats()["work_items"] < items_tuned
+        with pytest.raises(mrv.MrvError):
+            mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 2)
         t = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
         assert t["slices_per_item"] >= 1 and t["warps_per_block"] >= 1
         assert (tmp_path / "tune.txt").read_text().strip()
@@ -327,7 +341,7 @@ def test_tunings_do_not_change_results(ctx, tmp_path):
         assert same(ctx.run(ba), ref)
     finally:
         mrv.mrv_set_tuning(ctx.h, saved["slices_per_item"], saved["warps_per_block"], saved["blocks_per_sm"],
-                           saved["tile_split"])
+                           saved["tile_split"], saved["mv_order"])
 
 
 # --------------------------------------------- full sizes, benchmark launches
