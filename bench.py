@@ -203,11 +203,14 @@ def serving(ctx, duration_s=6.0, loads=(0.5, 0.8, 0.95), n_clients=64, seed=206)
                 if t > now:
                     time.sleep(t - now)
                 req = pool[int(r.integers(0, len(pool)))]
+                # arrival = the submit (a client thread that woke late does
+                # not add its own delay to the server's latency)
+                t_sub = time.perf_counter()
                 tk = srv.submit(req)
                 srv.wait(tk, req.n_queries, timeout_ms=600000)
                 fin = time.perf_counter()
                 with lock:
-                    lat.append(fin - t)
+                    lat.append(fin - t_sub)
                     done_q[0] += req.n_queries
                 t += r.exponential(n_clients / lam)
 

@@ -117,6 +117,15 @@ struct Cands {
   uint32_t yc[kCand];        // frame slot << 24 | obstacle cylinder
   int32_t np, ne, nb, ns, overflow, ny;
   uint32_t need[kWords], placed[kWords];
+  // large teams (NR > kTeamRobots): robot-level cull of the robot-robot
+  // phase.  Per robot a sphere enclosing its frame bounding spheres at the
+  // state; the phase's pair-table entries whose robot spheres overlap; the
+  // exclusive prefix of their frame-pair counts.
+  static constexpr int kCullR = NR > kTeamRobots ? NR : 1;
+  static constexpr int kCullP = NR > kTeamRobots ? NR * (NR - 1) / 2 : 1;
+  float4 rsph[kCullR];
+  int16_t kept[kCullP];
+  int32_t keptf[kCullP + 1];
 };
 
 constexpr int kEnvCache = 64;    // obstacle spheres staged per warp (more: read from L1)
@@ -1607,25 +1616,88 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   }
   __syncwarp();
   // the phase's entries of the pair table (prioritized MV: the pairs (0, j),
-  // listed first; pairs first: the adjacent pairs, listed first, or the rest)
-  const int ftot = S.rpf[C.pr1];
-  {
+  // listed first; pairs first: the adjacent pairs, listed first, or the rest);
+  // frame pair g of table entry it: test the two frames' bounding spheres
+  auto frame_pair = [&](int it, int g) {
+    const uint32_t e = S.rp[it];
+    const int i = (int)(e & 15u), j = (int)((e >> 4) & 15u), nj = (int)((e >> 8) & 15u);
+    const int u = (g * (int)(e >> 16)) >> 12, v = g - u * nj;
+    const int k = i * kMaxLinks + u, k2 = j * kMaxLinks + v;
+    const float4 bu = S.BS[k], bv = S.BS[k2];
+    if (bu.w < 0.f || bv.w < 0.f) return;
+    acc.tests += 1;
+    if (sph_hit(bu, bv)) {
+      push_cand(cl.pc, &cl.np, &cl.overflow, ((uint32_t)k << 8) | (uint32_t)k2);
+      need_frame(cl, k);
+      need_frame(cl, k2);
+    }
+  };
+  if constexpr (WS::kClass == 1) {
+    // large teams: frame pairs only for robot pairs whose enclosing spheres
+    // overlap.  Robot r's sphere: center at the middle of its frame centers'
+    // box, radius the largest distance to a frame sphere's far side, enlarged
+    // by 1e-6 relative + 1e-4 m, so it holds every frame sphere with a margin
+    // above the FP32 rounding of both tests: a frame pair whose spheres the
+    // test finds overlapping always has its robot pair kept (same candidates).
+    if (lane < n) {
+      const float4 *bs = S.BS + lane * kMaxLinks;
+      const int nl = S.rs[lane].n_links;
+      float x0 = INFINITY, y0 = INFINITY, z0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY, z1 = -INFINITY;
+      for (int l = 0; l < nl; ++l) {
+        const float4 b = bs[l];
+        if (b.w < 0.f) continue;
+        x0 = fminf(x0, b.x); y0 = fminf(y0, b.y); z0 = fminf(z0, b.z);
+        x1 = fmaxf(x1, b.x); y1 = fmaxf(y1, b.y); z1 = fmaxf(z1, b.z);
+      }
+      float4 rs = make_float4(0.f, 0.f, 0.f, -1.f);
+      if (x0 <= x1) {
+        rs.x = 0.5f * (x0 + x1); rs.y = 0.5f * (y0 + y1); rs.z = 0.5f * (z0 + z1);
+        float R = 0.f;
+        for (int l = 0; l < nl; ++l) {
+          const float4 b = bs[l];
+          if (b.w < 0.f) continue;
+          const float dx = b.x - rs.x, dy = b.y - rs.y, dz = b.z - rs.z;
+          R = fmaxf(R, sqrtf(dx * dx + dy * dy + dz * dz) + b.w);
+        }
+        rs.w = R * (1.f + 1e-6f) + 1e-4f;
+      }
+      cl.rsph[lane] = rs;
+    }
+    __syncwarp();
+    int nk = 0;
+    for (int p0 = C.pr0; p0 < C.pr1; p0 += kWarp) {
+      const int p = p0 + lane;
+      bool keep = false;
+      if (p < C.pr1) {
+        const uint32_t e = S.rp[p];
+        const float4 a = cl.rsph[e & 15u], b = cl.rsph[(e >> 4) & 15u];
+        keep = a.w >= 0.f && b.w >= 0.f && sph_hit(a, b);
+        acc.tests += 1;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) cl.kept[nk + __popc(m & ((1u << lane) - 1u))] = (int16_t)p;
+      nk += __popc(m);
+    }
+    __syncwarp();
+    int base = 0;
+    for (int i0 = 0; i0 < nk; i0 += kWarp) {
+      const int i = i0 + lane;
+      const int c = i < nk ? S.rpf[cl.kept[i] + 1] - S.rpf[cl.kept[i]] : 0;
+      base = scan_chunk(cl.keptf, i, nk, c, base, lane);
+    }
+    if (lane == 0) cl.keptf[nk] = base;
+    __syncwarp();
+    int it = 0;
+    for (int f = lane; f < base; f += kWarp) {
+      while (cl.keptf[it + 1] <= f) ++it;
+      frame_pair(cl.kept[it], f - cl.keptf[it]);
+    }
+  } else {
+    const int ftot = S.rpf[C.pr1];
     int it = C.pr0;
     for (int f = S.rpf[C.pr0] + lane; f < ftot; f += kWarp) {
       while (S.rpf[it + 1] <= f) ++it;
-      const uint32_t e = S.rp[it];
-      const int i = (int)(e & 15u), j = (int)((e >> 4) & 15u), nj = (int)((e >> 8) & 15u);
-      const int g = f - S.rpf[it];
-      const int u = (g * (int)(e >> 16)) >> 12, v = g - u * nj;
-      const int k = i * kMaxLinks + u, k2 = j * kMaxLinks + v;
-      const float4 bu = S.BS[k], bv = S.BS[k2];
-      if (bu.w < 0.f || bv.w < 0.f) continue;
-      acc.tests += 1;
-      if (sph_hit(bu, bv)) {
-        push_cand(cl.pc, &cl.np, &cl.overflow, ((uint32_t)k << 8) | (uint32_t)k2);
-        need_frame(cl, k);
-        need_frame(cl, k2);
-      }
+      frame_pair(it, f - S.rpf[it]);
     }
   }
   __syncwarp();
