@@ -67,8 +67,8 @@ MAKERS = None
 # DRAM bytes of one k_main launch of the benchmark step, from an ncu capture
 # (profiles/k_main_cage_mv_traffic.md), valid for the kernel source it was
 # taken on; any other source reports null
-TRAFFIC = {"kernel_sha256": "6794bc9873f3146752d7a9a732ac0bea66b01466ffddc768dfeb67d3287ff469",
-           "bytes": 4119552 + 768}
+TRAFFIC = {"kernel_sha256": "e267e86e8950539cc833a3e1bd764c29d8202b11b12db1383c1c81d42b7f6c26",
+           "bytes": 4443392 + 2560}
 
 
 def traffic_per_launch():

@@ -300,9 +300,10 @@ typedef struct {
                                 kinematic-chain queries (point-robot queries
                                 always use whole tiles)                      */
   int32_t mv_order;          /* order of MV queries with obstacle checks in
-                                batches whose flags name none
+                                early-exit batches whose flags name none
                                 (MRV_HIERARCHICAL, MRV_PAIRS_FIRST): 0 the
-                                combined order, 1 the hierarchical order.
+                                combined order, 1 the hierarchical order
+                                (MRV_EXHAUSTIVE runs use the combined one).
                                 Same verdicts; mrv_autotune times both.     */
 } mrv_tuning;
 int mrv_set_tuning(mrv_ctx *ctx, const mrv_tuning *t);

@@ -348,8 +348,11 @@ __global__ void k_prep(BatchDev B) {
     Q.split = split;
     Q.spt = kWarp / split;
     Q.nslices = Q.ntiles * split;
-    // hierarchical order: named by the batch, or the tuned default of batches naming no order
-    const bool hier = (B.flags & MRV_HIERARCHICAL) || (B.mv_order == 1 && !(B.flags & MRV_PAIRS_FIRST));
+    // hierarchical order: named by the batch, or the tuned order of early-exit
+    // batches naming none (an exhaustive run visits every state in any order,
+    // and two phases would only compute the link frames twice)
+    const bool hier = (B.flags & MRV_HIERARCHICAL) ||
+                      (B.mv_order == 1 && !(B.flags & (MRV_PAIRS_FIRST | MRV_EXHAUSTIVE)));
     Q.nphase = (check_env && hier) ? 2 : 1;
     if (mv && (B.flags & MRV_PAIRS_FIRST) && !(B.flags & MRV_EXHAUSTIVE)) {
       adjacent_pairs(B, s0, n, Q);

@@ -110,7 +110,7 @@ extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_pa
   static const int splits[] = {2, 4, 8, 16};
   static const int warps[] = {4, 8};
   // the MV order is timed too when the batch names none and has obstacle checks
-  const bool orders = (b->flags & MRV_CHECK_ENV) && !(b->flags & (MRV_HIERARCHICAL | MRV_PAIRS_FIRST));
+  const bool orders = (b->flags & MRV_CHECK_ENV) && !(b->flags & (MRV_HIERARCHICAL | MRV_PAIRS_FIRST | MRV_EXHAUSTIVE));
   for (int ord = 0; ord < (orders ? 2 : 1); ++ord)
   for (int w : warps)
     for (int sp : splits)

@@ -320,17 +320,21 @@ def test_tunings_do_not_change_results(ctx, tmp_path):
                                (1, 4, 16, 1), (2, 6, 32, 0)]:
             mrv.mrv_set_tuning(ctx.h, ch, wp, 0, sp, mo)
             assert same(ctx.run(ba), ref)
-        # the tuned MV order (1: hierarchical) is the order of batches naming
-        # none: exhaustive runs take the hierarchical order's work items
-        # (two phases per slice of an MV query)
+        # the tuned MV order (1: hierarchical) is the order of early-exit
+        # batches naming none; exhaustive runs keep the combined order (fewer
+        # work items: one phase per slice) unless the flag names it
         mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 1)
         ctx.run(ba, exhaustive=True)
-        items_tuned = ctx.stats()["work_items"]
-        mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 0)
+        items_tuned_ex = ctx.stats()["work_items"]
         ctx.run(ba, exhaustive=True, flags=mrv.MRV_HIERARCHICAL)
-        assert ctx.stats()["work_items"] == items_tuned
+        items_hier_ex = ctx.stats()["work_items"]
+        mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 0)
         ctx.run(ba, exhaustive=True)
-        assert ctx.stats()["work_items"] < items_tuned
+        assert ctx.stats()["work_items"] == items_tuned_ex < items_hier_ex
+        # early exit with the tuned order runs two phases: the MV queries'
+        # verdicts are those of the combined order
+        mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 1)
+        assert same(ctx.run(ba), ref)
         with pytest.raises(mrv.MrvError):
             mrv.mrv_set_tuning(ctx.h, 1, 4, 0, 4, 2)
         t = mrv.mrv_autotune(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), str(tmp_path / "tune.txt"))
