@@ -81,6 +81,27 @@ def test_mixed_classes_one_batch(ctx):
     assert st["states_checked"] == st["states_available"] == int((o.query_T() + 1).sum())
 
 
+def test_graph_replay_of_mixed_classes(ctx):
+    """A CUDA graph of a batch holding both kernel classes (the large-team
+    instance captured on the fork's stream) replays to the direct results."""
+    w = tiny_workload(1710, n_queries=150, timed=True, min_robots=1, max_robots=16, n_models=5, max_steps=10)
+    ba = ctx.bind(w).to("cuda")
+    v1, c1 = ctx.run(ba)
+    kind = torch.as_tensor(w.batch.q_kind, device="cuda")
+    vg = torch.full_like(v1, 7)
+    cg = torch.full_like(c1, 7)
+    g = mrv.mrv_graph_create(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), vg, cg)
+    for _ in range(3):
+        mrv.mrv_graph_launch(g)
+        ctx.sync()
+        assert torch.equal(vg[kind == 0], v1[kind == 0])
+        assert torch.equal(cg[kind == 1], c1[kind == 1])
+    mrv.mrv_graph_destroy(g)
+    o = O.Oracle(w)
+    PA.check_mv(o, _np(v1)[w.batch.q_kind == 0], np.nonzero(w.batch.q_kind == 0)[0])
+    PA.check_ffc(o, _np(c1)[w.batch.q_kind == 1], np.nonzero(w.batch.q_kind == 1)[0])
+
+
 def test_sphere_count_alone_selects_large_layout(ctx):
     """Three robots of 200 spheres (600 > 512): the large-team instance by
     sphere count, with dense and broadphase paths agreeing with the oracle."""

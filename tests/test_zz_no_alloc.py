@@ -32,7 +32,8 @@ def test_noalloc_matches_mv_validate_twice():
     ctx = mrv.Context(0)
     arms = ctx.bind(W.make_cage_mv(1500, query_seed=611)).to("cuda")
     discs = ctx.bind(W.make_plain_discs(700, query_seed=612)).to("cuda")
-    for ba in (arms, discs, arms):                 # back-to-back calls share the scratch
+    team16 = ctx.bind(W.make_cage16_mv(300, query_seed=613)).to("cuda")   # the large-team instance
+    for ba in (arms, discs, team16, arms):         # back-to-back calls share the scratch
         ref, got = _ref_and_noalloc(ctx, ba)
         np.testing.assert_array_equal(got, ref)
     ctx.close()
