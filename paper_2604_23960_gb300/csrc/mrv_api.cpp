@@ -274,10 +274,16 @@ cudaError_t Scratch::reset(cudaStream_t st) const {
 }
 
 int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
-  int occ = 0;
-  if (max_blocks_per_sm(warps, clr, cls, &occ) != cudaSuccess || occ < 1) {
-    cudaGetLastError();
-    occ = 1;
+  // the occupancy of a kernel configuration does not change: queried once
+  int *slot = (warps >= 1 && warps <= 12) ? &ctx->occ[clr ? 1 : 0][cls ? 1 : 0][warps] : nullptr;
+  int occ = slot ? *slot : 0;
+  if (occ < 1) {
+    if (max_blocks_per_sm(warps, clr, cls, &occ) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    } else if (slot) {
+      *slot = occ;
+    }
   }
   if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
   return ctx->num_sms * occ;

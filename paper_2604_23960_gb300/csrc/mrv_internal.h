@@ -132,6 +132,7 @@ struct mrv_ctx {
   long long clock_budget = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   mrv::Fork fork;               // second stream of the large-team instance
+  int occ[2][2][13] = {};       // resident blocks per SM by [clearance][class][warps] (0: not queried yet)
   void *h_pinned = nullptr;
   uint32_t *h_status = nullptr;
   unsigned long long *h_stats = nullptr;
