@@ -620,7 +620,9 @@ def run(args):
                    "sphere_tests_vs_dense": st_step["sphere_tests"] / max(1, st_step["sphere_tests_available"])},
         "valid_total": f"{nvalid}/{nq}",
         "kernel_ms_mean": kms,
-        "gpu_launches": 5 * args.steps,
+        # per graph step: k_prep, k_levels, k_scatter, the team k_main, the
+        # large-team k_main (forked beside it; no work item on this batch), k_finish
+        "gpu_launches": 6 * args.steps,
         "clocks": clocks,
     }
     if not args.no_configs:
