@@ -16,6 +16,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -425,8 +426,32 @@ def cpu_baseline(w, seconds_hint: float = 20.0):
     t0 = time.perf_counter()
     o.mv(idx, threads=threads)
     dt = time.perf_counter() - t0
+    # one core on a fixed subset of about a fifth of that time
+    k1 = int(min(n, max(64, 0.2 * seconds_hint / max(per_q * threads, 1e-9))))
+    t1 = time.perf_counter()
+    o.mv(np.arange(k1), threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": k / dt, "unit": "motion-checks/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {k} of the {n} motions, FP64 scalar MV with early exit, {threads} threads"}
+            "sample": f"first {k} of the {n} motions, FP64 scalar MV with early exit, {threads} threads",
+            "cpu": _cpu_model(),
+            "single_core": {"value": k1 / dt1, "unit": "motion-checks/s", "cores": 1,
+                            "sample": f"first {k1} of the {n} motions, one thread"}}
+
+
+def _cpu_model() -> str:
+    """The host CPU's name as the kernel reports it (x86 model name, or the
+    Arm implementer / part numbers), with the core count."""
+    info = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    name = info.get("model name") or " ".join(
+        f"{k} {info[k]}" for k in ("CPU implementer", "CPU part") if k in info) or platform.machine()
+    return f"{name}, {os.cpu_count()} logical cores"
+
 
 
 def run_reference(args):
