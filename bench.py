@@ -410,6 +410,51 @@ def order_study(ctx, ba, flush, reps=3, linear=True):
     return out
 
 
+def validation_study(ctx, flush, n_queries=500, reps=3):
+    """The paper's validation experiment (Sec. V-B, its validation table) on
+    the synthetic stand-ins: 500 Cage motions with valid endpoints for 4, 8
+    and 16 arms, with and without obstacles; per state order (combined or
+    hierarchical x rake or linear packing): valid/total, the effort of early
+    termination (sphere tests executed / available, dense kernel; states
+    checked / available) and k_main time with the frame-level broadphase and
+    dense, early-terminating and exhaustive."""
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import workloads as W
+    saved = mrv.mrv_get_tuning(ctx.h)
+    mrv.mrv_set_tuning(ctx.h, **dict(saved, mv_order=0))   # flags 0: the combined order
+    orders = [("combined_rake", 0), ("hierarchical_rake", mrv.MRV_HIERARCHICAL),
+              ("combined_linear", mrv.MRV_LINEAR), ("hierarchical_linear", mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR)]
+
+    def kernel_ms(ba, flags, exhaustive):
+        ctx.mv_validate(ba, flags=flags, exhaustive=exhaustive)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            ctx.mv_validate(ba, flags=flags, exhaustive=exhaustive)
+            ms.append(ctx.stats()["device_ms"])
+        return statistics.median(ms), ctx.stats()
+
+    out = {}
+    for n in (4, 8, 16):
+        for obst in (True, False):
+            w = W.make_cage_team_study(n, n_queries, obstacles=obst)
+            ba = ctx.bind(w).to("cuda")
+            v = ctx.mv_validate(ba)
+            cell = {"valid_total": f"{int(v.sum().item())}/{n_queries}"}
+            for name, fl in orders:
+                ms_b, st_b = kernel_ms(ba, fl, False)
+                ms_d, st_d = kernel_ms(ba, fl | mrv.MRV_NO_BROADPHASE, False)
+                ex_b, _ = kernel_ms(ba, fl, True)
+                ex_d, _ = kernel_ms(ba, fl | mrv.MRV_NO_BROADPHASE, True)
+                cell[name] = {"effort_tests": st_d["sphere_tests"] / max(1, st_d["sphere_tests_available"]),
+                              "effort_states": st_b["states_checked"] / max(1, st_b["states_available"]),
+                              "kernel_ms": ms_b, "kernel_ms_dense": ms_d,
+                              "exhaustive_ms": ex_b, "exhaustive_ms_dense": ex_d}
+            out[f"{n}_arms_{'obstacles' if obst else 'no_obstacles'}"] = cell
+    mrv.mrv_set_tuning(ctx.h, **saved)
+    return out
+
+
 def cpu_baseline(w, seconds_hint: float = 20.0):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
     from oracle import oracle as O
@@ -652,6 +697,7 @@ def run(args):
     }
     if not args.no_configs:
         line["configs"] = other_configs(ctx, flush)
+        line["validation_study"] = validation_study(ctx, flush)
     if not args.no_serve:
         line["serving"] = serving(ctx, args.serve_seconds)
     if world == 1 and not args.no_cpu_baseline:

@@ -603,6 +603,34 @@ def make_cage16_ffc(n_queries: int = 10000, query_seed: int = 210, fixtures: Opt
     return w
 
 
+def make_cage_team_study(n_arms: int, n_queries: int = 500, query_seed: int = 211, obstacles: bool = True,
+                         fixtures: Optional[dict] = None, fixtures16: Optional[dict] = None) -> Workload:
+    """The validation study's motions (Sec. V-B: 500 random Cage motions with
+    valid endpoints for 4, 8 and 16 Pandas, with and without obstacles): the
+    first n_arms arms of the 16-arm team (4: the floor corners; 8: the
+    floor- and ceiling-mounted 8-arm team), whole motions between two of the
+    whole-team valid configurations restricted to those arms (a valid team
+    stays valid without some of its arms); resolution 1/32 rad; the cylinder
+    cage, or no obstacles (self and robot-robot checks only)."""
+    if n_arms not in (4, 8, 16):
+        raise ValueError("n_arms must be 4, 8 or 16")
+    fx = load_cage_fixtures() if fixtures is None else fixtures
+    f16 = load_cage16_fixtures() if fixtures16 is None else fixtures16
+    models = cage16_arms(fx)[:n_arms]
+    team = f16["team_states"][:, :n_arms]            # (K, n_arms, 7)
+    K = team.shape[0]
+    rng = np.random.default_rng(query_seed + n_arms)
+    a = rng.integers(0, K, n_queries)
+    b = (a + rng.integers(1, K, n_queries)) % K
+    cfg = np.stack([team[a], team[b]], axis=2)       # (Q, n_arms, 2, 7)
+    bt = _fast_batch(n_queries, n_arms, np.tile(np.arange(n_arms), n_queries), cfg.reshape(-1, 7), None,
+                     1.0 / 32.0, KIND_MV, 0 if obstacles else -1)
+    envs = [cage_env_cyl()] if obstacles else []
+    return Workload(f"cage{n_arms}_study{'_obst' if obstacles else ''}", models, envs, bt,
+                    env=0 if obstacles else -1, check_env=True,
+                    meta={"robots": n_arms, "obstacles": obstacles, "resolution": 1.0 / 32.0})
+
+
 TEAM_ARM_BASES = [(4.4, 5.0, 0.0), (5.6, 5.0, math.pi)]
 TEAM_PAD = (3.8, 3.8, 6.2, 6.2)
 

@@ -227,3 +227,21 @@ def test_server_mixes_team_and_large_requests():
         np.testing.assert_array_equal(_np(va), _np(vm))
     assert st["completed"] == len(reqs)
     c.close()
+
+
+@pytest.mark.parametrize("n_arms", [4, 8, 16])
+@pytest.mark.parametrize("obstacles", [True, False])
+def test_validation_study_motions(ctx, n_arms, obstacles):
+    """The validation study's motions (4, 8 and 16 arms between whole-team
+    valid configurations, with and without obstacles): every order against
+    the oracle, early-terminating and exhaustive."""
+    w = W.make_cage_team_study(n_arms, 120, obstacles=obstacles)
+    o = O.Oracle(w)
+    ba = ctx.bind(w).to("cuda")
+    v = _np(ctx.mv_validate(ba))
+    PA.check_mv(o, v)
+    for fl in (mrv.MRV_HIERARCHICAL, mrv.MRV_LINEAR, mrv.MRV_HIERARCHICAL | mrv.MRV_LINEAR, mrv.MRV_NO_BROADPHASE):
+        np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=fl)), v)
+        np.testing.assert_array_equal(_np(ctx.mv_validate(ba, flags=fl, exhaustive=True)), v)
+        st = ctx.stats()
+        assert st["states_checked"] == st["states_available"]
