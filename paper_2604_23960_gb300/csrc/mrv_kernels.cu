@@ -1321,6 +1321,102 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WS &S, const uint32_t 
   return hit;
 }
 
+// Resolves the self-pair groups in the candidate list (blocks: lane = one
+// row sphere of a group's block; pair lists: contiguous runs per lane), after
+// placing the frames they need; returns this lane's hit and empties the list.
+// The large-team instance calls it once per batch of groups; the team
+// instance keeps the same steps inline in broad_state (as a call they
+// measured about 3% slower there).
+template <class WS>
+__device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int jj, int lane, BroadAcc &acc) {
+  auto &cl = S.u.b.cl;
+  const float4 *P = S.u.b.P;
+  bool hit = false;
+  if (!cl.ns) return false;
+  if (C.self_blk) {
+    // self pairs as blocks: lane = one row sphere of an overlapping
+    // group's block, tested against the columns its mask lists (lanes of
+    // one block read the same column spheres)
+    place_needed(C, S, xf, jj, lane, acc);
+    const int ns = cl.ns;
+    int base = 0;
+    for (int i0 = 0; i0 < ns; i0 += kWarp) {
+      const int i = i0 + lane;
+      int c = 0;
+      if (i < ns) {
+        const uint32_t v = cl.sc[i];
+        const int r = (int)(v >> 16);
+        const int4 Bk = __ldg(&S.rs[r].md->self_blocks[v & 0xffffu]);
+        const int o = S.off[r];
+        c = Bk.z & 0xffff;
+        cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 10) | ((uint32_t)r << 20);
+        cl.scn[i] = (uint16_t)Bk.w;
+        cl.sck[i] = (uint8_t)(r * kMaxLinks + ((Bk.z >> 24) & 15));
+      }
+      base = scan_chunk(cl.pf, i, ns, c, base, lane);
+    }
+    if (lane == 0) cl.pf[ns] = base;
+    __syncwarp();
+    int it = 0;
+    uint32_t nt = 0;
+    for (int f = lane; f < base; f += kWarp) {
+      while (cl.pf[it + 1] <= f) ++it;
+      const uint32_t v = cl.sc[it];
+      const int row = f - cl.pf[it];
+      const float4 pa = P[(int)(v & 1023u) + row];
+      // a row sphere clear of the column frame's bounding sphere is clear
+      // of every column sphere
+      nt += 1;
+      if (!sph_hit(pa, S.BS[cl.sck[it]])) continue;
+      const float4 *Pc = P + ((v >> 10) & 1023u);
+      uint32_t mk = __ldg(&S.rs[v >> 20].masks[cl.scn[it] + row]);
+      nt += (uint32_t)__popc(mk);
+      while (mk) {
+        const int c = __ffs(mk) - 1;
+        mk &= mk - 1;
+        hit |= sph_hit(pa, Pc[c]);
+      }
+    }
+    acc.tests += nt;
+    __syncwarp();
+  } else {
+    // self pairs from the pair list, one contiguous run per lane
+    place_needed(C, S, xf, jj, lane, acc);
+    const int ns = cl.ns;
+    int base = 0;
+    for (int i0 = 0; i0 < ns; i0 += kWarp) {
+      const int i = i0 + lane;
+      int c = 0;
+      if (i < ns) c = cl.scn[i];
+      base = scan_chunk(cl.pf, i, ns, c, base, lane);
+    }
+    if (lane == 0) cl.pf[ns] = base;
+    __syncwarp();
+    const int per = (base + kWarp - 1) / kWarp;
+    int f = lane * per;
+    const int fe = min(f + per, base);
+    if (f < fe) {
+      acc.tests += (uint32_t)(fe - f);
+      for (int it = list_find(cl.pf, ns, f); f < fe; ++it) {
+        const uint32_t v = cl.sc[it];
+        const int r = (int)(v >> 16);
+        const int ge = min(fe, cl.pf[it + 1]);
+        const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
+        const float4 *Pr = P + S.off[r];
+#pragma unroll 4
+        for (; f < ge; ++f) {
+          const uint32_t e = __ldg(&pr[f]);
+          hit |= sph_hit(Pr[e & 0xffffu], Pr[e >> 16]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) cl.ns = 0;
+  __syncwarp();
+  return hit;
+}
+
 // One state of the broadphase path: MV -> 1 on a collision, FFC -> the
 // code of the first colliding robot pair (0: none).  MV checks the obstacles, then the self
 // pairs, then the other robots, with a warp vote after each (all three
@@ -1500,113 +1596,154 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
       }
       // self-pair groups by their frames' bounding spheres
-      for (int r = 0; r < C.self_robots; ++r) {
-        const int4 *groups = S.rs[r].md->self_groups;
-        const int ng = S.rs[r].n_groups;
-        for (int g = lane; g < ng; g += kWarp) {
-          const int4 G = __ldg(&groups[g]);
-          acc.tests += 1;
-          if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
-            const int i = atomicAdd(&cl.ns, 1);
-            if (i < kCand) {
+      if constexpr (WS::kClass == 1) {
+        // large teams: 32 groups at a time, the overlapping ones appended to
+        // the list in order, and the list resolved (with a vote) whenever the
+        // next 32 might not fit, so it never overflows (16 arms: about 100 of
+        // 432 groups overlap at a state)
+        for (int r = 0; r < C.self_robots; ++r) {
+          const int4 *groups = S.rs[r].md->self_groups;
+          const int ng = S.rs[r].n_groups;
+          for (int g0 = 0; g0 < ng; g0 += kWarp) {
+            const int g = g0 + lane;
+            int4 G = make_int4(0, 0, 0, 0);
+            bool ov = false;
+            if (g < ng) {
+              G = __ldg(&groups[g]);
+              acc.tests += 1;
+              ov = sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y]);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ov);
+            if (!m) continue;
+            if (cl.ns + __popc(m) > kCand) {
+              hit |= resolve_self_list(C, S, xf, jj, lane, acc);
+              if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
+            }
+            if (ov) {
+              const int i = cl.ns + __popc(m & ((1u << lane) - 1u));
               // blocks: robot << 16 | group; pair list: robot << 16 | first pair
               cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)(C.self_blk ? g : G.z);
               cl.scn[i] = (uint16_t)G.w;
-            } else {
-              cl.overflow = 1;
+              need_frame(cl, r * kMaxLinks + G.x);
+              need_frame(cl, r * kMaxLinks + G.y);
             }
-            need_frame(cl, r * kMaxLinks + G.x);
-            need_frame(cl, r * kMaxLinks + G.y);
+            __syncwarp();
+            if (lane == 0) cl.ns += __popc(m);
+            __syncwarp();
           }
         }
-      }
-      __syncwarp();
-      if (cl.overflow) {
-        need_all(cl, lane);
-        place_needed(C, S, xf, jj, lane, acc);
-        unsigned long long t = 0, bx = 0, cy = 0;
-        hit |= env_broad(C, S, P, lane, t, bx, cy);
-        acc.tests += (uint32_t)t;
-        acc.boxes += (uint32_t)bx;
-        acc.cyls += (uint32_t)cy;
-      } else if (cl.ns && C.self_blk) {
-        // self pairs as blocks: lane = one row sphere of an overlapping
-        // group's block, tested against the columns its mask lists (lanes of
-        // one block read the same column spheres)
-        place_needed(C, S, xf, jj, lane, acc);
-        const int ns = cl.ns;
-        int base = 0;
-        for (int i0 = 0; i0 < ns; i0 += kWarp) {
-          const int i = i0 + lane;
-          int c = 0;
-          if (i < ns) {
-            const uint32_t v = cl.sc[i];
-            const int r = (int)(v >> 16);
-            const int4 Bk = __ldg(&S.rs[r].md->self_blocks[v & 0xffffu]);
-            const int o = S.off[r];
-            c = Bk.z & 0xffff;
-            cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 9) | ((uint32_t)r << 24);
-            cl.scn[i] = (uint16_t)Bk.w;
-            cl.sck[i] = (uint8_t)(r * kMaxLinks + ((Bk.z >> 24) & 15));
-          }
-          base = scan_chunk(cl.pf, i, ns, c, base, lane);
-        }
-        if (lane == 0) cl.pf[ns] = base;
-        __syncwarp();
-        int it = 0;
-        uint32_t nt = 0;
-        for (int f = lane; f < base; f += kWarp) {
-          while (cl.pf[it + 1] <= f) ++it;
-          const uint32_t v = cl.sc[it];
-          const int row = f - cl.pf[it];
-          const float4 pa = P[(int)(v & 511u) + row];
-          // a row sphere clear of the column frame's bounding sphere is clear
-          // of every column sphere
-          nt += 1;
-          if (!sph_hit(pa, S.BS[cl.sck[it]])) continue;
-          const float4 *Pc = P + ((v >> 9) & 511u);
-          uint32_t mk = __ldg(&S.rs[v >> 24].masks[cl.scn[it] + row]);
-          nt += (uint32_t)__popc(mk);
-          while (mk) {
-            const int c = __ffs(mk) - 1;
-            mk &= mk - 1;
-            hit |= sph_hit(pa, Pc[c]);
+        hit |= resolve_self_list(C, S, xf, jj, lane, acc);
+      } else {
+        // team layout: one pass (about 25 of the 4-arm cage's 108 groups
+        // overlap); an overflowing list sends env and self to the lanes
+        for (int r = 0; r < C.self_robots; ++r) {
+          const int4 *groups = S.rs[r].md->self_groups;
+          const int ng = S.rs[r].n_groups;
+          for (int g = lane; g < ng; g += kWarp) {
+            const int4 G = __ldg(&groups[g]);
+            acc.tests += 1;
+            if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
+              const int i = atomicAdd(&cl.ns, 1);
+              if (i < kCand) {
+                // blocks: robot << 16 | group; pair list: robot << 16 | first pair
+                cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)(C.self_blk ? g : G.z);
+                cl.scn[i] = (uint16_t)G.w;
+              } else {
+                cl.overflow = 1;
+              }
+              need_frame(cl, r * kMaxLinks + G.x);
+              need_frame(cl, r * kMaxLinks + G.y);
+            }
           }
         }
-        acc.tests += nt;
         __syncwarp();
-      } else if (cl.ns) {
-        // self pairs from the pair list, one contiguous run per lane
-        place_needed(C, S, xf, jj, lane, acc);
-        const int ns = cl.ns;
-        int base = 0;
-        for (int i0 = 0; i0 < ns; i0 += kWarp) {
-          const int i = i0 + lane;
-          int c = 0;
-          if (i < ns) c = cl.scn[i];
-          base = scan_chunk(cl.pf, i, ns, c, base, lane);
-        }
-        if (lane == 0) cl.pf[ns] = base;
-        __syncwarp();
-        const int per = (base + kWarp - 1) / kWarp;
-        int f = lane * per;
-        const int fe = min(f + per, base);
-        if (f < fe) {
-          acc.tests += (uint32_t)(fe - f);
-          for (int it = list_find(cl.pf, ns, f); f < fe; ++it) {
+        if (cl.overflow) {
+          need_all(cl, lane);
+          place_needed(C, S, xf, jj, lane, acc);
+          unsigned long long t = 0, bx = 0, cy = 0;
+          hit |= env_broad(C, S, P, lane, t, bx, cy);
+          acc.tests += (uint32_t)t;
+          acc.boxes += (uint32_t)bx;
+          acc.cyls += (uint32_t)cy;
+        } else if (cl.ns && C.self_blk) {
+          // self pairs as blocks: lane = one row sphere of an overlapping
+          // group's block, tested against the columns its mask lists (lanes of
+          // one block read the same column spheres)
+          place_needed(C, S, xf, jj, lane, acc);
+          const int ns = cl.ns;
+          int base = 0;
+          for (int i0 = 0; i0 < ns; i0 += kWarp) {
+            const int i = i0 + lane;
+            int c = 0;
+            if (i < ns) {
+              const uint32_t v = cl.sc[i];
+              const int r = (int)(v >> 16);
+              const int4 Bk = __ldg(&S.rs[r].md->self_blocks[v & 0xffffu]);
+              const int o = S.off[r];
+              c = Bk.z & 0xffff;
+              cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 10) | ((uint32_t)r << 20);
+              cl.scn[i] = (uint16_t)Bk.w;
+              cl.sck[i] = (uint8_t)(r * kMaxLinks + ((Bk.z >> 24) & 15));
+            }
+            base = scan_chunk(cl.pf, i, ns, c, base, lane);
+          }
+          if (lane == 0) cl.pf[ns] = base;
+          __syncwarp();
+          int it = 0;
+          uint32_t nt = 0;
+          for (int f = lane; f < base; f += kWarp) {
+            while (cl.pf[it + 1] <= f) ++it;
             const uint32_t v = cl.sc[it];
-            const int r = (int)(v >> 16);
-            const int ge = min(fe, cl.pf[it + 1]);
-            const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
-            const float4 *Pr = P + S.off[r];
-#pragma unroll 4
-            for (; f < ge; ++f) {
-              const uint32_t e = __ldg(&pr[f]);
-              hit |= sph_hit(Pr[e & 0xffffu], Pr[e >> 16]);
+            const int row = f - cl.pf[it];
+            const float4 pa = P[(int)(v & 1023u) + row];
+            // a row sphere clear of the column frame's bounding sphere is clear
+            // of every column sphere
+            nt += 1;
+            if (!sph_hit(pa, S.BS[cl.sck[it]])) continue;
+            const float4 *Pc = P + ((v >> 10) & 1023u);
+            uint32_t mk = __ldg(&S.rs[v >> 20].masks[cl.scn[it] + row]);
+            nt += (uint32_t)__popc(mk);
+            while (mk) {
+              const int c = __ffs(mk) - 1;
+              mk &= mk - 1;
+              hit |= sph_hit(pa, Pc[c]);
             }
           }
+          acc.tests += nt;
+          __syncwarp();
+        } else if (cl.ns) {
+          // self pairs from the pair list, one contiguous run per lane
+          place_needed(C, S, xf, jj, lane, acc);
+          const int ns = cl.ns;
+          int base = 0;
+          for (int i0 = 0; i0 < ns; i0 += kWarp) {
+            const int i = i0 + lane;
+            int c = 0;
+            if (i < ns) c = cl.scn[i];
+            base = scan_chunk(cl.pf, i, ns, c, base, lane);
+          }
+          if (lane == 0) cl.pf[ns] = base;
+          __syncwarp();
+          const int per = (base + kWarp - 1) / kWarp;
+          int f = lane * per;
+          const int fe = min(f + per, base);
+          if (f < fe) {
+            acc.tests += (uint32_t)(fe - f);
+            for (int it = list_find(cl.pf, ns, f); f < fe; ++it) {
+              const uint32_t v = cl.sc[it];
+              const int r = (int)(v >> 16);
+              const int ge = min(fe, cl.pf[it + 1]);
+              const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
+              const float4 *Pr = P + S.off[r];
+      #pragma unroll 4
+              for (; f < ge; ++f) {
+                const uint32_t e = __ldg(&pr[f]);
+                hit |= sph_hit(Pr[e & 0xffffu], Pr[e >> 16]);
+              }
+            }
+          }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
     if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
