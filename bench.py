@@ -68,8 +68,8 @@ MAKERS = None
 # DRAM bytes of one k_main launch of the benchmark step, from an ncu capture
 # (profiles/k_main_cage_mv_traffic.md), valid for the kernel source it was
 # taken on; any other source reports null
-TRAFFIC = {"kernel_sha256": "e267e86e8950539cc833a3e1bd764c29d8202b11b12db1383c1c81d42b7f6c26",
-           "bytes": 4443392 + 2560}
+TRAFFIC = {"kernel_sha256": "1d43cef9368475bb945ea0375a261a77dc6ee44d5ef8960291f6578e38011258",
+           "bytes": 4441600 + 8192}
 
 
 def traffic_per_launch():
