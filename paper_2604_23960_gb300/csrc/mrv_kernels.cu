@@ -2256,9 +2256,8 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
   const bool skip_dead = !(B.flags & MRV_EXHAUSTIVE);
   unsigned long long items = 0;
   // Items are claimed g at a time.  Lane l < g resolves item base + l (level,
-  // query) and whether its query already has a verdict: items are ordered by
-  // level, so an item claimed after its query's verdict is past it (MV: any
-  // collision ends the query; FFC: the conflict lies at a lower level).  g
+  // query) and whether its query already has a verdict that makes it dead
+  // (MV: any collision; FFC: a conflict before the item's first state).  g
   // doubles while whole claims are settled and drops back to 1 at live work,
   // so live items are still spread one per claim.
   int g = 1;
@@ -2286,8 +2285,17 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
       }
       lvl = lo;
       q = __ldg(&B.sorted[qbase + idx - __ldg(&level_start[lo])]);
-      live = !skip_dead ||
-             (*(volatile int *)&B.q_hit[q] == 0 && *(volatile int *)&B.q_best[q] == 0x7fffffff);
+      if (!skip_dead) {
+        live = true;
+      } else {
+        // MV: any collision ends the query.  FFC: only a conflict before
+        // the item's first state makes it dead (another warp may record a
+        // later item's conflict between this claim and this check)
+        const int best = *(volatile int *)&B.q_best[q];
+        live = *(volatile int *)&B.q_hit[q] == 0 &&
+               (best == 0x7fffffff ||
+                best >= (min(lo * __ldg(&B.q[q].cte) * __ldg(&B.q[q].spt), __ldg(&B.q[q].T)) << kKeyShift));
+      }
     }
     unsigned live_mask = __ballot_sync(0xffffffffu, live);
     g = live_mask ? 1 : min(2 * g, kWarp);

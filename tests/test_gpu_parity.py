@@ -413,3 +413,26 @@ def test_longest_motions(ctx):
            [[T + 1], [1]])
     with pytest.raises(mrv.MrvError):
         ctx.ffc_find(ctx.bind(W.Workload("toolong", [disc], [], bb.build(0.05), env=-1, check_env=False)))
+
+
+def test_ffc_repeatable_under_concurrent_claims(ctx):
+    """FFC work items of one query run on many warps at once, and a warp may
+    check an item's liveness long after claiming it; an item may only be
+    skipped for a conflict before its own first state.  Repeated runs of
+    long timed paths (and of both MV orders on mixed batches) give identical
+    first conflicts, equal to the oracle's on a sample."""
+    w = W.make_cage_ffc(20000, query_seed=41)
+    ba = ctx.bind(w).to("cuda")
+    ref = _np(ctx.ffc_find(ba))
+    for _ in range(6):
+        np.testing.assert_array_equal(_np(ctx.ffc_find(ba)), ref)
+    idx = PA.sample(w.batch.n_queries, 200, seed=3)
+    PA.check_ffc(O.Oracle(w), ref[idx], idx)
+    wr = W.make_ragged_teams(20000, seed=79)
+    br = ctx.bind(wr).to("cuda")
+    kind = wr.batch.q_kind
+    v0, c0 = (_np(x) for x in ctx.run(br))
+    for fl in (0, mrv.MRV_HIERARCHICAL, 0, mrv.MRV_HIERARCHICAL):
+        v, c = (_np(x) for x in ctx.run(br, flags=fl))
+        np.testing.assert_array_equal(v[kind == 0], v0[kind == 0])
+        np.testing.assert_array_equal(c[kind == 1], c0[kind == 1])
