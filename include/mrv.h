@@ -294,7 +294,8 @@ int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
  * work item is slices_per_item consecutive slices of one query. */
 typedef struct {
   int32_t slices_per_item;   /* slices per work item (>= 1)                  */
-  int32_t warps_per_block;   /* 1..12 (17 KB of shared memory per warp)      */
+  int32_t warps_per_block;   /* 1..12 (18.7 KB of shared memory per warp; the
+                                large-team instance uses 6 warps of 35.1 KB) */
   int32_t blocks_per_sm;     /* 0 = as many as fit                           */
   int32_t tile_split;        /* 1, 2, 4, 8, 16 or 32 slices per 32-state tile for
                                 kinematic-chain queries (point-robot queries
