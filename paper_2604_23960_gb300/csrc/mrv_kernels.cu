@@ -2262,13 +2262,17 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
   // so live items are still spread one per claim.
   int g = 1;
   for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&B.counters[cls ? 4 : 0], g);
+    // the abort flag is read together with the claim (both round trips at once)
+    int base = 0, aborted = 0;
+    if (lane == 0) {
+      base = atomicAdd(&B.counters[cls ? 4 : 0], g);
+      aborted = *(volatile int *)&B.counters[2];
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_items) break;
     int halt = 0;
     if (lane == 0) {
-      if (*(volatile int *)&B.counters[2]) halt = 1;
+      if (aborted) halt = 1;
       else if (B.clock_budget > 0 && clock64() - t_start > B.clock_budget) halt = 2;
       if (halt) atomicOr(B.err, halt == 1 ? kErrAbort : kErrTimeout);
     }
