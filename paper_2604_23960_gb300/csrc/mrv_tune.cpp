@@ -107,7 +107,7 @@ extern "C" int mrv_autotune(mrv_ctx *c, const mrv_batch *b, const char *cache_pa
   uint8_t *valid = (uint8_t *)outs + ((size_t)b->n_queries * sizeof(mrv_conflict) + 255) / 256 * 256;
   const mrv_tuning saved = c->tuning;
   float best_ms = INFINITY;
-  static const int chunks[] = {1, 2};
+  static const int chunks[] = {1, 2, 4};
   static const int splits[] = {2, 4, 8, 16};
   static const int warps[] = {4, 8};
   // the MV order is timed too when the batch names none and has obstacle checks
