@@ -311,15 +311,18 @@ int mrv_set_tuning(mrv_ctx *ctx, const mrv_tuning *t);
 int mrv_get_tuning(mrv_ctx *ctx, mrv_tuning *t);
 
 /* Times candidate tunings on `batch` (MRV_PTRS_ON_DEVICE, run through
- * mrv_run semantics), keeps the fastest in the context, and caches it in the
- * text file `cache_path` (nullable) keyed by device name and a batch class
- * (robot count, sphere count and length buckets, query kinds).  A cached
- * entry is reused without timing. */
+ * mrv_run semantics): 1, 2 or 4 slices per item x 2, 4, 8 or 16 slices per
+ * tile x 4- or 8-warp blocks, and both MV orders when the batch has obstacle
+ * checks and names no order; each scored by the fastest of four timed runs.
+ * Keeps the fastest in the context and caches it in the text file
+ * `cache_path` (nullable) keyed by device name and a batch class (robot
+ * count, sphere count and length buckets, query kinds).  A cached entry is
+ * reused without timing. */
 int mrv_autotune(mrv_ctx *ctx, const mrv_batch *batch, const char *cache_path, mrv_tuning *chosen);
 
 /* ---- CUDA-graph replay of one batch ----------------------------------------
  * Captures the whole mixed run of a device-resident batch (counter reset,
- * preparation kernels, persistent kernel, result kernel) into a CUDA graph
+ * preparation kernels, both persistent kernel instances, result kernel) into a CUDA graph
  * bound to these exact pointers; mrv_graph_launch replays it on the
  * context's stream (asynchronous; mrv_sync waits). */
 typedef struct mrv_graph mrv_graph;
