@@ -547,6 +547,32 @@ int orc_ffc(const orc_batch *b, const orc_robot *robots, int q, int32_t *out3) {
   return rc;
 }
 
+/* The first conflict deeper than a bound: the lexicographically smallest
+ * (t, i, j), i < j, whose pair clearance is below `bound` (Alg. 2's order
+ * with the collision test `clearance < 0` replaced by `clearance < bound`),
+ * or (-1, -1, -1).  With bound = -margin it is the first pair that every
+ * correct FP32 answer must not skip: an answer later than it passed over a
+ * collision deeper than the decidability margin. */
+int orc_ffc_below(const orc_batch *b, const orc_robot *robots, int q, double bound, int32_t *out3) {
+  int64_t T;
+  out3[0] = out3[1] = out3[2] = -1;
+  if (orc_query_T(b, robots, q, &T)) return -1;
+  qstate qs;
+  if (qstate_init(&qs, b, robots, q)) return -1;
+  int rc = 0, found = 0;
+  for (int64_t t = 0; !found && t <= T; ++t) {
+    if ((rc = qstate_fk(&qs, b, robots, q, T, t))) break;
+    for (int i = 0; i < qs.n && !found; ++i)
+      for (int j = i + 1; j < qs.n && !found; ++j)
+        if (pair_min(&qs, i, j) < bound) {
+          out3[0] = (int32_t)t; out3[1] = i; out3[2] = j;
+          found = 1;
+        }
+  }
+  qstate_free(&qs);
+  return rc;
+}
+
 /* FFC decidability: 1 iff every robot pair visited before the answer (in
  * (t, i, j) order) has clearance > margin and the answer's pair has
  * clearance < -margin (no answer: every pair at every state > margin). */
@@ -663,7 +689,7 @@ int orc_clearance(const orc_batch *b, const orc_robot *robots, const orc_env *en
 /* batch drivers (independent queries, static interleaved partition)         */
 /* ------------------------------------------------------------------------ */
 
-enum { JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T, JOB_MV_PRIO, JOB_MINCLR_PRIO };
+enum { JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T, JOB_MV_PRIO, JOB_MINCLR_PRIO, JOB_FFC_BELOW };
 
 typedef struct {
   int job;
@@ -718,6 +744,9 @@ static void *job_run(void *arg) {
       case JOB_MINCLR_PRIO:
         rc = orc_mv_prio_min_clearance(J->b, J->robots, e, J->check_env, q, J->param,
                                        (double *)J->out + k);
+        break;
+      case JOB_FFC_BELOW:
+        rc = orc_ffc_below(J->b, J->robots, q, J->param, (int32_t *)J->out + 3 * (size_t)k);
         break;
     }
     if (rc && !J->rc) J->rc = rc;

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
 CPU-baseline leg of the benchmark, never by the product path.  It marshals the
 seeded workload arrays (numpy, the same FP32 values the CUDA path reads) into
 the oracle's own C structs and calls the plain-definition routines: MV
-(Alg. 1), FFC (Alg. 2), decidability margins, per-sphere clearances and the
+(Alg. 1), FFC (Alg. 2), the first conflict deeper than a bound, decidability margins, per-sphere clearances and the
 composite step count (Sec. IV-A3).
 """
 from __future__ import annotations
@@ -26,7 +26,7 @@ LIB = Path(os.environ.get("MRV_ORACLE_LIB", HERE / "liboracle.so"))
 _lock = threading.Lock()
 _lib = None
 
-JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T, JOB_MV_PRIO, JOB_MINCLR_PRIO = range(7)
+JOB_MV, JOB_FFC, JOB_MINCLR, JOB_FFC_DEC, JOB_T, JOB_MV_PRIO, JOB_MINCLR_PRIO, JOB_FFC_BELOW = range(8)
 
 
 def build(force: bool = False, src: Path = SRC, out: Path = None) -> Path:
@@ -187,6 +187,12 @@ class Oracle:
         ce = self.w.check_env if check_env is None else check_env
         return self._run(JOB_MINCLR_PRIO if priority else JOB_MINCLR, idx, np.zeros(len(idx), np.float64), ce,
                          stop_below, threads)
+
+    def ffc_below(self, bound, idx=None, threads=1):
+        """First (t, i, j) in Alg. 2's order whose pair clearance is below
+        `bound` ((-1, -1, -1) if none); bound 0 is FFC itself."""
+        idx = self._idx(idx)
+        return self._run(JOB_FFC_BELOW, idx, np.zeros((len(idx), 3), np.int32), param=bound, threads=threads)
 
     def ffc_decidable(self, idx=None, margin=1e-4, threads=1):
         idx = self._idx(idx)

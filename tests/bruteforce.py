@@ -78,12 +78,14 @@ class Geometry:
             self._c[key] = O.fk(self.models[i], config(self.w, self.q, self.slots[i], t, self.T))
         return self._c[key]
 
-    def pair_hit(self, t, i, j):
+    def pair_hit(self, t, i, j, bound=0.0):
+        """Some sphere pair of robots i and j at state t has clearance below
+        `bound` (0: they collide)."""
         ci, cj = self.centers(t, i), self.centers(t, j)
         ri = self.models[i].sphere_xyzr[:, 3].astype(np.float64)
         rj = self.models[j].sphere_xyzr[:, 3].astype(np.float64)
         d = np.linalg.norm(ci[:, None, :] - cj[None, :, :], axis=2) - ri[:, None] - rj[None, :]
-        return bool((d < 0).any())
+        return bool((d < bound).any())
 
     def env_hit(self, t, i):
         c = self.centers(t, i)
@@ -184,10 +186,12 @@ def ffc_alg2(g: Geometry, W: int):
     return (-1, -1, -1)
 
 
-def all_conflicts(g: Geometry):
-    """Every colliding (t, i, j), exhaustive."""
+def all_conflicts(g: Geometry, bound=0.0):
+    """Every colliding (t, i, j), exhaustive; with a bound, every (t, i, j)
+    whose pair clearance is below it."""
     n = len(g.slots)
-    return [(t, i, j) for t in range(g.T + 1) for i in range(n) for j in range(i + 1, n) if g.pair_hit(t, i, j)]
+    return [(t, i, j) for t in range(g.T + 1) for i in range(n) for j in range(i + 1, n)
+            if g.pair_hit(t, i, j, bound)]
 
 
 def any_env(g: Geometry):

@@ -48,6 +48,8 @@ MUTANTS = {
     "cyl_axis_unnormalised": ("for (int k = 0; k < 3; ++k) u[k] /= L;", "for (int k = 0; k < 3; ++k) u[k] /= 1.0;"),
     "cyl_radius_dropped": ("const double ed = d > rho ? d - rho : 0.0;", "const double ed = d;"),
     "cyl_ignored_in_mv": ("      for (int o = 0; o < e->n_cylinders; ++o) {", "      for (int o = 0; o < 0; ++o) {"),
+    "ffc_below_bound_ignored": ("if (pair_min(&qs, i, j) < bound) {", "if (pair_min(&qs, i, j) < 0.0) {"),
+    "ffc_below_bound_sign": ("if (pair_min(&qs, i, j) < bound) {", "if (pair_min(&qs, i, j) < -bound) {"),
 }
 
 PIN_ARGS = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",

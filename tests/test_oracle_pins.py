@@ -14,6 +14,10 @@
   permutation, motion reversal, padding = holding the last configuration,
   obstacles do not change FFC, MV without environment is false exactly when
   FFC finds a conflict.
+* The first conflict deeper than a bound (what an undecidable FFC answer
+  must not pass over): exhaustive enumeration below the bound, the
+  closed-form discs with the contact distance moved by the bound, and FFC of
+  the same robots with every radius shrunk by half the margin.
 """
 from __future__ import annotations
 
@@ -379,6 +383,59 @@ def test_decidability_and_clearance_consistency():
                 break
         exp = all(v > 1e-4 for v in vals[:-1]) and (vals[-1] < -1e-4 if ffc[q][0] >= 0 else (not vals or vals[-1] > 1e-4))
         assert bool(dec[q]) == bool(exp)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_ffc_below_bruteforce(seed):
+    """The first pair deeper than a bound (the test of undecidable FFC answers)
+    against exhaustive enumeration of every (t, i, j) below the bound; bound 0
+    is FFC itself, and a lower bound never comes earlier."""
+    w = tiny_workload(450 + seed, n_queries=10, timed=bool(seed & 1), max_robots=4)
+    o = O.Oracle(w)
+    ffc = o.ffc()
+    res = {b: o.ffc_below(b) for b in (0.03, 0.0, -1e-4, -0.02, -0.08)}
+    np.testing.assert_array_equal(res[0.0], ffc)
+    for q in range(w.batch.n_queries):
+        g = BF.Geometry(w, q)
+        for b, r in res.items():
+            conf = BF.all_conflicts(g, b)
+            assert tuple(r[q]) == (min(conf) if conf else (-1, -1, -1))
+        keys = [tuple(res[b][q]) if res[b][q][0] >= 0 else (math.inf,) for b in (0.03, 0.0, -1e-4, -0.02, -0.08)]
+        assert keys == sorted(keys)
+
+
+def test_ffc_below_closed_form_discs():
+    """Two linearly moving discs of radius 0.25: the pair clearance is below b
+    exactly when the centers are closer than 0.5 + b, so the first such state
+    is the closed-form first conflict with R = 0.5 + b."""
+    rng = np.random.default_rng(17)
+    checked = 0
+    for _ in range(300):
+        s0, g0, s1, g1 = (rng.uniform(0, 4, 2).astype(np.float32) for _ in range(4))
+        T = int(rng.integers(5, 120))
+        b = float(rng.choice([-0.1, -1e-4, 0.05]))
+        first, near, _, _ = _disc_closed_form(s0, g0, s1, g1, T, 0.5 + b)
+        if near < 1e-6:
+            continue
+        f = O.Oracle(_disc_query(s0, g0, s1, g1, T=T)).ffc_below(b)[0]
+        assert f[0] == first
+        if first >= 0:
+            assert tuple(f[1:]) == (0, 1)
+        checked += 1
+    assert checked > 250
+
+
+def test_ffc_below_equals_ffc_of_shrunk_spheres():
+    """Clearance below -m is a collision of the same spheres with every
+    radius reduced by m/2: the first deep conflict is FFC of the shrunk
+    robots."""
+    m = 0.04
+    w = tiny_workload(470, n_queries=16, timed=True, max_robots=4)
+    shrunk = copy.deepcopy(w)
+    for mdl in shrunk.models:
+        mdl.sphere_xyzr[:, 3] = (mdl.sphere_xyzr[:, 3].astype(np.float64) - m / 2).astype(np.float32)
+    assert all(float(mdl.sphere_xyzr[:, 3].min()) > 0 for mdl in shrunk.models)
+    np.testing.assert_array_equal(O.Oracle(w).ffc_below(-m), O.Oracle(shrunk).ffc())
 
 
 def test_ffc_tie_is_lexicographic():
