@@ -4,7 +4,7 @@ instance; these tests cover random teams of 9-16 robots through every code
 path and flag, batches mixing both kernel instances, FFC keys naming pairs
 past index 31, a few robots whose sphere count alone exceeds the team
 layout, 16 discs (one lane per state), and the floor- and ceiling-mounted
-16-arm team in the cylinder cage at small and at full size (sampled)."""
+16-arm team in the cylinder cage at small and at full size."""
 from __future__ import annotations
 
 import dataclasses
@@ -172,16 +172,21 @@ def test_cage16_small(ctx):
 
 
 def test_cage16_full_10k(ctx):
-    """The benchmark's size and launch (device batch), sampled against the oracle."""
+    """The benchmark's sizes and launches (device batches): all 10,000 MV
+    edges and 2,000 of the 10,000 FFC motions (a seeded sample; each costs
+    the oracle about 120 robot pairs x 4,096 sphere pairs per state) against
+    the oracle."""
     w = W.make_cage16_mv(10000)
     o = O.Oracle(w)
     ba = ctx.bind(w).to("cuda")
     v = _np(ctx.mv_validate(ba))
-    PA.check_mv(o, v, idx=PA.sample(w.batch.n_queries, 300, seed=9))
+    n, _ = PA.check_mv(o, v)
+    assert n == 10000
     wf = W.make_cage16_ffc(10000)
     of = O.Oracle(wf)
     c = _np(ctx.ffc_find(ctx.bind(wf).to("cuda")))
-    PA.check_ffc(of, c, idx=PA.sample(wf.batch.n_queries, 300, seed=10))
+    n, _ = PA.check_ffc(of, c, idx=PA.sample(wf.batch.n_queries, 2000, seed=10))
+    assert n == 2000
 
 
 def test_clearance_diagnostic_sixteen_arms(ctx):
