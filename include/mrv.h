@@ -237,11 +237,13 @@ int mrv_run(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out, mrv_confli
  * batch and valid_out; at most MRV_NOALLOC_MAX_QUERIES queries and
  * MRV_NOALLOC_MAX_WAYPOINTS waypoints (MRV_ERR_LIMIT beyond); MRV_ASYNC,
  * MRV_EXHAUSTIVE and MRV_PER_QUERY_LAUNCH are rejected (MRV_ERR_ARG).  The
- * first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  All calls on a
- * device share the array: each call resets what must start from zero, and
- * calls whose work overlaps on the device race, so issue them on one stream
- * or synchronize between them.  Returns after valid_out is written. */
+ * array's device address is looked up on every call (the lookup allocates
+ * nothing).  The call waits for its result, so it must not be called while
+ * the context's stream is being captured into a CUDA graph (MRV_ERR_ARG).
+ * All calls on a device share the array: each call resets what must start
+ * from zero, and calls whose work overlaps on the device race, so issue them
+ * on one stream or synchronize between them.  Returns after valid_out is
+ * written; mrv_get_stats then describes this call. */
 #define MRV_NOALLOC_MAX_QUERIES 4096
 #define MRV_NOALLOC_MAX_WAYPOINTS 65536
 int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out);
@@ -285,6 +287,16 @@ typedef struct {
   uint64_t fk_chains;        /* (state, robot) kinematic chains evaluated     */
   uint64_t spheres_placed;   /* sphere centers computed (states x spheres)    */
   uint64_t cylinder_tests;   /* the sphere-cylinder part of sphere_tests      */
+  /* The method's own work on the states checked (each state once): what a
+   * dense check of those states performs, whatever the broadphase skipped.
+   * It is the numerator of the FP32 roofline of a call. */
+  uint64_t method_sphere_tests;   /* robot-robot, obstacle-sphere and self
+                                     sphere pairs                             */
+  uint64_t method_box_tests;      /* sphere-box pairs                         */
+  uint64_t method_cylinder_tests; /* sphere-cylinder pairs                    */
+  uint64_t method_joints;         /* joints of the kinematic-chain robots     */
+  uint64_t method_chains;         /* kinematic chains (one per robot, state)  */
+  uint64_t method_spheres;        /* sphere placements                        */
 } mrv_stats;
 int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
 

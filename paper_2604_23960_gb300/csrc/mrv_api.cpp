@@ -377,6 +377,12 @@ int mrv_ctx::sync() {
   stats.fk_chains = h_stats[6];
   stats.spheres_placed = h_stats[7];
   stats.cylinder_tests = h_stats[8];
+  stats.method_sphere_tests = h_stats[9];
+  stats.method_box_tests = h_stats[10];
+  stats.method_cylinder_tests = h_stats[11];
+  stats.method_joints = h_stats[12];
+  stats.method_chains = h_stats[13];
+  stats.method_spheres = h_stats[14];
   stats.n_valid = h_counts[0];
   stats.n_conflicts = h_counts[1];
   float ms = 0.f;
@@ -541,6 +547,8 @@ int mrv_create(mrv_ctx **out, int device, void *cuda_stream) {
     delete c;
     return cuda_fail(e, "context resources");
   }
+  // pinned host words: status at 0, statistics at 64, counts at 256
+  static_assert(64 + sizeof(unsigned long long) * kNumStats <= 256, "statistics fit before the counts");
   c->h_status = (uint32_t *)c->h_pinned;
   c->h_stats = (unsigned long long *)((char *)c->h_pinned + 64);
   c->h_counts = (int32_t *)((char *)c->h_pinned + 256);

@@ -27,7 +27,7 @@ constexpr int kFkChains = 8;          // (state, robot) chains per FK round
 constexpr int kTeamRobots = 8;
 constexpr int kTeamSpheres = 512;
 constexpr int kLevelBins = 2 * (kMaxLevels + 1);
-constexpr int kNumStats = 9;          // statistics counters of a call (see mrv_stats)
+constexpr int kNumStats = 15;         // statistics counters of a call (see mrv_stats)
 
 // device error bits (BatchDev::err)
 enum : uint32_t {
@@ -117,6 +117,8 @@ struct QueryDev {
                       // bit 3: work class 1 (more than kTeamRobots robots or kTeamSpheres spheres)
   float rho2;         // largest squared sphere radius of the query's robots
   int32_t nadj;       // pairs-first MV: adjacent robot pairs (0: the order is off)
+  int32_t nchain;     // robots that are kinematic chains (one FK chain per state each)
+  int32_t njoint;     // joints summed over those robots
   uint32_t adj[4];    // pairs-first MV: bit p = pair p (in (i, j) order) is adjacent
   long long adjtests;   // pairs-first MV: sphere tests per state of the adjacent pairs
   long long pairtests;  // robot-robot sphere tests per state
@@ -159,7 +161,14 @@ struct BatchDev {
   unsigned long long *stats;         // [0] states checked, [1] tests executed,
                                      // [2] states available, [3] tests available,
                                      // [4] items, [5] box tests executed,
-                                     // [6] FK chains, [7] spheres placed
+                                     // [6] FK chains, [7] spheres placed,
+                                     // [8] cylinder tests executed; the
+                                     // method's dense work of the states
+                                     // checked: [9] sphere-sphere tests
+                                     // (robot-robot, obstacle spheres, self
+                                     // pairs), [10] box tests, [11] cylinder
+                                     // tests, [12] joints, [13] chains,
+                                     // [14] sphere placements
   // tables
   const ModelDev *models;
   int32_t n_models;

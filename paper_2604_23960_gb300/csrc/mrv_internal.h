@@ -161,4 +161,7 @@ int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st);
 int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr, mrv_conflict *conf);
 int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls);
 int check_device_err(uint32_t err);
+// copies the error word, statistics and counts of the call just enqueued to
+// the context's pinned host words; waits for them unless async
+int finish_call(mrv_ctx *ctx, Scratch &S, bool async);
 }  // namespace mrv

@@ -266,6 +266,7 @@ __global__ void k_prep(BatchDev B) {
   uint32_t err = 0;
   QueryDev Q;
   Q.T = 0; Q.n = 0; Q.M = 0; Q.ntiles = 0; Q.split = 1; Q.spt = kWarp; Q.nslices = 0; Q.nphase = 1;
+  Q.nchain = 0; Q.njoint = 0;
   Q.nchunks = 0; Q.cte = 1; Q.env = -1; Q.bits = 0; Q.rho2 = 0.f; Q.nadj = 0;
   Q.adj[0] = Q.adj[1] = Q.adj[2] = Q.adj[3] = 0u; Q.adjtests = 0;
   Q.pairtests = 0; Q.envtests = 0; Q.boxtests = 0; Q.cyltests = 0;
@@ -299,7 +300,11 @@ __global__ void k_prep(BatchDev B) {
       self_total += m.n_self;
       if (i == 0) self0 = m.n_self;
       rho2 = fmaxf(rho2, m.r2max);
-      if (m.kind != MRV_ROBOT_POINT) all_point = false;
+      if (m.kind != MRV_ROBOT_POINT) {
+        all_point = false;
+        Q.nchain += 1;
+        Q.njoint += m.dof;
+      }
       const int w0 = B.slot_wp_off[s], w1 = B.slot_wp_off[s + 1];
       if (w0 < 0 || w1 <= w0 || w1 > B.n_waypoints) { err |= kErrWaypoints; break; }
       long long Ts = 0;
@@ -2220,6 +2225,24 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   }
   __syncwarp();
   if (lane == 0) {
+    // the method's dense work of the states this item checked (each state
+    // counts once, in its first phase): every test and placement of the
+    // query's flavor, whatever the broadphase skipped
+    const unsigned long long s = C.states;
+    if (s) {
+      const QueryDev *Qd = B.q + q;   // read again here: not held in registers over the item
+      const unsigned long long bt = (unsigned long long)__ldg(&Qd->boxtests);
+      const unsigned long long ct = (unsigned long long)__ldg(&Qd->cyltests);
+      const int nch = __ldg(&Qd->nchain);
+      atomicAdd(&B.stats[9], s * (unsigned long long)(__ldg(&Qd->pairtests) + __ldg(&Qd->envtests)));
+      if (bt) atomicAdd(&B.stats[10], s * bt);
+      if (ct) atomicAdd(&B.stats[11], s * ct);
+      if (nch) {
+        atomicAdd(&B.stats[12], s * (unsigned long long)__ldg(&Qd->njoint));
+        atomicAdd(&B.stats[13], s * (unsigned long long)nch);
+      }
+      atomicAdd(&B.stats[14], s * (unsigned long long)__ldg(&Qd->M));
+    }
     atomicAdd(&B.stats[0], C.states);
     atomicAdd(&B.stats[1], C.tests);
     atomicAdd(&B.stats[5], C.btests);
@@ -2270,11 +2293,14 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_items) break;
+    // a warp whose clock budget runs out raises the abort flag, so every
+    // other warp stops at its next claim instead of at its own budget
     int halt = 0;
     if (lane == 0) {
       if (aborted) halt = 1;
       else if (B.clock_budget > 0 && clock64() - t_start > B.clock_budget) halt = 2;
       if (halt) atomicOr(B.err, halt == 1 ? kErrAbort : kErrTimeout);
+      if (halt == 2) atomicExch(&B.counters[2], 1);
     }
     if (__shfl_sync(0xffffffffu, halt, 0)) break;
     const int idx = base + lane;

@@ -18,7 +18,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "mrv_internal.h"
 
@@ -37,22 +36,15 @@ constexpr size_t kBytes =
 
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices];   // device address of g_scratch, per device
-
 // The address of g_scratch on the current device (host code cannot use the
-// symbol itself as a device pointer).  Looked up once per device.
-int scratch_address(int device, void **out) {
-  if (device < 0 || device >= kMaxDevices) return fail(MRV_ERR_ARG, "device %d outside 0..%d", device, kMaxDevices - 1);
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[device]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "scratch symbol address");
-    g_scratch_addr[device] = p;
-  }
-  *out = g_scratch_addr[device];
+// symbol itself as a device pointer).  Looked up on every call: the lookup
+// allocates nothing, and a cached address would go stale if the device's
+// primary context were ever recreated (cudaDeviceReset).
+int scratch_address(void **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch symbol address");
+  *out = p;
   return MRV_OK;
 }
 
@@ -107,16 +99,21 @@ extern "C" int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *b, uint8_t *va
   if (ctx->pending && (rc = ctx->sync())) return rc;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  // the call waits for its result, which a stream under capture cannot do
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(ctx->stream, &cs)) != cudaSuccess) return cuda_fail(e, "capture status");
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(MRV_ERR_ARG, "mv_validate_noalloc cannot run on a stream that is being captured");
   void *base = nullptr;
-  if ((rc = scratch_address(ctx->device, &base))) return rc;
+  if ((rc = scratch_address(&base))) return rc;
   Scratch S;   // a view only: it owns nothing (base stays null)
   carve(base, b->n_queries, b->n_waypoints, &S);
   const BatchDev B = make_batchdev(ctx, b, S, MRV_KIND_MV, ctx->tuning.slices_per_item);
-  if ((rc = enqueue_run_on(ctx, B, S, false, valid_out, nullptr, nullptr, ctx->stream, nullptr, nullptr, &ctx->fork)))
+  if ((rc = enqueue_run_on(ctx, B, S, false, valid_out, nullptr, nullptr, ctx->stream, ctx->ev0, ctx->ev1,
+                           &ctx->fork)))
     return rc;
-  // the error word comes back through the context's pinned status word
-  e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "mv_validate_noalloc");
-  return check_device_err(ctx->h_status[0]);
+  // error word, statistics and counts come back through the context's pinned
+  // host words, as for every other call (mrv_get_stats then describes this one)
+  ctx->timed_pending = true;
+  return finish_call(ctx, S, false);
 }

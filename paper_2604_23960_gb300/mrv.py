@@ -73,7 +73,10 @@ class Stats(C.Structure):
     _fields_ = [("states_available", C.c_uint64), ("states_checked", C.c_uint64), ("sphere_tests", C.c_uint64),
                 ("sphere_tests_available", C.c_uint64), ("work_items", C.c_uint64), ("n_valid", C.c_int32),
                 ("n_conflicts", C.c_int32), ("device_ms", C.c_float), ("box_tests", C.c_uint64),
-                ("fk_chains", C.c_uint64), ("spheres_placed", C.c_uint64), ("cylinder_tests", C.c_uint64)]
+                ("fk_chains", C.c_uint64), ("spheres_placed", C.c_uint64), ("cylinder_tests", C.c_uint64),
+                ("method_sphere_tests", C.c_uint64), ("method_box_tests", C.c_uint64),
+                ("method_cylinder_tests", C.c_uint64), ("method_joints", C.c_uint64),
+                ("method_chains", C.c_uint64), ("method_spheres", C.c_uint64)]
 
 
 class Tuning(C.Structure):

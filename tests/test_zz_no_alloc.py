@@ -11,6 +11,9 @@ every other test.
 """
 from __future__ import annotations
 
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -37,6 +40,35 @@ def test_noalloc_matches_mv_validate_twice():
         ref, got = _ref_and_noalloc(ctx, ba)
         np.testing.assert_array_equal(got, ref)
     ctx.close()
+
+
+def test_noalloc_allocates_nothing():
+    """On a fresh context (its scratch arena never allocated), the library's
+    next device allocation is made to fail; the allocation-free call still
+    succeeds, and the mv_validate after it fails with MRV_ERR_OOM, which
+    shows the injected failure was still armed during the first call.  The
+    statistics then describe the allocation-free call."""
+    import torch
+    ctx = mrv.Context(0)
+    try:
+        ba = ctx.bind(W.make_cage_mv(800, query_seed=614)).to("cuda")   # uploads allocate here
+        out = torch.full((ba.n_queries,), 7, dtype=torch.uint8, device="cuda")
+        os.environ["MRV_FAULT_INJECT_ALLOC"] = f"noalloc-{os.getpid()}-{time.monotonic_ns()}"
+        try:
+            mrv.mv_validate_noalloc(ctx.h, ba.struct(mrv.MRV_CHECK_ENV), out)
+            st = ctx.stats()
+            with pytest.raises(mrv.MrvError) as e:
+                ctx.mv_validate(ba)
+            assert e.value.code == -2
+        finally:
+            del os.environ["MRV_FAULT_INJECT_ALLOC"]
+        ref = ctx.mv_validate(ba).cpu().numpy()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
+        assert st["n_valid"] == int(ref.sum())
+        assert 0 < st["states_checked"] <= st["states_available"]
+        assert st["work_items"] > 0
+    finally:
+        ctx.close()
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
