@@ -1,11 +1,16 @@
-"""Benchmark: MV motion-checks/s on 4 Panda-like arms in the cage (10k
-composite joint-space motions, resolution 1/32 rad), one GB300.
+"""Benchmark: MV/FFC motion-checks/s on the heterogeneous ragged batch, one GB300.
 
-A step is one MotionValidation pass over the whole 10k-motion batch with
-inputs resident in HBM: counter reset, preparation kernels, the persistent
-work-stealing kernel and the result kernel, replayed from one CUDA graph.
-L2 is flushed (a 512 MB write) before every timed step; each step is timed
-with CUDA events on the launching stream.  Rank 0 prints one JSON line.
+The headline workload is 1,000,000 mixed MV/FFC queries (teams of 2 arms plus
+0-6 discs in the box world, 8-512 steps per query, half MV and half FFC) run
+as one persistent work-stealing launch replayed from a CUDA graph, with the
+scheduler tuning picked by the library's autotuner.  A step is one pass over
+the whole batch with inputs resident in HBM: counter reset, preparation
+kernels, the persistent kernel instances and the result kernel.  L2 is
+flushed (a 512 MB write) before every timed step; each step is timed with
+CUDA events on the launching stream.  The other workloads (the 4-arm cage
+MV and FFC batches, discs, the 8- and 16-arm cages, prioritized edges) and the
+request server are reported under their own keys.  Rank 0 prints one JSON
+line.
 
 --impl reference times the FP64 oracle on the host cores instead (the
 reference arm for this workload: the paper ships no code).
@@ -29,13 +34,19 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "MV/FFC motion-checks/s vs per-query launch; p50/p99 latency, 1 GB300"
-WORKLOAD = "cage_mv: MV, 4 Panda-like 7-DOF arms x 64 spheres, cage env 40 spheres + 12 boxes, " \
-           "10k start/goal joint-space motions, resolution 1/32 rad"
+WORKLOAD = "ragged_teams_1m: 1M mixed MV/FFC queries (1/2 each) in one persistent CUDA-graph launch; teams of " \
+           "2 Panda-like 7-DOF arms x 64 spheres + 0-6 discs (2-8 robots), box world with 20 boxes, one segment " \
+           "per robot, 8-512 steps per query (log-uniform)"
+CAGE_WORKLOAD = "cage_mv: MV, 4 Panda-like 7-DOF arms x 64 spheres, cage env 40 spheres + 12 boxes, " \
+                "10k start/goal joint-space motions, resolution 1/32 rad"
 # FP32 flops per unit of work the kernel counts (FMA = 2):
 FLOPS_PER_TEST = 10     # sphere-sphere test: 3 sub, 1 mul + 2 fma, radius add + square
 FLOPS_PER_BOX = 13      # sphere-box test: per axis clamp + sub + fma, radius square
 FLOPS_PER_CHAIN = 390   # 7-joint modified-DH chain + flange: 48 per joint, 54 for the flange
+FLOPS_PER_JOINT = 48    # one modified-DH joint of a chain (sin/cos, row mixing, position update)
+FLOPS_PER_FLANGE = 54   # the fixed flange transform at the end of a chain
 FLOPS_PER_SPHERE = 28   # sphere placement: 3x4 transform, shift, |p|^2 - r^2
+FLOPS_PER_CYL = 32      # sphere-cylinder test: axial coordinate, radial distance, clamps, compare
 
 
 def dense_flops_per_state(w):
@@ -63,13 +74,30 @@ def work_flops(st):
     box = st["box_tests"]
     return (FLOPS_PER_TEST * (st["sphere_tests"] - box) + FLOPS_PER_BOX * box
             + FLOPS_PER_CHAIN * st["fk_chains"] + FLOPS_PER_SPHERE * st["spheres_placed"])
+
+
+def method_flops(st):
+    """FP32 flops of the method's dense work on the states a call checked
+    (every robot-robot, obstacle and self test of each checked state, its FK
+    chains and sphere placements, for each query's own team and obstacles),
+    from the kernel's counters of that work: the ALU roofline's numerator."""
+    return (FLOPS_PER_TEST * st["method_sphere_tests"] + FLOPS_PER_BOX * st["method_box_tests"]
+            + FLOPS_PER_CYL * st["method_cylinder_tests"] + FLOPS_PER_JOINT * st["method_joints"]
+            + FLOPS_PER_FLANGE * st["method_chains"] + FLOPS_PER_SPHERE * st["method_spheres"])
+
+
+def roofline_frac(st, kernel_ms, peak):
+    """(achieved TFLOP/s of the method's work, fraction of the FP32 peak)."""
+    a = method_flops(st) / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else 0.0
+    return a, a / peak
+
+
 MAKERS = None
 
-# DRAM bytes of one k_main launch of the benchmark step, from an ncu capture
-# (profiles/k_main_cage_mv_traffic.md), valid for the kernel source it was
-# taken on; any other source reports null
-TRAFFIC = {"kernel_sha256": "3d39a3def4b8b006ac6484c46ac0dc9688806f6b7afaab6c94f7ace3b1afa74c",
-           "bytes": 4452352 + 7424}
+# DRAM bytes of one persistent-kernel launch of the headline step, from a
+# one-pass ncu capture of that launch; valid only for the kernel source it was
+# taken on (any other source reports null)
+TRAFFIC = {"kernel_sha256": None, "bytes": None}
 
 
 def traffic_per_launch():
@@ -235,6 +263,9 @@ def serving(ctx, duration_s=6.0, loads=(0.5, 0.8, 0.95), n_clients=64, seed=206)
     st = srv.stats()
     out["micro_batches"] = st["micro_batches"]
     out["max_inflight"] = st["max_inflight"]
+    out["device_budget_bytes"] = st["device_budget_bytes"]
+    out["device_free_bytes_after_sizing"] = st["device_free_bytes"]
+    out["presized_queries_per_micro_batch"] = st["presized_queries"]
     srv.close()
     return out
 
@@ -254,10 +285,12 @@ def autotune(ctx, w, flags, kind=None, n_sample=None):
     return t
 
 
-def other_configs(ctx, flush, per_query_n=1000, reps=3):
+def other_configs(ctx, flush, fp32_peak, per_query_n=1000, reps=3):
     """Throughput of the other workload configurations (device-resident
-    inputs, batched persistent launch; the ragged batch replays a CUDA graph)
-    next to one synchronous launch per query on a sample of the same batch."""
+    inputs, batched persistent launch) next to one synchronous launch per
+    query on a sample of the same batch; per configuration the persistent
+    kernel's time (CUDA events on its stream) and the FP32 roofline fraction
+    of the method's work on the states it checked."""
     import torch
     from paper_2604_23960_gb300 import mrv
     from paper_2604_23960_gb300 import workloads as W
@@ -266,7 +299,7 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
     def timed(fn):
         fn()
         torch.cuda.synchronize()
-        best = []
+        best, kms = [], []
         for _ in range(reps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -274,7 +307,8 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
             fn()
             torch.cuda.synchronize()
             best.append(time.perf_counter() - t0)
-        return statistics.median(best)
+            kms.append(ctx.stats()["device_ms"])
+        return statistics.median(best), statistics.median(kms), ctx.stats()
 
     def per_query(w, call):
         sub = W.subset(w, np.arange(min(per_query_n, w.batch.n_queries)))
@@ -286,98 +320,154 @@ def other_configs(ctx, flush, per_query_n=1000, reps=3):
         torch.cuda.synchronize()
         return sub.batch.n_queries / (time.perf_counter() - t0)
 
+    def entry(w, dt, kms, st, pq, **extra):
+        a, f = roofline_frac(st, kms, fp32_peak)
+        e = {"value": w.batch.n_queries / dt, "per_query_launch": pq, "speedup": w.batch.n_queries / dt / pq,
+             "ms": dt * 1e3, "kernel_ms": kms, "roofline_achieved_tflops": a, "roofline_frac": f,
+             "effort_states": st["states_checked"] / max(1, st["states_available"])}
+        e.update(extra)
+        return e
+
     # two discs in the box world, 1,000 queries: MV and FFC
     w = W.make_plain_discs(1000)
     ba = ctx.bind(w).to("cuda")
     for kind, call in (("mv", lambda b, f=0: ctx.mv_validate(b, flags=f)), ("ffc", lambda b, f=0: ctx.ffc_find(b, flags=f))):
-        dt = timed(lambda: call(ba))
+        dt, kms, st = timed(lambda: call(ba))
         pq = per_query(w, lambda b: call(b, mrv.MRV_PER_QUERY_LAUNCH))
-        out[f"discs_{kind}_1k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
-                                   "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3}
+        out[f"discs_{kind}_1k"] = entry(w, dt, kms, st, pq)
     # four arms, 100k timed path-sets: FFC
     w = W.make_cage_ffc(100000)
     ba = ctx.bind(w).to("cuda")
     tune = autotune(ctx, w, 0, kind=1, n_sample=20000)
-    dt = timed(lambda: ctx.ffc_find(ba))
-    st = ctx.stats()
+    dt, kms, st = timed(lambda: ctx.ffc_find(ba))
     pq = per_query(w, lambda b: ctx.ffc_find(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
-    out["cage_ffc_100k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
-                            "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
-                            "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                            "kernel_ms": st["device_ms"], "tuning": tune}
+    out["cage_ffc_100k"] = entry(w, dt, kms, st, pq, tuning=tune)
     # the Cage scenario's team (Sec. V-A): 4 floor- and 4 ceiling-mounted arms
     # among cylinder obstacles, 10k composite motions
     w = W.make_cage8_mv(10000)
     ba = ctx.bind(w).to("cuda")
     tune = autotune(ctx, w, mrv.MRV_CHECK_ENV, kind=0)
-    dt = timed(lambda: ctx.mv_validate(ba))
-    st = ctx.stats()
+    dt, kms, st = timed(lambda: ctx.mv_validate(ba))
     nvalid = int(ctx.mv_validate(ba).sum().item())
     pq = per_query(w, lambda b: ctx.mv_validate(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
-    out["cage8_cyl_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
-                            "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
-                            "valid_total": f"{nvalid}/{w.batch.n_queries}",
-                            "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                            "kernel_ms": st["device_ms"], "tuning": tune}
+    out["cage8_cyl_10k"] = entry(w, dt, kms, st, pq, tuning=tune, valid_total=f"{nvalid}/{w.batch.n_queries}")
     # the 16-arm Cage team (8 floor- and 8 ceiling-mounted arms, 1024 spheres
     # and 120 robot pairs per state: the large-team kernel): MV on 10k
     # planner-like edges of at most 0.5 rad, FFC on 10k whole motions
     w = W.make_cage16_mv(10000)
     ba = ctx.bind(w).to("cuda")
     tune = autotune(ctx, w, mrv.MRV_CHECK_ENV, kind=0)
-    dt = timed(lambda: ctx.mv_validate(ba))
-    st = ctx.stats()
+    dt, kms, st = timed(lambda: ctx.mv_validate(ba))
     nvalid = int(ctx.mv_validate(ba).sum().item())
     pq = per_query(w, lambda b: ctx.mv_validate(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
-    out["cage16_cyl_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
-                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
-                             "valid_total": f"{nvalid}/{w.batch.n_queries}",
-                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                             "kernel_ms": st["device_ms"], "tuning": tune,
-                             "order_study": order_study(ctx, ba, flush, linear=False)}
+    out["cage16_cyl_10k"] = entry(w, dt, kms, st, pq, tuning=tune, valid_total=f"{nvalid}/{w.batch.n_queries}",
+                                  order_study=order_study(ctx, ba, flush, linear=False))
     w = W.make_cage16_ffc(10000)
     ba = ctx.bind(w).to("cuda")
-    dt = timed(lambda: ctx.ffc_find(ba))
-    st = ctx.stats()
+    dt, kms, st = timed(lambda: ctx.ffc_find(ba))
     pq = per_query(w, lambda b: ctx.ffc_find(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
-    out["cage16_ffc_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
-                             "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
-                             "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                             "kernel_ms": st["device_ms"]}
+    out["cage16_ffc_10k"] = entry(w, dt, kms, st, pq)
     # prioritized planning's edge checks (Sec. IV-C): 10k cage edges, one arm
     # against the cage, itself and three higher-priority arms' timed paths
     w = W.make_cage_priority(10000)
     ba = ctx.bind(w).to("cuda")
     tune = autotune(ctx, w, mrv.MRV_CHECK_ENV | mrv.MRV_PRIORITY, kind=0)
-    dt = timed(lambda: ctx.mv_validate(ba, flags=mrv.MRV_PRIORITY))
-    st = ctx.stats()
+    dt, kms, st = timed(lambda: ctx.mv_validate(ba, flags=mrv.MRV_PRIORITY))
     nvalid = int(ctx.mv_validate(ba, flags=mrv.MRV_PRIORITY).sum().item())
     pq = per_query(w, lambda b: ctx.mv_validate(b, flags=mrv.MRV_PRIORITY | mrv.MRV_PER_QUERY_LAUNCH))
-    out["cage_priority_10k"] = {"value": w.batch.n_queries / dt, "per_query_launch": pq,
-                                "speedup": w.batch.n_queries / dt / pq, "ms": dt * 1e3,
-                                "valid_total": f"{nvalid}/{w.batch.n_queries}",
-                                "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                                "kernel_ms": st["device_ms"], "tuning": tune}
-    # ragged teams, 1M mixed MV/FFC queries in one persistent graph launch
-    w = W.make_ragged_teams(1_000_000)
-    ba = ctx.bind(w).to("cuda")
-    tune = autotune(ctx, w, mrv.MRV_CHECK_ENV, n_sample=100000)
+    out["cage_priority_10k"] = entry(w, dt, kms, st, pq, tuning=tune, valid_total=f"{nvalid}/{w.batch.n_queries}")
+    return out
+
+
+def cage_mv_config(ctx, flush, fp32_peak, stream, steps=20, per_query_n=2000):
+    """The 4-arm cage MV batch (10k motions): CUDA-graph replay with inputs in
+    HBM, the same through mv_validate with pinned host buffers, one launch
+    per query, the exhaustive passes (frame-level broadphase and dense) and
+    the effort of the state orders."""
+    import torch
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import workloads as W
+    w = W.make_cage_mv(10000)
+    ba_host = ctx.bind(w)
+    ba = ba_host.to("cuda")
     nq = w.batch.n_queries
+    ba.a["q_kind"] = torch.zeros(nq, dtype=torch.uint8, device="cuda")   # every query is MV
+    bs = ba.struct(mrv.MRV_CHECK_ENV, with_kind=True)
+    mrv.mrv_autotune(ctx.h, bs)
+    tune = mrv.mrv_get_tuning(ctx.h)
     valid = torch.empty(nq, dtype=torch.uint8, device="cuda")
     conf = torch.empty((nq, 3), dtype=torch.int32, device="cuda")
-    g = mrv.mrv_graph_create(ctx.h, ba.struct(mrv.MRV_CHECK_ENV, with_kind=True), valid, conf)
-
-    def replay():
-        mrv.mrv_graph_launch(g)
+    graph = mrv.mrv_graph_create(ctx.h, bs, valid, conf)
+    for _ in range(3):
+        mrv.mrv_graph_launch(graph)
         ctx.sync()
-    dt = timed(replay)
+    step_ms, kern_ms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mrv.mrv_graph_launch(graph)
+        e1.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(ctx.stats()["device_ms"])
     st = ctx.stats()
-    mrv.mrv_graph_destroy(g)
-    pq = per_query(w, lambda b: ctx.run(b, flags=mrv.MRV_PER_QUERY_LAUNCH))
-    out["ragged_teams_1m"] = {"value": nq / dt, "per_query_launch": pq, "speedup": nq / dt / pq, "ms": dt * 1e3,
-                              "effort_states": st["states_checked"] / max(1, st["states_available"]),
-                              "kernel_ms": st["device_ms"], "tuning": tune}
-    return out
+    mrv.mrv_graph_destroy(graph)
+    nvalid = int(valid.sum().item())
+    kms = statistics.mean(kern_ms)
+    per_state = dense_flops_per_state(w)
+    ach, frac = roofline_frac(st, kms, fp32_peak)
+    # end to end with pinned host buffers through mv_validate
+    bh = ba_host.to("cpu", pin=True)
+    out_h = torch.empty(nq, dtype=torch.uint8).pin_memory()
+    e2e = []
+    for i in range(6):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mrv.mv_validate(ctx.h, bh.struct(mrv.MRV_CHECK_ENV), out_h, None)
+        e2e.append(time.perf_counter() - t0)
+    assert int(out_h.sum()) == nvalid
+    # one synchronous launch per query
+    pq_n = min(nq, per_query_n)
+    bsub = ctx.bind(W.subset(w, np.arange(pq_n)), ctx.robot_ids, ctx.env_ids).to("cuda")
+    ctx.mv_validate(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pq_valid = ctx.mv_validate(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
+    torch.cuda.synchronize()
+    pq_rate = pq_n / (time.perf_counter() - t0)
+    assert torch.equal(pq_valid, valid[:pq_n])
+    # exhaustive passes: with the frame-level broadphase and testing every
+    # sphere pair (the dense, ALU-bound regime)
+    ex = {}
+    for name, flags in (("broadphase", 0), ("dense", mrv.MRV_NO_BROADPHASE)):
+        ctx.mv_validate(ba, exhaustive=True, flags=flags)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            ctx.mv_validate(ba, exhaustive=True, flags=flags)
+            ms.append(ctx.stats()["device_ms"])
+        est = ctx.stats()
+        m = statistics.median(ms)
+        a, f = roofline_frac(est, m, fp32_peak)
+        ex[name] = {"kernel_ms": m, "achieved": a, "frac": f, "performed": work_flops(est) / (m / 1e3) / 1e12,
+                    "sphere_tests": est["sphere_tests"], "fk_chains": est["fk_chains"]}
+    return {"workload": CAGE_WORKLOAD, "value": nq / (statistics.mean(step_ms) / 1e3), "unit": "motion-checks/s",
+            "ms_per_step": statistics.mean(step_ms), "kernel_ms": kms, "tuning": tune,
+            "valid_total": f"{nvalid}/{nq}",
+            "roofline_achieved_tflops": ach, "roofline_frac": frac,
+            "flops_per_state": per_state,
+            "performed_tflops": work_flops(st) / (kms / 1e3) / 1e12,
+            "effort": {"states": st["states_checked"] / max(1, st["states_available"]),
+                       "sphere_tests_vs_dense": st["sphere_tests"] / max(1, st["sphere_tests_available"])},
+            "e2e": {"value": nq / statistics.median(e2e), "unit": "motion-checks/s",
+                    "api": "mv_validate with pinned host buffers"},
+            "per_query_launch": {"value": pq_rate, "queries": pq_n,
+                                 "speedup_batched": nq / (statistics.mean(step_ms) / 1e3) / pq_rate},
+            "roofline_exhaustive": ex,
+            "order_study": order_study(ctx, ba, flush)}
 
 
 def order_study(ctx, ba, flush, reps=3, linear=True):
@@ -462,32 +552,44 @@ def validation_study(ctx, flush, n_queries=500, reps=3):
     return out
 
 
+def _oracle_mixed(o, kind, idx, threads):
+    """The oracle on queries idx of a mixed batch: MV (Alg. 1) where kind is
+    0, FFC (Alg. 2) where it is 1."""
+    idx = np.asarray(idx)
+    k = kind[idx]
+    if (k == 0).any():
+        o.mv(idx[k == 0], threads=threads)
+    if (k == 1).any():
+        o.ffc(idx[k == 1], threads=threads)
+
+
 def cpu_baseline(w, seconds_hint: float = 20.0):
-    """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample
+    (the first queries of the batch, MV or FFC by their kind)."""
     from oracle import oracle as O
     o = O.Oracle(w)
+    kind = w.batch.q_kind if w.batch.q_kind is not None else np.zeros(w.batch.n_queries, np.uint8)
     threads = os.cpu_count() or 1
     n = w.batch.n_queries
-    idx = np.arange(min(n, 256))
+    idx = np.arange(min(n, 512))
     t0 = time.perf_counter()
-    o.mv(idx, threads=threads)
-    dt = time.perf_counter() - t0
-    per_q = dt / len(idx)
+    _oracle_mixed(o, kind, idx, threads)
+    per_q = (time.perf_counter() - t0) / len(idx)
     k = int(min(n, max(len(idx), seconds_hint / max(per_q, 1e-9))))
-    idx = np.arange(k)
     t0 = time.perf_counter()
-    o.mv(idx, threads=threads)
+    _oracle_mixed(o, kind, np.arange(k), threads)
     dt = time.perf_counter() - t0
     # one core on a fixed subset of about a fifth of that time
     k1 = int(min(n, max(64, 0.2 * seconds_hint / max(per_q * threads, 1e-9))))
     t1 = time.perf_counter()
-    o.mv(np.arange(k1), threads=1)
+    _oracle_mixed(o, kind, np.arange(k1), 1)
     dt1 = time.perf_counter() - t1
     return {"value": k / dt, "unit": "motion-checks/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {k} of the {n} motions, FP64 scalar MV with early exit, {threads} threads",
+            "sample": f"first {k} of the {n} queries (MV or FFC by kind), FP64 scalar with early exit, "
+                      f"{threads} threads",
             "cpu": _cpu_model(),
             "single_core": {"value": k1 / dt1, "unit": "motion-checks/s", "cores": 1,
-                            "sample": f"first {k1} of the {n} motions, one thread"}}
+                            "sample": f"first {k1} of the {n} queries, one thread"}}
 
 
 def _cpu_model() -> str:
@@ -512,26 +614,66 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_2604_23960_gb300 import workloads as W
-    w = W.make_cage_mv(10000)
+    w = W.make_ragged_teams(args.queries)
     o = O.Oracle(w)
+    kind = w.batch.q_kind
     threads = os.cpu_count() or 1
     sample = args.ref_sample
-    rng_idx = [np.arange(s * sample, (s + 1) * sample) % w.batch.n_queries for s in range(args.warmup + args.steps)]
+    n = w.batch.n_queries
+    rng_idx = [np.arange(s * sample, (s + 1) * sample) % n for s in range(args.warmup + args.steps)]
     for s in range(args.warmup):
-        o.mv(rng_idx[s], threads=threads)
+        _oracle_mixed(o, kind, rng_idx[s], threads)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        o.mv(rng_idx[args.warmup + s], threads=threads)
+        _oracle_mixed(o, kind, rng_idx[args.warmup + s], threads)
     dt = time.perf_counter() - t0
     v = sample * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "motion-checks/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": f"{sample} motions of the 10k batch per step"},
+            "config": {"workload": WORKLOAD,
+                       "step": f"{sample} consecutive queries of the {n}-query batch per step (MV or FFC by kind)"},
             "cpu_baseline": {"value": v, "unit": "motion-checks/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{sample} motions per step"},
+                             "sample": f"{sample} queries per step, FP64 scalar oracle with early exit, "
+                                       f"{threads} threads, {_cpu_model()}"},
             "e2e": {"value": v, "unit": "motion-checks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def strong_scaling(ctx, n_queries, world, rank, group, flush, reps=3):
+    """One batch split across the ranks by estimated cost (multi.shard_by_cost),
+    each rank validating its shard with mrv_run on its own GPU, results
+    gathered on rank 0 over a host (gloo) group; the time is the slowest
+    rank's, between barriers."""
+    import torch
+    import torch.distributed as dist
+    from paper_2604_23960_gb300 import mrv
+    from paper_2604_23960_gb300 import multi
+    from paper_2604_23960_gb300 import workloads as W
+    w = W.make_ragged_teams(n_queries)
+    ba = ctx.bind(w)
+    mine = multi.shard_of(ba, world, rank)
+    sh = multi.take_queries(ba, mine).to("cuda")
+    ts = []
+    for _ in range(reps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier(group=group)
+        t0 = time.perf_counter()
+        v, c = ctx.run(sh)
+        torch.cuda.synchronize()
+        t = torch.tensor([time.perf_counter() - t0], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+        ts.append(float(t.item()))
+    full_v = multi.gather_results(mine, v.cpu().numpy(), n_queries, world, rank, group=group)
+    full_c = multi.gather_results(mine, c.cpu().numpy(), n_queries, world, rank, group=group)
+    if rank != 0:
+        return None
+    dt = statistics.median(ts[1:])
+    return {"value": n_queries / dt, "unit": "motion-checks/s", "ms": dt * 1e3, "n_gpus": world,
+            "queries": n_queries, "shard_sizes_by_cost": "LPT greedy on robot pairs x states",
+            "gathered": int(len(full_v) == n_queries and len(full_c) == n_queries), "_valid": full_v,
+            "_conf": full_c}
 
 
 def run(args):
@@ -541,44 +683,42 @@ def run(args):
     from paper_2604_23960_gb300 import workloads as W
 
     rank, world, local = _dist()
+    host_group = None
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        host_group = dist.new_group(backend="gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     ctx = mrv.Context(local, stream.cuda_stream)
-    # weak scaling: every rank validates its own 10k motions (distinct seeds),
-    # with no collective on the data path
-    w = W.make_cage_mv(args.queries, query_seed=203 + rank)
+    peaks, src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # weak scaling: every rank validates its own batch (distinct seeds), with
+    # no collective on the data path
+    w = W.make_ragged_teams(args.queries, seed=205 + rank)
     ba_host = ctx.bind(w)
     ba = ba_host.to("cuda")
     nq = w.batch.n_queries
+    kind = torch.as_tensor(w.batch.q_kind, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
     valid = torch.empty(nq, dtype=torch.uint8, device=dev)
     conf = torch.empty((nq, 3), dtype=torch.int32, device=dev)
-    kind = torch.zeros(nq, dtype=torch.uint8, device=dev)       # every query is MV
-    ba.a["q_kind"] = kind
     bs = ba.struct(mrv.MRV_CHECK_ENV, with_kind=True)
-    # scheduler tuning for this batch class (untimed setup; the graph keeps it)
-    mrv.mrv_autotune(ctx.h, bs)
-    torch.cuda.synchronize()
-    graph = mrv.mrv_graph_create(ctx.h, bs, valid, conf)
-
-    def step():
-        mrv.mrv_graph_launch(graph)
+    with torch.cuda.stream(stream):
+        # scheduler tuning for this batch class (untimed setup; the graph keeps it)
+        autotune(ctx, w, mrv.MRV_CHECK_ENV, n_sample=min(nq, 100000))
+        graph = mrv.mrv_graph_create(ctx.h, bs, valid, conf)
+    tuning = mrv.mrv_get_tuning(ctx.h)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kern_ms = []
-    # clocks are sampled from the warm-up through the end of the timed steps
     torch.cuda.nvtx.range_push("timed")
     with Clocks(local) as clk:
-        # warm-up (also validates the run)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
-                step()
+                mrv.mrv_graph_launch(graph)
                 ctx.sync()
-        stats = ctx.stats()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -586,7 +726,7 @@ def run(args):
             for i in range(args.steps):
                 flush.zero_()
                 ev[i][0].record(stream)
-                step()
+                mrv.mrv_graph_launch(graph)
                 ev[i][1].record(stream)
                 ctx.sync()
                 st_step = ctx.stats()
@@ -602,114 +742,121 @@ def run(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_s = float(t.item())
     value = nq * world * args.steps / total_s
-    nvalid = int(valid.sum().item())
+    mvq, ffq = kind == 0, kind == 1
+    nvalid = int(valid[mvq].sum().item())
+    nconf = int((conf[ffq][:, 0] >= 0).sum().item())
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API (mrv_run) with pinned host buffers:
+    # the inputs' host->device copies and the results' device->host copies
+    # are inside the timed region
     bh = ba_host.to("cpu", pin=True)
+    vh = torch.empty(nq, dtype=torch.uint8).pin_memory()
+    ch = torch.empty((nq, 3), dtype=torch.int32).pin_memory()
+    bhs = bh.struct(mrv.MRV_CHECK_ENV, with_kind=True)
     e2e_ms = []
     with torch.cuda.stream(stream):
-        ctx.mv_validate(bh)
+        mrv.mrv_run(ctx.h, bhs, vh, ch)
         for i in range(max(3, min(args.steps, 10))):
             flush.zero_()
             torch.cuda.synchronize()
             if world > 1:
                 dist.barrier()
             t0 = time.perf_counter()
-            out = ctx.mv_validate(bh)
+            mrv.mrv_run(ctx.h, bhs, vh, ch)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    assert int(out.sum()) == nvalid
-    h2d = sum(v.numel() * v.element_size() for k, v in bh.a.items() if v is not None and k != "q_kind")
+    kh = w.batch.q_kind
+    assert np.array_equal(vh.numpy()[kh == 0], valid.cpu().numpy()[kh == 0])
+    assert np.array_equal(ch.numpy()[kh == 1], conf.cpu().numpy()[kh == 1])
+    h2d = sum(v.numel() * v.element_size() for v in bh.a.values() if v is not None)
+    d2h = vh.numel() * vh.element_size() + ch.numel() * ch.element_size()
     e2e_t = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_val = nq * world / (float(e2e_t.item()) / 1e3)
+
+    strong = None
+    if world > 1:
+        with torch.cuda.stream(stream):
+            strong = strong_scaling(ctx, nq, world, rank, host_group, flush)
+        if rank == 0:
+            # the gathered answer of the split batch equals this rank's whole-batch answer (same seed)
+            assert np.array_equal(strong.pop("_valid")[kh == 0], valid.cpu().numpy()[kh == 0])
+            assert np.array_equal(strong.pop("_conf")[kh == 1], conf.cpu().numpy()[kh == 1])
     if rank != 0:   # the remaining measurements run on rank 0 only
         mrv.mrv_graph_destroy(graph)
         ctx.close()
         dist.destroy_process_group()
         return
 
-    # one synchronous launch per query (the plain GPU path)
-    pq_n = min(nq, args.per_query_n)
-    sub = W.subset(w, np.arange(pq_n))
-    bsub = ctx.bind(sub, ctx.robot_ids, ctx.env_ids).to("cuda")
-    ctx.mv_validate(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pq_valid = ctx.mv_validate(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
-    torch.cuda.synchronize()
-    pq_rate = pq_n / (time.perf_counter() - t0)
-    assert torch.equal(pq_valid, valid[:pq_n])
+    # one synchronous launch per query (the plain GPU path) on the first
+    # queries of the same batch
+    with torch.cuda.stream(stream):
+        pq_n = min(nq, args.per_query_n)
+        bsub = ctx.bind(W.subset(w, np.arange(pq_n)), ctx.robot_ids, ctx.env_ids).to("cuda")
+        ctx.run(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pv, pc = ctx.run(bsub, flags=mrv.MRV_PER_QUERY_LAUNCH)
+        torch.cuda.synchronize()
+        pq_rate = pq_n / (time.perf_counter() - t0)
+    km = kind[:pq_n]
+    assert torch.equal(pv[km == 0], valid[:pq_n][km == 0]) and torch.equal(pc[km == 1], conf[:pq_n][km == 1])
 
-    # exhaustive passes (every state of every motion): with the frame-level
-    # broadphase, and testing every sphere pair (the dense, ALU-bound regime)
-    torch.cuda.nvtx.range_push("exhaustive")
-    ex = {}
-    for name, flags in (("broadphase", 0), ("dense", mrv.MRV_NO_BROADPHASE)):
-        ctx.mv_validate(ba, exhaustive=True, flags=flags)
-        ms = []
-        for _ in range(3):
-            flush.zero_()
-            ctx.mv_validate(ba, exhaustive=True, flags=flags)
-            ms.append(ctx.stats()["device_ms"])
-        ex[name] = (statistics.median(ms), ctx.stats())
-    torch.cuda.nvtx.range_pop()
-    orders = order_study(ctx, ba, flush)
-
-    peaks, src = _peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     kms = statistics.mean(kern_ms)
-    per_state = dense_flops_per_state(w)
-    achieved = st_step["states_checked"] * per_state / (kms / 1e3) / 1e12
+    achieved, frac = roofline_frac(st_step, kms, fp32_peak)
     performed = work_flops(st_step) / (kms / 1e3) / 1e12
-    ex_out = {name: {"kernel_ms": ms, "achieved": st["states_checked"] * per_state / (ms / 1e3) / 1e12,
-                     "frac": st["states_checked"] * per_state / (ms / 1e3) / 1e12 / fp32_peak,
-                     "performed": work_flops(st) / (ms / 1e3) / 1e12,
-                     "sphere_tests": st["sphere_tests"], "fk_chains": st["fk_chains"]}
-              for name, (ms, st) in ex.items()}
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "motion-checks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries_per_gpu": nq, "parallelism": f"replicas{world}",
+        "config": {"workload": WORKLOAD, "queries_per_gpu": nq, "mv_queries": int(mvq.sum().item()),
+                   "ffc_queries": int(ffq.sum().item()), "parallelism": f"replicas{world}",
                    "l2": "flushed before every timed step (512 MB write)",
-                   "launch": "CUDA graph: reset + prepare + persistent work-stealing kernel + results",
-                   "tuning": mrv.mrv_get_tuning(ctx.h)},
+                   "launch": "CUDA graph: reset + prepare + persistent work-stealing kernel instances + results",
+                   "tuning": tuning},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic_per_launch(),
-                     "kernel": "k_main (persistent MV kernel), early exit, frame-level broadphase",
-                     "work": f"states checked x {per_state} FP32 flops per composite state (every sphere pair, "
-                             "obstacle and self pair tested, 4 FK chains, 256 spheres placed)",
+                     "kernel": "k_main (persistent MV/FFC kernel, team layout), early exit, frame-level broadphase",
+                     "work": "the method's dense FP32 work on the states checked, from the kernel's counters: "
+                             f"{FLOPS_PER_TEST} flops per sphere-sphere test (robot-robot, obstacle, self), "
+                             f"{FLOPS_PER_BOX} per sphere-box test, {FLOPS_PER_JOINT} per joint and "
+                             f"{FLOPS_PER_FLANGE} per flange of each FK chain, {FLOPS_PER_SPHERE} per sphere placed",
+                     "flops_per_step": method_flops(st_step),
                      "states_checked": st_step["states_checked"],
-                     "performed": {"achieved": performed, "frac": performed / fp32_peak,
-                                   "work": "tests the kernel ran after the broadphase (bounding-sphere and "
-                                           "exact), FK chains and spheres placed, counted by the kernel"},
-                     "peak_source": f"SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({src} sm_max_mhz)"},
-        "roofline_exhaustive": ex_out,
-        "order_study": orders,
-        "e2e": {"value": e2e_val, "unit": "motion-checks/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(nq),
-                "api": "mv_validate with pinned host buffers", "ms_median": statistics.median(e2e_ms)},
+                     "kernel_ms": kms,
+                     "pipe_utilisation": {"achieved": performed, "frac": performed / fp32_peak,
+                                          "work": "the tests the kernel actually ran after the broadphase "
+                                                  "(bounding-sphere and exact), FK chains and spheres placed"},
+                     "peak_source": f"SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                    f"({src} sm_max_mhz)"},
+        "e2e": {"value": e2e_val, "unit": "motion-checks/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "api": "mrv_run with pinned host buffers",
+                "ms_median": statistics.median(e2e_ms)},
         "per_query_launch": {"value": pq_rate, "unit": "motion-checks/s", "queries": pq_n,
                              "speedup_batched": value / world / pq_rate},
         "effort": {"states": st_step["states_checked"] / max(1, st_step["states_available"]),
                    "sphere_tests_vs_dense": st_step["sphere_tests"] / max(1, st_step["sphere_tests_available"])},
-        "valid_total": f"{nvalid}/{nq}",
+        "valid_mv": f"{nvalid}/{int(mvq.sum().item())}",
+        "conflicts_ffc": f"{nconf}/{int(ffq.sum().item())}",
         "kernel_ms_mean": kms,
         # per graph step: k_prep, k_levels, k_scatter, the team k_main, the
         # large-team k_main (forked beside it; no work item on this batch), k_finish
         "gpu_launches": 6 * args.steps,
         "clocks": clocks,
     }
-    if not args.no_configs:
-        line["configs"] = other_configs(ctx, flush)
-        line["validation_study"] = validation_study(ctx, flush)
-    if not args.no_serve:
-        line["serving"] = serving(ctx, args.serve_seconds)
+    if strong is not None:
+        line["strong_scaling"] = strong
+    mrv.mrv_graph_destroy(graph)
+    with torch.cuda.stream(stream):
+        if not args.no_configs:
+            line["configs"] = {"cage_mv_10k": cage_mv_config(ctx, flush, fp32_peak, stream)}
+            line["configs"].update(other_configs(ctx, flush, fp32_peak))
+            line["validation_study"] = validation_study(ctx, flush)
+        if not args.no_serve:
+            line["serving"] = serving(ctx, args.serve_seconds)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-    mrv.mrv_graph_destroy(graph)
     ctx.close()
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -722,10 +869,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrv", choices=["mrv", "reference"])
-    ap.add_argument("--queries", type=int, default=10000)
+    ap.add_argument("--queries", type=int, default=1_000_000)
     ap.add_argument("--per-query-n", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-sample", type=int, default=1000)
+    ap.add_argument("--ref-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true")

@@ -350,7 +350,13 @@ int mrv_graph_destroy(mrv_graph *g);
  * device footprint fits in the free part of `device_budget_bytes`, packs
  * every admitted request into one micro-batch, and runs it while other
  * micro-batches are still on the device.  Robot and env ids refer to the
- * context's resident uploads. */
+ * context's resident uploads.  At creation every stream's device arena and
+ * pinned staging are sized for a micro-batch of max_batch_queries queries
+ * of up to 8 robots on two waypoints each (halved until all of them take at
+ * most half of the device's free memory), micro-batches are packed within
+ * those buffers, and only a single request larger than them makes its
+ * stream's buffers grow.  The budget is clamped to the device's free memory
+ * after that sizing plus the arenas themselves (see mrv_server_stats). */
 typedef struct mrv_server mrv_server;
 typedef struct {
   int32_t n_streams;            /* concurrent micro-batches (1..16)          */
@@ -372,6 +378,10 @@ typedef struct {
   uint64_t submitted, completed, rejected, micro_batches, queries;
   uint64_t max_inflight;        /* largest number of micro-batches in flight */
   double busy_ms;               /* device time summed over micro-batches     */
+  uint64_t device_budget_bytes; /* admission budget in force (after clamping) */
+  uint64_t device_free_bytes;   /* device free memory after the buffers were
+                                   sized at creation                        */
+  uint64_t presized_queries;    /* queries per micro-batch the buffers hold  */
 } mrv_server_stats;
 int mrv_server_get_stats(mrv_server *s, mrv_server_stats *out);
 

@@ -80,6 +80,14 @@ static int grow_pinned(void **p, size_t *cap, size_t need) {
   return MRV_OK;
 }
 
+// pinned staging of one micro-batch: packed inputs, and results (valid
+// bytes rounded up to 256, conflicts, the error word)
+static size_t in_bytes_for(size_t nq, size_t ns, size_t nw, size_t stride, bool timed) {
+  return sizeof(int32_t) * (nq + 1 + ns + ns + 1 + (timed ? nw : 0) + nq) + sizeof(float) * nw * stride + nq +
+         64 * 8;
+}
+static size_t out_bytes_for(size_t nq) { return ((nq + 255) & ~size_t(255)) + sizeof(mrv_conflict) * nq + 64; }
+
 }  // namespace mrv
 
 struct mrv_server {
@@ -118,10 +126,10 @@ void mrv_server::launch(Slot &s) {
     any_env |= r->has_env || r->env_id != -1;
     any_kind |= r->has_kind;
   }
-  const size_t in_bytes = sizeof(int32_t) * ((size_t)nq + 1 + ns + ns + 1 + (timed ? nw : 0) + nq) +
-                          sizeof(float) * (size_t)nw * stride + nq + 64 * 8;
-  // valid bytes (rounded up to 256), conflicts, the error word
-  const size_t out_bytes = (((size_t)nq + 255) & ~size_t(255)) + sizeof(mrv_conflict) * (size_t)nq + 64;
+  const size_t in_bytes = in_bytes_for(nq, ns, nw, stride, timed);
+  const size_t out_bytes = out_bytes_for(nq);
+  // buffers were sized at creation; they grow here only for a single request
+  // larger than that (the packing below never exceeds them otherwise)
   int rc = grow_pinned(&s.pin_in, &s.pin_in_cap, in_bytes);
   if (!rc) rc = grow_pinned(&s.pin_out, &s.pin_out_cap, out_bytes);
   if (!rc) rc = s.scratch.ensure(nq, ns, nw, stride, s.stream);
@@ -285,12 +293,23 @@ void mrv_server::loop() {
       // admission in arrival order: the head request decides the group
       auto &head = pending.front();
       if (used + head->footprint > opts.device_budget_bytes) break;
-      int32_t q = 0;
+      int32_t q = 0, ns = 0, nw = 0, stride = 1;
       while (!pending.empty()) {
         auto &r = pending.front();
         if (!s.reqs.empty() && !compatible(*s.reqs[0], *r)) break;
         if (!s.reqs.empty() && q + r->nq > opts.max_batch_queries) break;
         if (used + r->footprint > opts.device_budget_bytes) break;
+        // keep a micro-batch inside the slot's buffers (sized at creation),
+        // so nothing is allocated while other micro-batches are in flight
+        const int32_t st2 = std::max(stride, r->stride);
+        if (!s.reqs.empty() &&
+            (Scratch::bytes_for(q + r->nq, ns + r->ns, nw + r->nw, st2) > s.scratch.cap ||
+             in_bytes_for(q + r->nq, ns + r->ns, nw + r->nw, st2, r->timed) > s.pin_in_cap ||
+             out_bytes_for(q + r->nq) > s.pin_out_cap))
+          break;
+        ns += r->ns;
+        nw += r->nw;
+        stride = st2;
         used += r->footprint;
         q += r->nq;
         s.reqs.push_back(r);
@@ -336,6 +355,44 @@ int mrv_server_create(mrv_ctx *c, const mrv_server_opts *o, mrv_server **out) {
       return rc;
     }
   }
+  // Every slot's device arena and pinned staging are sized here for a full
+  // micro-batch of max_batch_queries queries of up to kTeamRobots robots on
+  // two waypoints each (stride 8), within half of the free device memory, so
+  // the scheduler allocates nothing while micro-batches are in flight (a
+  // cudaFree or cudaFreeHost there would synchronize the whole device).
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "device memory query");
+    mrv_server_destroy(s);
+    return rc;
+  }
+  int64_t nq0 = o->max_batch_queries;
+  auto arena = [](int64_t nq) { return Scratch::bytes_for(nq, nq * kTeamRobots, 2 * nq * kTeamRobots, 8); };
+  while (nq0 > 256 && (size_t)o->n_streams * (arena(nq0) + arena(nq0) / 4) > free_b / 2) nq0 /= 2;
+  for (auto &sl : s->slots) {
+    int rc = sl.scratch.ensure(nq0, nq0 * kTeamRobots, 2 * nq0 * kTeamRobots, 8, sl.stream);
+    if (!rc) rc = grow_pinned(&sl.pin_in, &sl.pin_in_cap, in_bytes_for(nq0, nq0 * kTeamRobots, 2 * nq0 * kTeamRobots, 8, true));
+    if (!rc) rc = grow_pinned(&sl.pin_out, &sl.pin_out_cap, out_bytes_for(nq0));
+    if (rc) {
+      mrv_server_destroy(s);
+      return rc;
+    }
+  }
+  // admission by device memory: the budget cannot exceed what the device
+  // holds for requests (its free memory now plus the arenas just sized)
+  size_t free_after = 0;
+  if ((e = cudaMemGetInfo(&free_after, &total_b)) != cudaSuccess) {
+    int rc = cuda_fail(e, "device memory query");
+    mrv_server_destroy(s);
+    return rc;
+  }
+  size_t arenas = 0;
+  for (auto &sl : s->slots) arenas += sl.scratch.cap;
+  s->opts.device_budget_bytes = std::min(o->device_budget_bytes, free_after + arenas);
+  s->st.device_budget_bytes = s->opts.device_budget_bytes;
+  s->st.device_free_bytes = free_after;
+  s->st.presized_queries = (uint64_t)nq0;
   try {
     s->th = std::thread([s] { s->loop(); });
   } catch (...) {

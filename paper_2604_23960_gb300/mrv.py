@@ -96,7 +96,8 @@ class ServerOpts(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
                 ("micro_batches", C.c_uint64), ("queries", C.c_uint64), ("max_inflight", C.c_uint64),
-                ("busy_ms", C.c_double)]
+                ("busy_ms", C.c_double), ("device_budget_bytes", C.c_uint64), ("device_free_bytes", C.c_uint64),
+                ("presized_queries", C.c_uint64)]
 
 
 # name -> (restype, argtypes)

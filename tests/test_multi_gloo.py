@@ -64,3 +64,27 @@ def test_partition_is_balanced_and_complete():
         loads = [costs[s].sum() for s in sh]
         assert max(loads) - min(loads) <= costs.max() + 1e-9
         assert [list(s) for s in multi.shard_by_cost(costs, world)] == [list(s) for s in sh]
+
+
+def test_take_queries_equals_subset():
+    """The vectorised CSR gather of run_sharded's shards equals the
+    query-by-query subset of the workload module."""
+    from paper_2604_23960_gb300 import mrv
+    for w in (W.make_ragged_teams(300, seed=9), W.make_cage_mv(50)):
+        b = w.batch
+        arrays = {"q_robot_off": b.q_robot_off.astype(np.int32), "slot_robot_id": b.slot_robot.astype(np.int32),
+                  "slot_wp_off": b.slot_wp_off.astype(np.int32), "waypoints": b.waypoints,
+                  "seg_steps": b.seg_steps, "q_env_id": b.q_env, "q_kind": b.q_kind}
+        ba = mrv.BatchArrays(arrays, b.n_queries, int(b.q_robot_off[-1]), int(b.slot_wp_off[-1]), b.wp_stride,
+                             b.resolution, 0, False)
+        idx = np.sort(np.random.default_rng(1).choice(b.n_queries, 17, replace=False))
+        t = multi.take_queries(ba, idx)
+        ws = W.subset(w, idx).batch
+        for k, ref in (("q_robot_off", ws.q_robot_off), ("slot_robot_id", ws.slot_robot),
+                       ("slot_wp_off", ws.slot_wp_off), ("waypoints", ws.waypoints), ("seg_steps", ws.seg_steps),
+                       ("q_kind", ws.q_kind)):
+            if ref is None:
+                assert t.a[k] is None
+            else:
+                np.testing.assert_array_equal(np.asarray(t.a[k]), np.asarray(ref))
+        assert (t.n_queries, t.n_slots, t.n_waypoints) == (17, int(ws.q_robot_off[-1]), int(ws.slot_wp_off[-1]))
