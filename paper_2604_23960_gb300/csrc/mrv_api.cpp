@@ -80,7 +80,7 @@ size_t Scratch::layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char 
   set(&level_start, sizeof(int32_t) * kLevelBins);
   set(&cursor, sizeof(int32_t) * kLevelBins);
   set(&counters, sizeof(int32_t) * 8);
-  set(&err, sizeof(uint32_t) * 2);
+  set(&err, sizeof(uint32_t) * kErrWords);
   set(&stats, sizeof(unsigned long long) * kNumStats);
   set(&counts, sizeof(int32_t) * 4);
   // staged inputs
@@ -267,7 +267,7 @@ cudaError_t Scratch::reset(cudaStream_t st) const {
   if (contiguous) return cudaMemsetAsync(hist, 0, (size_t)(b - a), st);
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * kLevelBins, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * 8, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t) * 2, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t) * kErrWords, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kNumStats, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 4, st);
   return e;
@@ -330,8 +330,21 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   return MRV_OK;
 }
 
-int check_device_err(uint32_t err) {
+static const char *check_site_name(uint32_t site) {
+  static const char *const names[] = {"none",
+#define MRV_CK_NAME(name, text) text,
+                                      MRV_CHECK_SITES(MRV_CK_NAME)
+#undef MRV_CK_NAME
+  };
+  return site < sizeof(names) / sizeof(names[0]) ? names[site] : "unknown site";
+}
+
+int check_device_err(const uint32_t *rec) {
+  const uint32_t err = rec[0];
   if (!err) return MRV_OK;
+  if (err & kErrChecked)
+    return fail(MRV_ERR_CUDA, "bounds check failed (MRV_CHECKED build): %s, index %u outside 0..%u",
+                check_site_name(rec[1]), rec[2], rec[3] ? rec[3] - 1 : 0u);
   if (err & kErrTimeout) return fail(MRV_ERR_TIMEOUT, "device work exceeded its clock budget");
   if (err & kErrAbort) return fail(MRV_ERR_TIMEOUT, "device work aborted");
   if (err & kErrRobotId) return fail(MRV_ERR_NOT_FOUND, "batch names an unknown robot id");
@@ -346,7 +359,7 @@ int check_device_err(uint32_t err) {
 
 int finish_call(mrv_ctx *ctx, Scratch &S, bool async) {
   cudaStream_t st = ctx->stream;
-  cudaError_t e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(ctx->h_status, S.err, sizeof(uint32_t) * kErrWords, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->h_stats, S.stats, sizeof(unsigned long long) * kNumStats, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
@@ -389,7 +402,7 @@ int mrv_ctx::sync() {
   if (timed_pending && cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) stats.device_ms = ms;
   cudaGetLastError();
   timed_pending = false;
-  return check_device_err(h_status[0]);
+  return check_device_err(h_status);
 }
 
 namespace mrv {
@@ -661,6 +674,7 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
   }
   D.self_blocks = PM.self_blocks.empty() ? nullptr : (const int4 *)m.d_blocks;
   D.self_masks = PM.self_masks.empty() ? nullptr : (const uint32_t *)m.d_masks;
+  D.n_masks = (int32_t)PM.self_masks.size();
   // rectangles pay off only when they are large enough to fill a warp's
   // 4-rows-per-lane tiling; small ones stay on the sparse pair path
   std::vector<std::pair<int32_t, int32_t>> spr(sp);
@@ -796,6 +810,7 @@ int env_upload(mrv_ctx *c, const mrv_env_desc *d, int32_t *id_out) {
     h.dev.g_off = (const int32_t *)h.d_goff;
     h.dev.g_cnt = (const uint32_t *)h.d_gcnt;
     h.dev.g_items = (const uint16_t *)h.d_gitems;
+    h.dev.g_nitems = (int32_t)G.items.size();
   }
   h.refs = 1;
   c->envs.push_back(h);
@@ -920,9 +935,10 @@ int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, 
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_fail(e, "query record copy");
   if (hq.bits & 4u) {
-    uint32_t err = 0;
-    cudaMemcpy(&err, S.err, sizeof err, cudaMemcpyDeviceToHost);
-    return check_device_err(err ? err : kErrRobots);
+    uint32_t rec[kErrWords] = {};
+    cudaMemcpy(rec, S.err, sizeof rec, cudaMemcpyDeviceToHost);
+    if (!rec[0]) rec[0] = kErrRobots;
+    return check_device_err(rec);
   }
   const int32_t *d_ts = ts;
   float *d_out = out;
@@ -937,13 +953,12 @@ int mrv_clearance(mrv_ctx *c, const mrv_batch *b, int32_t q, const int32_t *ts, 
   if (e == cudaSuccess) e = launch_clearance(B, q, d_ts, nt, (b->flags & MRV_CHECK_ENV) ? 1 : 0, d_out, st);
   if (e == cudaSuccess && !dev)
     e = cudaMemcpyAsync(out, d_out, sizeof(float) * (size_t)nt * hq.M, cudaMemcpyDeviceToHost, st);
-  uint32_t err = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, S.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_status, S.err, sizeof(uint32_t) * kErrWords, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(e, "clearance");
-  err = c->h_status[0];
-  return check_device_err(err);
+  return check_device_err(c->h_status);
 }
 
 // ---- graphs -----------------------------------------------------------------
@@ -1014,7 +1029,7 @@ int mrv_graph_launch(mrv_graph *g) {
   cudaError_t e = cudaGraphLaunch(g->exec, c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
   // status of the replay is read by the next mrv_sync
-  e = cudaMemcpyAsync(c->h_status, g->scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+  e = cudaMemcpyAsync(c->h_status, g->scratch.err, sizeof(uint32_t) * kErrWords, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->h_stats, g->scratch.stats, sizeof(unsigned long long) * kNumStats, cudaMemcpyDeviceToHost,
                         c->stream);

@@ -40,6 +40,55 @@ enum : uint32_t {
   kErrDof = 1u << 6,         // wp_stride < dof
   kErrTimeout = 1u << 7,     // persistent kernel exceeded its clock budget
   kErrAbort = 1u << 8,       // abort flag observed
+  kErrChecked = 1u << 9,     // MRV_CHECKED build: an index left its array
+};
+
+// The error record of a call: err[0] the bits above; in the MRV_CHECKED
+// build err[1] = the first failing check site (below), err[2] its index and
+// err[3] the extent it was checked against (low 32 bits each).
+constexpr int kErrWords = 4;
+
+// Index checks of the MRV_CHECKED build, one per array access class: a
+// failing check records its site and redirects the access to element 0 of
+// the same array (in bounds), so the kernel runs to its end without a fault
+// and the call reports MRV_ERR_CUDA naming the site.
+#define MRV_CHECK_SITES(X)                                                    \
+  X(HIST, "k_prep: level-histogram bin")                                      \
+  X(SEGSTEPS, "k_prep: waypoint step count index")                            \
+  X(LEVELS, "k_levels: level-start entry")                                    \
+  X(SCATTER, "k_scatter: sorted position")                                    \
+  X(SORTED, "k_main: sorted query index")                                     \
+  X(QUERY, "k_main: query index")                                             \
+  X(FINISH_PAIR, "k_finish: robot pair decoded from the FFC key")             \
+  X(SLOTS, "run_chunk: robot slot of the query")                              \
+  X(PAIRTAB, "run_chunk: robot-pair table entry")                             \
+  X(PAIRTAB_PREFIX, "run_chunk: frame-pair prefix (16 bits)")                 \
+  X(CHAIN, "slice_b: FK chain slot in the link-frame buffer")                 \
+  X(WAYPOINT, "interp: waypoint row")                                         \
+  X(LINK, "frame index of a sphere or bounding sphere")                       \
+  X(FRAME_SLOT, "frame slot (robot x frame) of a bounding sphere or mask")    \
+  X(SPHERE, "sphere center of the query (P)")                                 \
+  X(GRID_CELL, "obstacle grid cell")                                          \
+  X(GRID_ITEM, "obstacle grid item")                                          \
+  X(OBST_SPHERE, "obstacle sphere index")                                     \
+  X(OBST_BOX, "obstacle box index")                                           \
+  X(OBST_CYL, "obstacle cylinder index")                                      \
+  X(SELF_GROUP, "self-pair group frames")                                     \
+  X(SELF_BLOCK, "self-pair block rows / columns (10-bit offsets)")            \
+  X(SELF_MASK, "self-pair block row mask")                                    \
+  X(SELF_PAIR, "self-pair list entry")                                        \
+  X(CAND, "candidate list entry")                                             \
+  X(ROBOT_CULL, "large-team robot cull list")                                 \
+  X(FLAVOR_A, "one-lane-per-state sphere buffer")                             \
+  X(RECT, "self-pair rectangle rows / columns")                               \
+  X(CLEAR_OUT, "k_clearance: output or sphere index")
+
+enum : uint32_t {
+  kCkNone = 0,
+#define MRV_CK_ENUM(name, text) kCk_##name,
+  MRV_CHECK_SITES(MRV_CK_ENUM)
+#undef MRV_CK_ENUM
+  kCkCount
 };
 
 struct ModelDev {
@@ -67,7 +116,7 @@ struct ModelDev {
                                  // first row mask; null: pair list only
   const uint32_t *self_masks;    // per block row: bit c = pair with column c
   int32_t n_groups;
-  int32_t pad3;
+  int32_t n_masks;               // self-pair block rows (entries of self_masks)
   const int32_t *perm;           // sorted sphere index -> caller's index
 };
 
@@ -94,7 +143,7 @@ struct EnvDev {
   const uint16_t *g_items;
   // solid cylinders with flat caps
   int32_t n_cyl;
-  int32_t pad2;
+  int32_t g_nitems;              // entries of g_items
   const float4 *cyl_a;           // axis end a xyz, radius
   const float4 *cyl_u;           // unit axis (a -> b) xyz, length |b - a|
 };
@@ -157,7 +206,7 @@ struct BatchDev {
   int32_t *counters;                 // [0] class-0 work counter, [1] class-0 items, [2] abort flag,
                                      // [3] class-1 items, [4] class-1 work counter,
                                      // [5] class-0 queries (first sorted position of class 1)
-  uint32_t *err;
+  uint32_t *err;                     // kErrWords: error bits, check site, index, extent
   unsigned long long *stats;         // [0] states checked, [1] tests executed,
                                      // [2] states available, [3] tests available,
                                      // [4] items, [5] box tests executed,

@@ -160,7 +160,8 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
 int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st);
 int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr, mrv_conflict *conf);
 int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls);
-int check_device_err(uint32_t err);
+// maps a device error record (kErrWords words) to a status and message
+int check_device_err(const uint32_t *rec);
 // copies the error word, statistics and counts of the call just enqueued to
 // the context's pinned host words; waits for them unless async
 int finish_call(mrv_ctx *ctx, Scratch &S, bool async);

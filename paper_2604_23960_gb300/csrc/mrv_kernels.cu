@@ -57,6 +57,29 @@
 
 namespace mrv {
 
+// Index checks of the MRV_CHECKED build (see MRV_CHECK_SITES): CK(i, n, site,
+// err) is i when 0 <= i < n; otherwise the first failure's site, index and
+// extent go to the error record err[0..3] and the access is redirected to
+// element 0 (in bounds), so the kernel never faults and runs to its end.  In
+// the normal build CK(i, ...) is i.
+#ifdef MRV_CHECKED
+__device__ __noinline__ void ck_fail(uint32_t *err, uint32_t site, long long i, long long n) {
+  if (atomicCAS(err + 1, 0u, site) == 0u) {
+    err[2] = (uint32_t)i;
+    err[3] = (uint32_t)n;
+  }
+  atomicOr(err, kErrChecked);
+}
+__device__ __forceinline__ long long ck_idx(long long i, long long n, uint32_t site, uint32_t *err) {
+  if (i >= 0 && i < n) return i;
+  ck_fail(err, site, i, n);
+  return 0;
+}
+#define CK(i, n, site, err) ((decltype(i))::mrv::ck_idx((long long)(i), (long long)(n), ::mrv::kCk_##site, (err)))
+#else
+#define CK(i, n, site, err) (i)
+#endif
+
 constexpr int kFlavorAMaxSpheres = 16;
 constexpr int kSlotWords = 28;                   // words per RobotSlot in shared memory
 constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
@@ -75,6 +98,7 @@ struct RobotSlot {           // per-warp staged view of one robot of the query
 static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
 struct TileCtx {
+  uint32_t *err;             // the call's error record (index checks of MRV_CHECKED)
   int q, T, n, M, nb, ffc, check_env, exhaustive, broad;
   int lin;                   // linear state order (FFC, or MV with MRV_LINEAR)
   int prio;                  // prioritized MV: slot 0 against obstacles, itself and slots 1..n-1
@@ -311,7 +335,7 @@ __global__ void k_prep(BatchDev B) {
       if (B.seg_steps) {
         B.slot_tau[w0] = 0;
         for (int w = w0; w < w1 - 1; ++w) {
-          const int st = B.seg_steps[w];
+          const int st = B.seg_steps[CK(w, B.n_waypoints, SEGSTEPS, B.err)];
           if (st < 1) { err |= kErrSteps; break; }
           Ts += st;
           if (Ts > MRV_MAX_STEPS) { err |= kErrSteps; break; }
@@ -396,7 +420,8 @@ __global__ void k_prep(BatchDev B) {
   B.q_hit[q] = 0;
   B.q_best[q] = 0x7fffffff;
   B.q_minclr[q] = __int_as_float(f2ord(INFINITY));
-  atomicAdd(&B.hist[((Q.bits & 8u) ? kMaxLevels + 1 : 0) + (Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks)], 1);
+  atomicAdd(&B.hist[CK(((Q.bits & 8u) ? kMaxLevels + 1 : 0) + (Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks),
+                       kLevelBins, HIST, B.err)], 1);
 }
 
 // level layout, per work class: the class's queries sorted by item count
@@ -437,7 +462,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_levels(BatchDev B) {
   if (t < kLevelBins) {
     const int qbase = cls ? n0 : 0;
     B.cursor[t] = qbase + S1;
-    if (k < kMaxLevels) B.level_start[cls * L + k + 1] = pre[t];
+    if (k < kMaxLevels) B.level_start[CK(cls * L + k + 1, kLevelBins, LEVELS, B.err)] = pre[t];
     if (k == 0) B.level_start[cls * L] = 0;
     if (k == kMaxLevels - 1) B.counters[cls ? 3 : 1] = pre[t];   // the class's work items
     if (t == 0) B.counters[5] = n0;
@@ -451,7 +476,7 @@ __global__ void k_scatter(BatchDev B) {
   int c = Q.nchunks;
   if (c > kMaxLevels) c = kMaxLevels;
   const int pos = atomicAdd(&B.cursor[((Q.bits & 8u) ? kMaxLevels + 1 : 0) + c], 1);
-  B.sorted[pos] = q;
+  B.sorted[CK(pos, B.n_queries, SCATTER, B.err)] = q;
 }
 
 // ---------------------------------------------------------------------------
@@ -464,7 +489,7 @@ __device__ __forceinline__ void interp(const BatchDev &B, int w0, int w1, int do
   const int last = w1 - 1;
   const int *tau = B.slot_tau;
   if (t >= tau[last]) {
-    const float *a = B.waypoints + (size_t)last * B.wp_stride;
+    const float *a = B.waypoints + (size_t)CK(last, B.n_waypoints, WAYPOINT, B.err) * B.wp_stride;
 #pragma unroll
     for (int j = 0; j < MRV_MAX_DOF; ++j)
       if (j < dof) q[j] = a[j];
@@ -476,6 +501,7 @@ __device__ __forceinline__ void interp(const BatchDev &B, int w0, int w1, int do
     if (tau[mid] <= t) lo = mid;
     else hi = mid - 1;
   }
+  lo = CK(lo, B.n_waypoints - 1, WAYPOINT, B.err);   // rows lo and lo + 1
   const float f = (float)(t - tau[lo]) / (float)(tau[lo + 1] - tau[lo]);
   const float *a = B.waypoints + (size_t)lo * B.wp_stride;
   const float *g = a + B.wp_stride;
@@ -493,7 +519,7 @@ __device__ __forceinline__ void interp_from(const BatchDev &B, int w0, int w1, i
   const int last = w1 - 1;
   const int *tau = B.slot_tau;
   if (t >= tau[last]) {
-    const float *a = B.waypoints + (size_t)last * B.wp_stride;
+    const float *a = B.waypoints + (size_t)CK(last, B.n_waypoints, WAYPOINT, B.err) * B.wp_stride;
 #pragma unroll
     for (int j = 0; j < MRV_MAX_DOF; ++j)
       if (j < dof) q[j] = a[j];
@@ -512,6 +538,7 @@ __device__ __forceinline__ void interp_from(const BatchDev &B, int w0, int w1, i
     }
   }
   *lo_out = lo;
+  lo = CK(lo, B.n_waypoints - 1, WAYPOINT, B.err);   // rows lo and lo + 1
   const float f = (float)(t - tau[lo]) / (float)(tau[lo + 1] - tau[lo]);
   const float *a = B.waypoints + (size_t)lo * B.wp_stride;
   const float *g = a + B.wp_stride;
@@ -731,7 +758,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
         w.y = m.base[4] * lx + m.base[5] * ly + m.base[6] * lz + m.base[7];
         w.z = m.base[8] * lx + m.base[9] * ly + m.base[10] * lz + m.base[11];
         w.w = s.w;
-        PA[(S.off[r] + kk) * kWarp + lane] = w;
+        PA[CK(S.off[r] + kk, kFlavorAMaxSpheres, FLAVOR_A, C.err) * kWarp + lane] = w;
       }
     }
   }
@@ -766,8 +793,8 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
       for (int r = 0; r < C.self_robots; ++r)
         for (int p = 0; p < S.rs[r].n_self; ++p) {
           const uint32_t sp = S.rs[r].self[p];
-          const float4 x = PA[(S.off[r] + (int)(sp & 0xffffu)) * kWarp + lane];
-          const float4 y = PA[(S.off[r] + (int)(sp >> 16)) * kWarp + lane];
+          const float4 x = PA[CK(S.off[r] + (int)(sp & 0xffffu), C.M, FLAVOR_A, C.err) * kWarp + lane];
+          const float4 y = PA[CK(S.off[r] + (int)(sp >> 16), C.M, FLAVOR_A, C.err) * kWarp + lane];
           if (CLR) minclr = fminf(minclr, sph_clr(x, y));
           else hit |= sph_hit(x, y);
         }
@@ -972,6 +999,8 @@ __device__ bool env_mv(const TileCtx &C, const WS &S, const float4 *P, const flo
     if (nr > 0) {
       for (int k = 0; k < nr; ++k) {
         const int4 R = __ldg(&S.rs[r].rects[k]);
+        CK(R.y - 1, S.rs[r].m, RECT, C.err);
+        CK(R.w - 1, S.rs[r].m, RECT, C.err);
         hit |= rect_test(P, o + R.x, o + R.y, P, K, o + R.z, o + R.w, 0.f, 0.f, 0.f, eps, lane);
       }
     } else {
@@ -990,7 +1019,9 @@ __device__ bool env_mv(const TileCtx &C, const WS &S, const float4 *P, const flo
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (p0 + lane + kWarp * u < ns) hit |= sph_hit(Pr[e[u] & 0xffffu], Pr[e[u] >> 16]);
+          if (p0 + lane + kWarp * u < ns)
+            hit |= sph_hit(Pr[CK((int)(e[u] & 0xffffu), S.rs[r].m, SELF_PAIR, C.err)],
+                           Pr[CK((int)(e[u] >> 16), S.rs[r].m, SELF_PAIR, C.err)]);
       }
     }
   }
@@ -1016,14 +1047,14 @@ __device__ void link_spheres(const TileCtx &C, WS &S, const float *xf, int jj, i
     const ModelDev &md = *S.rs[r].md;
     float4 o = make_float4(0.f, 0.f, 0.f, -1.f);
     if (l < S.rs[r].n_links && md.link_bs[l][3] >= 0.f) {
-      const float *X = xf + ((jj * n + r) * kMaxLinks + l) * 12;
+      const float *X = xf + (CK(jj * n + r, WS::kChains, CHAIN, C.err) * kMaxLinks + l) * 12;
       const float cx = md.link_bs[l][0], cy = md.link_bs[l][1], cz = md.link_bs[l][2];
       o.x = fmaf(X[0], cx, fmaf(X[1], cy, fmaf(X[2], cz, X[3]))) - S.ox;
       o.y = fmaf(X[4], cx, fmaf(X[5], cy, fmaf(X[6], cz, X[7]))) - S.oy;
       o.z = fmaf(X[8], cx, fmaf(X[9], cy, fmaf(X[10], cz, X[11]))) - S.oz;
       o.w = md.link_bs[l][3];
     }
-    S.BS[k] = o;
+    S.BS[CK(k, WS::kRobots * kMaxLinks, FRAME_SLOT, C.err)] = o;
   }
 }
 
@@ -1041,14 +1072,14 @@ __device__ unsigned pairs_broad(const TileCtx &C, const WS &S, const float4 *P, 
     const int i = k / kMaxLinks, u = k - i * kMaxLinks;   // constant divisor
     const float4 bu = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
     if (bu.w >= 0.f && i < C.pair_robots) {
-      const int a0 = S.off[i] + S.rs[i].ls[u], a1 = S.off[i] + S.rs[i].ls[u + 1];
+      const int a0 = S.off[i] + S.rs[i].ls[u], a1 = CK(S.off[i] + S.rs[i].ls[u + 1], C.M + 1, SPHERE, C.err);
       for (int k2 = (i + 1) * kMaxLinks; k2 < nk; ++k2) {
         const float4 bv = S.BS[k2];
         if (bv.w < 0.f) continue;
         ntests += 1;
         if (!sph_hit(bu, bv)) continue;
         const int j = k2 / kMaxLinks, v = k2 - j * kMaxLinks;
-        const int b0 = S.off[j] + S.rs[j].ls[v], b1 = S.off[j] + S.rs[j].ls[v + 1];
+        const int b0 = S.off[j] + S.rs[j].ls[v], b1 = CK(S.off[j] + S.rs[j].ls[v + 1], C.M + 1, SPHERE, C.err);
         bool h = false;
         for (int a = a0; a < a1 && !h; ++a) {
           const float4 pa = P[a];
@@ -1076,7 +1107,7 @@ __device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int la
     const float4 bl = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
     if (bl.w < 0.f) continue;
     const int r = k / kMaxLinks, l = k - r * kMaxLinks;
-    const int a0 = S.off[r] + S.rs[r].ls[l], a1 = S.off[r] + S.rs[r].ls[l + 1];
+    const int a0 = S.off[r] + S.rs[r].ls[l], a1 = CK(S.off[r] + S.rs[r].ls[l + 1], C.M + 1, SPHERE, C.err);
     const float4 bw = make_float4(bl.x + S.ox, bl.y + S.oy, bl.z + S.oz, bl.w);
     for (int e = 0; e < C.env_ns; ++e) {
       const float4 es = e < ns_c ? S.ES[e] : __ldg(&C.env_s[e]);
@@ -1128,7 +1159,8 @@ __device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int la
       bool ov = false;
       if (g < ng) {
         G = __ldg(&md.self_groups[g]);
-        ov = sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y]);
+        ov = sph_hit(S.BS[r * kMaxLinks + CK(G.x, S.rs[r].n_links, SELF_GROUP, C.err)],
+                     S.BS[r * kMaxLinks + CK(G.y, S.rs[r].n_links, SELF_GROUP, C.err)]);
         ntests += 1;
       }
       unsigned m = __ballot_sync(0xffffffffu, ov);
@@ -1137,8 +1169,9 @@ __device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int la
         m &= m - 1;
         const int gs = __shfl_sync(0xffffffffu, G.z, src), gc = __shfl_sync(0xffffffffu, G.w, src);
         for (int p = lane; p < gc; p += kWarp) {
-          const uint32_t e = __ldg(&md.self_pairs[gs + p]);
-          hit |= sph_hit(P[o + (int)(e & 0xffffu)], P[o + (int)(e >> 16)]);
+          const uint32_t e = __ldg(&md.self_pairs[CK(gs + p, (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err)]);
+          hit |= sph_hit(P[o + CK((int)(e & 0xffffu), S.rs[r].m, SELF_PAIR, C.err)],
+                         P[o + CK((int)(e >> 16), S.rs[r].m, SELF_PAIR, C.err)]);
           ntests += 1;
         }
       }
@@ -1232,21 +1265,21 @@ __device__ void place_needed(const TileCtx &C, WS &S, const float *xf, int jj, i
     const uint32_t hi = wd + 1 < NW ? cl.need[wd + 1] & ~cl.placed[wd + 1] : 0u;
     const uint32_t mr = (uint32_t)((((unsigned long long)hi << 32) | lo) >> sh) & ((1u << kMaxLinks) - 1u);
     if (!mr) continue;
-    const float *Xr = xf + (jj * n + r) * (kMaxLinks * 12);
+    const float *Xr = xf + CK(jj * n + r, WS::kChains, CHAIN, C.err) * (kMaxLinks * 12);
     const float4 *sph = S.rs[r].spheres;
     const int32_t *lnk = S.rs[r].links;
     const int a0 = S.off[r];
     // spheres are sorted by frame: walk from the first to the last frame to place
     const int s0 = S.rs[r].ls[__ffs(mr) - 1], s1 = S.rs[r].ls[32 - __clz(mr)];
     for (int kk = s0 + lane; kk < s1; kk += kWarp) {
-      const int l = __ldg(&lnk[kk]);
+      const int l = CK(__ldg(&lnk[kk]), S.rs[r].n_links, LINK, C.err);
       if (!((mr >> l) & 1u)) continue;
       const float4 sp = __ldg(&sph[kk]);
       const float *X = Xr + l * 12;
       const float wx = fmaf(X[0], sp.x, fmaf(X[1], sp.y, fmaf(X[2], sp.z, X[3])));
       const float wy = fmaf(X[4], sp.x, fmaf(X[5], sp.y, fmaf(X[6], sp.z, X[7])));
       const float wz = fmaf(X[8], sp.x, fmaf(X[9], sp.y, fmaf(X[10], sp.z, X[11])));
-      P[a0 + kk] = make_float4(wx - S.ox, wy - S.oy, wz - S.oz, sp.w);
+      P[CK(a0 + kk, C.M, SPHERE, C.err)] = make_float4(wx - S.ox, wy - S.oy, wz - S.oz, sp.w);
       acc.placed += 1;
     }
   }
@@ -1295,10 +1328,13 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WS &S, const uint32_t 
     if (KIND == 2) acc.cyls += (uint32_t)(fe - f);
     const float ox = S.ox, oy = S.oy, oz = S.oz;
     for (int it = list_find(cl.pf, n, f); f < fe; ++it) {
-      const uint32_t v = list[it];
-      const int o = (int)(v & 0xffffffu);
+      const uint32_t v = list[CK(it, kCand, CAND, C.err)];
+      const int o = CK((int)(v & 0xffffffu), KIND == 0 ? C.env_ns : (KIND == 1 ? C.env_nb : C.env_nc),
+                       CAND, C.err);
       const int ge = min(fe, cl.pf[it + 1]);
-      const float4 *Pk = P + frame_first(S, (int)(v >> 24)) - cl.pf[it];
+      const int k = CK((int)(v >> 24), WS::kRobots * kMaxLinks, CAND, C.err);
+      CK(frame_first(S, k) + (ge - cl.pf[it]) - 1, C.M, SPHERE, C.err);
+      const float4 *Pk = P + frame_first(S, k) - cl.pf[it];
       if (KIND == 0) {
         const float4 es = o < kEnvCache ? S.ES[o] : __ldg(&C.env_s[o]);
 #pragma unroll 4
@@ -1350,13 +1386,16 @@ __device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int 
       int c = 0;
       if (i < ns) {
         const uint32_t v = cl.sc[i];
-        const int r = (int)(v >> 16);
-        const int4 Bk = __ldg(&S.rs[r].md->self_blocks[v & 0xffffu]);
+        const int r = CK((int)(v >> 16), C.n, SELF_BLOCK, C.err);
+        const int4 Bk = __ldg(&S.rs[r].md->self_blocks[CK((int)(v & 0xffffu), S.rs[r].n_groups, SELF_BLOCK, C.err)]);
         const int o = S.off[r];
         c = Bk.z & 0xffff;
+        CK(o + Bk.x + c - 1, min(C.M, 1024), SELF_BLOCK, C.err);
+        CK(o + Bk.y + ((Bk.z >> 16) & 0xff) - 1, min(C.M, 1024), SELF_BLOCK, C.err);
+        CK(Bk.w + c - 1, min(S.rs[r].md->n_masks, 65536), SELF_MASK, C.err);
         cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 10) | ((uint32_t)r << 20);
         cl.scn[i] = (uint16_t)Bk.w;
-        cl.sck[i] = (uint8_t)(r * kMaxLinks + ((Bk.z >> 24) & 15));
+        cl.sck[i] = (uint8_t)(r * kMaxLinks + CK((Bk.z >> 24) & 15, S.rs[r].n_links, SELF_BLOCK, C.err));
       }
       base = scan_chunk(cl.pf, i, ns, c, base, lane);
     }
@@ -1379,7 +1418,7 @@ __device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int 
       while (mk) {
         const int c = __ffs(mk) - 1;
         mk &= mk - 1;
-        hit |= sph_hit(pa, Pc[c]);
+        hit |= sph_hit(pa, Pc[CK((int)((v >> 10) & 1023u) + c, C.M, SELF_MASK, C.err) - (int)((v >> 10) & 1023u)]);
       }
     }
     acc.tests += nt;
@@ -1408,10 +1447,12 @@ __device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int 
         const int ge = min(fe, cl.pf[it + 1]);
         const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
         const float4 *Pr = P + S.off[r];
+        CK((int)(v & 0xffffu) + (ge - cl.pf[it]) - 1, (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err);
 #pragma unroll 4
         for (; f < ge; ++f) {
           const uint32_t e = __ldg(&pr[f]);
-          hit |= sph_hit(Pr[e & 0xffffu], Pr[e >> 16]);
+          hit |= sph_hit(Pr[CK((int)(e & 0xffffu), S.rs[r].m, SELF_PAIR, C.err)],
+                         Pr[CK((int)(e >> 16), S.rs[r].m, SELF_PAIR, C.err)]);
         }
       }
     }
@@ -1462,7 +1503,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         if (bw.w <= gR) {
           const float fx = (bw.x - glx) * gih, fy = (bw.y - gly) * gih, fz = (bw.z - glz) * gih;
           if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)gdx && fy < (float)gdy && fz < (float)gdz) {
-            const int c = ((int)fz * gdy + (int)fy) * gdx + (int)fx;
+            const int c = CK(((int)fz * gdy + (int)fy) * gdx + (int)fx, gdx * gdy * gdz, GRID_CELL, C.err);
             i0 = __ldg(&E.g_off[c]);
             i1 = __ldg(&E.g_off[c + 1]);
             const uint32_t cnt = __ldg(&E.g_cnt[c]);
@@ -1477,8 +1518,9 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           acc.tests += (uint32_t)(i1 - i0);
           acc.boxes += (uint32_t)(ib - is);
           acc.cyls += (uint32_t)(i1 - ib);
+          CK(i1 - 1, E.g_nitems, GRID_ITEM, C.err);
           for (int i = i0; i < is; ++i) {
-            const int e = __ldg(&E.g_items[i]);
+            const int e = CK((int)__ldg(&E.g_items[i]), env_ns, OBST_SPHERE, C.err);
             const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
             if (sph_hit(bw, es)) {
               push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
@@ -1487,7 +1529,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
           const float rr = bw.w * bw.w;
           for (int i = is; i < ib; ++i) {
-            const int b = __ldg(&E.g_items[i]);
+            const int b = CK((int)__ldg(&E.g_items[i]), env_nb, OBST_BOX, C.err);
             const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
             const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
             if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
@@ -1496,7 +1538,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
             }
           }
           for (int i = ib; i < i1; ++i) {
-            const int y = __ldg(&E.g_items[i]);
+            const int y = CK((int)__ldg(&E.g_items[i]), C.env_nc, OBST_CYL, C.err);
             if (cyl_d2(bw.x, bw.y, bw.z, __ldg(&C.cyl_a[y]), __ldg(&C.cyl_u[y])) < rr) {
               push_obst(cl.yc, &cl.ny, &cl.overflow, k, y);
               nd = true;
@@ -1616,7 +1658,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
             if (g < ng) {
               G = __ldg(&groups[g]);
               acc.tests += 1;
-              ov = sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y]);
+              ov = sph_hit(S.BS[r * kMaxLinks + CK(G.x, S.rs[r].n_links, SELF_GROUP, C.err)],
+                           S.BS[r * kMaxLinks + CK(G.y, S.rs[r].n_links, SELF_GROUP, C.err)]);
             }
             const unsigned m = __ballot_sync(0xffffffffu, ov);
             if (!m) continue;
@@ -1625,7 +1668,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
               if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
             }
             if (ov) {
-              const int i = cl.ns + __popc(m & ((1u << lane) - 1u));
+              const int i = CK(cl.ns + __popc(m & ((1u << lane) - 1u)), kCand, CAND, C.err);
               // blocks: robot << 16 | group; pair list: robot << 16 | first pair
               cl.sc[i] = ((uint32_t)r << 16) | (uint32_t)(C.self_blk ? g : G.z);
               cl.scn[i] = (uint16_t)G.w;
@@ -1647,7 +1690,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           for (int g = lane; g < ng; g += kWarp) {
             const int4 G = __ldg(&groups[g]);
             acc.tests += 1;
-            if (sph_hit(S.BS[r * kMaxLinks + G.x], S.BS[r * kMaxLinks + G.y])) {
+            if (sph_hit(S.BS[r * kMaxLinks + CK(G.x, S.rs[r].n_links, SELF_GROUP, C.err)],
+                        S.BS[r * kMaxLinks + CK(G.y, S.rs[r].n_links, SELF_GROUP, C.err)])) {
               const int i = atomicAdd(&cl.ns, 1);
               if (i < kCand) {
                 // blocks: robot << 16 | group; pair list: robot << 16 | first pair
@@ -1682,13 +1726,16 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
             int c = 0;
             if (i < ns) {
               const uint32_t v = cl.sc[i];
-              const int r = (int)(v >> 16);
-              const int4 Bk = __ldg(&S.rs[r].md->self_blocks[v & 0xffffu]);
+              const int r = CK((int)(v >> 16), C.n, SELF_BLOCK, C.err);
+              const int4 Bk = __ldg(&S.rs[r].md->self_blocks[CK((int)(v & 0xffffu), S.rs[r].n_groups, SELF_BLOCK, C.err)]);
               const int o = S.off[r];
               c = Bk.z & 0xffff;
+              CK(o + Bk.x + c - 1, min(C.M, 1024), SELF_BLOCK, C.err);
+              CK(o + Bk.y + ((Bk.z >> 16) & 0xff) - 1, min(C.M, 1024), SELF_BLOCK, C.err);
+              CK(Bk.w + c - 1, min(S.rs[r].md->n_masks, 65536), SELF_MASK, C.err);
               cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 10) | ((uint32_t)r << 20);
               cl.scn[i] = (uint16_t)Bk.w;
-              cl.sck[i] = (uint8_t)(r * kMaxLinks + ((Bk.z >> 24) & 15));
+              cl.sck[i] = (uint8_t)(r * kMaxLinks + CK((Bk.z >> 24) & 15, S.rs[r].n_links, SELF_BLOCK, C.err));
             }
             base = scan_chunk(cl.pf, i, ns, c, base, lane);
           }
@@ -1711,7 +1758,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
             while (mk) {
               const int c = __ffs(mk) - 1;
               mk &= mk - 1;
-              hit |= sph_hit(pa, Pc[c]);
+              hit |= sph_hit(pa, Pc[CK((int)((v >> 10) & 1023u) + c, C.M, SELF_MASK, C.err) - (int)((v >> 10) & 1023u)]);
             }
           }
           acc.tests += nt;
@@ -1740,10 +1787,12 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
               const int ge = min(fe, cl.pf[it + 1]);
               const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
               const float4 *Pr = P + S.off[r];
-      #pragma unroll 4
+              CK((int)(v & 0xffffu) + (ge - cl.pf[it]) - 1, (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err);
+#pragma unroll 4
               for (; f < ge; ++f) {
                 const uint32_t e = __ldg(&pr[f]);
-                hit |= sph_hit(Pr[e & 0xffffu], Pr[e >> 16]);
+                hit |= sph_hit(Pr[CK((int)(e & 0xffffu), S.rs[r].m, SELF_PAIR, C.err)],
+                               Pr[CK((int)(e >> 16), S.rs[r].m, SELF_PAIR, C.err)]);
               }
             }
           }
@@ -1764,9 +1813,11 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   // listed first; pairs first: the adjacent pairs, listed first, or the rest);
   // frame pair g of table entry it: test the two frames' bounding spheres
   auto frame_pair = [&](int it, int g) {
-    const uint32_t e = S.rp[it];
-    const int i = (int)(e & 15u), j = (int)((e >> 4) & 15u), nj = (int)((e >> 8) & 15u);
-    const int u = (g * (int)(e >> 16)) >> 12, v = g - u * nj;
+    const uint32_t e = S.rp[CK(it, WS::kRobots * (WS::kRobots - 1) / 2, PAIRTAB, C.err)];
+    const int i = CK((int)(e & 15u), n, PAIRTAB, C.err), j = CK((int)((e >> 4) & 15u), n, PAIRTAB, C.err);
+    const int nj = (int)((e >> 8) & 15u);
+    const int u = CK((g * (int)(e >> 16)) >> 12, S.rs[i].n_links, LINK, C.err);
+    const int v = CK(g - u * nj, nj, LINK, C.err);
     const int k = i * kMaxLinks + u, k2 = j * kMaxLinks + v;
     const float4 bu = S.BS[k], bv = S.BS[k2];
     if (bu.w < 0.f || bv.w < 0.f) return;
@@ -1806,7 +1857,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         }
         rs.w = R * (1.f + 1e-6f) + 1e-4f;
       }
-      cl.rsph[lane] = rs;
+      cl.rsph[CK(lane, WS::Cl::kCullR, ROBOT_CULL, C.err)] = rs;
     }
     __syncwarp();
     int nk = 0;
@@ -1820,7 +1871,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         acc.tests += 1;
       }
       const unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (keep) cl.kept[nk + __popc(m & ((1u << lane) - 1u))] = (int16_t)p;
+      if (keep) cl.kept[CK(nk + __popc(m & ((1u << lane) - 1u)), WS::Cl::kCullP, ROBOT_CULL, C.err)] = (int16_t)p;
       nk += __popc(m);
     }
     __syncwarp();
@@ -1872,11 +1923,13 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
     const int fe = min(f + per, base);
     if (f < fe) {
       for (int it = list_find(cl.pf, np, f); f < fe; ++it) {
-        const uint32_t v = cl.pc[it];
-        const int k = (int)(v >> 8), k2 = (int)(v & 0xffu);
+        const uint32_t v = cl.pc[CK(it, kCand, CAND, C.err)];
+        const int k = CK((int)(v >> 8), WS::kRobots * kMaxLinks, CAND, C.err);
+        const int k2 = CK((int)(v & 0xffu), WS::kRobots * kMaxLinks, CAND, C.err);
         const int ge = min(fe, cl.pf[it + 1]);
+        CK(frame_first(S, k) + (ge - cl.pf[it]) - 1, C.M, SPHERE, C.err);
         const float4 *Pk = P + frame_first(S, k) - cl.pf[it];
-        const int b0 = frame_first(S, k2), b1 = b0 + frame_count(S, k2);
+        const int b0 = frame_first(S, k2), b1 = CK(b0 + frame_count(S, k2), C.M + 1, SPHERE, C.err);
         acc.tests += (uint32_t)((ge - f) * (b1 - b0));
         bool h = false;
         for (; f < ge; ++f) {
@@ -1969,7 +2022,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
           float q[MRV_MAX_DOF];
           int lo;
           interp_from(B, rs.w0, rs.w1, rs.dof, t, S.seg[r], q, &lo);
-          chain_row(B.models[rs.mdl], q, xf + c * (kMaxLinks * 12), row);
+          chain_row(B.models[rs.mdl], q, xf + CK(c, WS::kChains, CHAIN, C.err) * (kMaxLinks * 12), row);
           if (row == 0) atomicMax(&S.seg[r], lo);
         }
       }
@@ -2008,14 +2061,14 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
       // sphere placement relative to the query origin, robot by robot
       float c2 = 0.f, cw2 = 0.f;
       for (int r = 0; r < n; ++r) {
-        const float *Xr = xf + ((j - j0) * n + r) * (kMaxLinks * 12);
+        const float *Xr = xf + CK((j - j0) * n + r, WS::kChains, CHAIN, C.err) * (kMaxLinks * 12);
         const float4 *sph = S.rs[r].spheres;
         const int32_t *lnk = S.rs[r].links;
-        const int m = S.rs[r].m, a0 = S.off[r];
+        const int m = S.rs[r].m, a0 = CK(S.off[r] + S.rs[r].m, C.M + 1, SPHERE, C.err) - S.rs[r].m;
 #pragma unroll 4
         for (int kk = lane; kk < m; kk += kWarp) {
           const float4 s = __ldg(&sph[kk]);
-          const float *X = Xr + __ldg(&lnk[kk]) * 12;
+          const float *X = Xr + CK(__ldg(&lnk[kk]), S.rs[r].n_links, LINK, C.err) * 12;
           const float wx = fmaf(X[0], s.x, fmaf(X[1], s.y, fmaf(X[2], s.z, X[3])));
           const float wy = fmaf(X[4], s.x, fmaf(X[5], s.y, fmaf(X[6], s.z, X[7])));
           const float wz = fmaf(X[8], s.x, fmaf(X[9], s.y, fmaf(X[10], s.z, X[11])));
@@ -2099,7 +2152,9 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   }
   TileCtx &C = S.ctx;   // kept in shared memory: read where used, not held in registers
   __syncwarp();
-  C.q = q; C.T = Q.T; C.n = Q.n; C.M = Q.M; C.nb = Q.ntiles;
+  C.err = B.err;
+  C.q = q; C.T = Q.T; C.n = CK(Q.n - 1, WS::kRobots, SLOTS, B.err) + 1;
+  C.M = CK(Q.M - 1, WS::kSpheres, SPHERE, B.err) + 1; C.nb = Q.ntiles;
   C.ffc = Q.bits & 1u;
   C.check_env = (!C.ffc) && (B.flags & MRV_CHECK_ENV);
   C.exhaustive = (B.flags & MRV_EXHAUSTIVE) ? 1 : 0;
@@ -2123,7 +2178,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   // stage the query's robots; origin of the relative frame = robot 0's base
   const int s0 = B.q_robot_off[q];
   if (lane < C.n) {
-    const int id = B.slot_robot_id[s0 + lane];
+    const int id = CK(B.slot_robot_id[CK(s0 + lane, B.n_slots, SLOTS, B.err)], B.n_models, SLOTS, B.err);
     const ModelDev &m = B.models[id];
     RobotSlot rs;
     rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects; rs.md = &m;
@@ -2157,12 +2212,13 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
         for (int j = i + 1; j < C.n; ++j, ++pi) {
           if (pf && (((__ldg(&adj[pi >> 5]) >> (pi & 31)) & 1u) != (pass == 0 ? 1u : 0u))) continue;
           const int nj = S.rs[j].n_links;
-          S.rp[p] = (uint32_t)(i | j << 4 | nj << 8) | ((uint32_t)((4096 + nj - 1) / nj) << 16);
-          S.rpf[p] = (int16_t)f;
+          const int pc = CK(p, WS::kRobots * (WS::kRobots - 1) / 2, PAIRTAB, B.err);
+          S.rp[pc] = (uint32_t)(i | j << 4 | nj << 8) | ((uint32_t)((4096 + nj - 1) / nj) << 16);
+          S.rpf[pc] = (int16_t)CK(f, 32768, PAIRTAB_PREFIX, B.err);
           f += S.rs[i].n_links * S.rs[j].n_links;
           ++p;
         }
-    S.rpf[p] = (int16_t)f;
+    S.rpf[CK(p, WS::kRobots * (WS::kRobots - 1) / 2 + 1, PAIRTAB, B.err)] = (int16_t)CK(f, 32768, PAIRTAB_PREFIX, B.err);
   }
   if (C.check_env && !(Q.bits & 2u)) {
     for (int o = lane; o < min(C.env_ns, kEnvCache); o += kWarp) {
@@ -2290,6 +2346,9 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
     if (lane == 0) {
       base = atomicAdd(&B.counters[cls ? 4 : 0], g);
       aborted = *(volatile int *)&B.counters[2];
+#ifdef MRV_CHECKED
+      aborted |= (*(volatile uint32_t *)B.err & kErrChecked) != 0u;   // stop at a failed index check
+#endif
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n_items) break;
@@ -2314,7 +2373,8 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
         else hi = mid - 1;
       }
       lvl = lo;
-      q = __ldg(&B.sorted[qbase + idx - __ldg(&level_start[lo])]);
+      q = __ldg(&B.sorted[CK(qbase + idx - __ldg(&level_start[lo]), B.n_queries, SORTED, B.err)]);
+      q = CK(q, B.n_queries, QUERY, B.err);
       if (!skip_dead) {
         live = true;
       } else {
@@ -2356,9 +2416,9 @@ __global__ void k_finish(BatchDev B, uint8_t *valid_out, float *minclr_out, mrv_
     if (key != 0x7fffffff && !(Q.bits & 4u)) {
       c.t = key >> kKeyShift;
       int p = key & ((1 << kKeyShift) - 1), i = 0;
-      while (p >= Q.n - 1 - i) { p -= Q.n - 1 - i; ++i; }
-      c.i = i;
-      c.j = i + 1 + p;
+      while (i < Q.n - 1 && p >= Q.n - 1 - i) { p -= Q.n - 1 - i; ++i; }
+      c.i = CK(i, Q.n, FINISH_PAIR, B.err);
+      c.j = CK(i + 1 + p, Q.n, FINISH_PAIR, B.err);
       atomicAdd(&counts[1], 1);
     }
     if (conf_out) conf_out[q] = c;
@@ -2410,8 +2470,8 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
     while (a >= off[r + 1]) ++r;
     const int i = a - off[r];
     const float4 s = rs[r].spheres[i];
-    const float *X = xf + r * kMaxLinks * 12 + rs[r].links[i] * 12;
-    P[a] = make_float4(fmaf(X[0], s.x, fmaf(X[1], s.y, fmaf(X[2], s.z, X[3]))),
+    const float *X = xf + r * kMaxLinks * 12 + CK(rs[r].links[i], kMaxLinks, LINK, B.err) * 12;
+    P[CK(a, MRV_MAX_QUERY_SPHERES, CLEAR_OUT, B.err)] = make_float4(fmaf(X[0], s.x, fmaf(X[1], s.y, fmaf(X[2], s.z, X[3]))),
                        fmaf(X[4], s.x, fmaf(X[5], s.y, fmaf(X[6], s.z, X[7]))),
                        fmaf(X[8], s.x, fmaf(X[9], s.y, fmaf(X[10], s.z, X[11]))), s.w);
   }
@@ -2433,13 +2493,14 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
       }
       const int li = a - off[r];
       for (int p = 0; p < rs[r].n_self; ++p) {
-        const int ex = (int)(rs[r].self[p] & 0xffffu), ey = (int)(rs[r].self[p] >> 16);
+        const int ex = CK((int)(rs[r].self[p] & 0xffffu), rs[r].m, CLEAR_OUT, B.err);
+        const int ey = CK((int)(rs[r].self[p] >> 16), rs[r].m, CLEAR_OUT, B.err);
         if (ex == li) m = fminf(m, sph_clr(pa, P[off[r] + ey]));
         else if (ey == li) m = fminf(m, sph_clr(pa, P[off[r] + ex]));
       }
     }
     // spheres are stored sorted by frame; the output keeps the caller's order
-    out[(size_t)k * Q.M + off[r] + rs[r].md->perm[a - off[r]]] = m;
+    out[(size_t)k * Q.M + off[r] + CK(rs[r].md->perm[a - off[r]], rs[r].m, CLEAR_OUT, B.err)] = m;
   }
 }
 

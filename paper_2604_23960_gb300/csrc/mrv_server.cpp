@@ -87,6 +87,7 @@ static size_t in_bytes_for(size_t nq, size_t ns, size_t nw, size_t stride, bool 
          64 * 8;
 }
 static size_t out_bytes_for(size_t nq) { return ((nq + 255) & ~size_t(255)) + sizeof(mrv_conflict) * nq + 64; }
+static_assert(sizeof(uint32_t) * kErrWords <= 64, "the error record fits the result staging's tail");
 
 }  // namespace mrv
 
@@ -209,7 +210,7 @@ void mrv_server::launch(Slot &s) {
     }
     if (e == cudaSuccess) {
       which = 2;
-      e = cudaMemcpyAsync(err_h, s.scratch.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream);
+      e = cudaMemcpyAsync(err_h, s.scratch.err, sizeof(uint32_t) * kErrWords, cudaMemcpyDeviceToHost, s.stream);
     }
     if (e != cudaSuccess) {
       // what the runtime knows about the buffers, for the error report
@@ -250,7 +251,7 @@ void mrv_server::complete(Slot &s) {
   if (!rc) {
     cudaError_t e = cudaEventQuery(s.done_ev);
     if (e != cudaSuccess) rc = cuda_fail(e, "micro-batch");
-    else if (*err_h) rc = check_device_err(*err_h);
+    else if (*err_h) rc = check_device_err(err_h);
     if (rc) msg = g_err;
   }
   float ms = 0.f;

@@ -25,12 +25,12 @@ static int batch_class(mrv_ctx *c, const mrv_batch *b, std::string *key) {
   cudaError_t e = S.reset(st);
   if (e == cudaSuccess) e = launch_prepare(B, st);
   std::vector<QueryDev> hq(b->n_queries);
-  uint32_t err = 0;
+  uint32_t err[kErrWords] = {};
   if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), S.q, sizeof(QueryDev) * hq.size(), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, S.err, sizeof err, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(err, S.err, sizeof err, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "autotune class");
-  if (err) return check_device_err(err);
+  if (err[0]) return check_device_err(err);
   std::vector<int> n, m, t;
   int ffc = 0;
   for (auto &q : hq) {

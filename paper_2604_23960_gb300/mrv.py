@@ -13,6 +13,7 @@ device pointers (torch CUDA tensors for device-resident batches).
 from __future__ import annotations
 
 import ctypes as C
+import os
 import threading
 from pathlib import Path
 from typing import Optional
@@ -21,7 +22,13 @@ import numpy as np
 
 from . import workloads as W
 
-LIB_PATH = Path(__file__).resolve().parent / "libmrv.so"
+# MRV_LIBRARY=checked loads the bounds-checked build of the same library
+# (libmrv_checked.so: every kernel index checked against its array, a failure
+# reported as MRV_ERR_CUDA naming the check); unset loads libmrv.so
+_LIBRARIES = {"": "libmrv.so", "checked": "libmrv_checked.so"}
+if os.environ.get("MRV_LIBRARY", "") not in _LIBRARIES:
+    raise ImportError(f"MRV_LIBRARY={os.environ['MRV_LIBRARY']!r}: expected one of {sorted(_LIBRARIES)}")
+LIB_PATH = Path(__file__).resolve().parent / _LIBRARIES[os.environ.get("MRV_LIBRARY", "")]
 
 MRV_OK = 0
 MRV_CHECK_ENV = 0x1

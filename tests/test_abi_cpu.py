@@ -94,3 +94,33 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(mrv, "_lib", None)
     with pytest.raises(ImportError):
         mrv.lib()
+
+
+def test_checked_library_exports_the_same_boundary(lib):
+    """The bounds-checked build (MRV_CHECKED kernels) is a drop-in library:
+    it loads, exports every declared entry point and fails cleanly too."""
+    from paper_2604_23960_gb300 import build
+    assert build.LIB_CHECKED.exists()
+    L = C.CDLL(str(build.LIB_CHECKED))
+    for name in declared_functions():
+        assert hasattr(L, name), f"{name} missing from the checked library"
+    L.mrv_last_error.restype = C.c_char_p
+    assert L.mv_validate(None, None, None, None) == -1
+
+
+def test_library_variant_is_selected_loudly(monkeypatch):
+    """MRV_LIBRARY picks the library variant; an unknown value is an error,
+    never a silent fallback."""
+    import importlib
+    import sys
+    monkeypatch.setenv("MRV_LIBRARY", "nonsense")
+    sys.modules.pop("paper_2604_23960_gb300.mrv", None)
+    with pytest.raises(ImportError):
+        importlib.import_module("paper_2604_23960_gb300.mrv")
+    monkeypatch.setenv("MRV_LIBRARY", "checked")
+    sys.modules.pop("paper_2604_23960_gb300.mrv", None)
+    m = importlib.import_module("paper_2604_23960_gb300.mrv")
+    assert m.LIB_PATH.name == "libmrv_checked.so"
+    monkeypatch.delenv("MRV_LIBRARY")
+    sys.modules.pop("paper_2604_23960_gb300.mrv", None)
+    assert importlib.import_module("paper_2604_23960_gb300.mrv").LIB_PATH.name == "libmrv.so"
