@@ -39,6 +39,33 @@ WORKLOAD = "ragged_teams_1m: 1M mixed MV/FFC queries (1/2 each) in one persisten
            "per robot, 8-512 steps per query (log-uniform)"
 CAGE_WORKLOAD = "cage_mv: MV, 4 Panda-like 7-DOF arms x 64 spheres, cage env 40 spheres + 12 boxes, " \
                 "10k start/goal joint-space motions, resolution 1/32 rad"
+# workloads the timed step can run (--workload; the default is the headline):
+# description, and the query kind when the batch holds one kind only
+STEP_WORKLOADS = {
+    "ragged_teams": (WORKLOAD, None),
+    "cage_mv": (CAGE_WORKLOAD, 0),
+    "cage_ffc": ("cage_ffc: FFC, the 4 arms on independent timed paths of 20-60 waypoints, 8-64 steps per "
+                 "segment", 1),
+    "cage16_ffc": ("cage16_ffc: FFC, the 16-arm Cage team (8 floor- and 8 ceiling-mounted arms) on whole "
+                   "motions between valid team configurations", 1),
+}
+
+
+def make_step_workload(name, n, rank):
+    """The timed step's batch: each rank its own seed (weak scaling)."""
+    from paper_2604_23960_gb300 import workloads as W
+    if name == "ragged_teams":
+        w = W.make_ragged_teams(n, seed=205 + rank)
+    elif name == "cage_mv":
+        w = W.make_cage_mv(n, query_seed=203 + rank)
+    elif name == "cage_ffc":
+        w = W.make_cage_ffc(n, query_seed=204 + rank)
+    else:
+        w = W.make_cage16_ffc(n, query_seed=210 + rank)
+    kind = STEP_WORKLOADS[name][1]
+    if kind is not None:
+        w.batch.q_kind = np.full(w.batch.n_queries, kind, np.uint8)
+    return w
 # FP32 flops per unit of work the kernel counts (FMA = 2):
 FLOPS_PER_TEST = 10     # sphere-sphere test: 3 sub, 1 mul + 2 fma, radius add + square
 FLOPS_PER_BOX = 13      # sphere-box test: per axis clamp + sub + fma, radius square
@@ -696,7 +723,7 @@ def run(args):
     fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     # weak scaling: every rank validates its own batch (distinct seeds), with
     # no collective on the data path
-    w = W.make_ragged_teams(args.queries, seed=205 + rank)
+    w = make_step_workload(args.workload, args.queries, rank)
     ba_host = ctx.bind(w)
     ba = ba_host.to("cuda")
     nq = w.batch.n_queries
@@ -775,7 +802,7 @@ def run(args):
     e2e_val = nq * world / (float(e2e_t.item()) / 1e3)
 
     strong = None
-    if world > 1:
+    if world > 1 and args.workload == "ragged_teams":
         with torch.cuda.stream(stream):
             strong = strong_scaling(ctx, nq, world, rank, host_group, flush)
         if rank == 0:
@@ -810,7 +837,8 @@ def run(args):
         "metric": METRIC, "value": value, "unit": "motion-checks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries_per_gpu": nq, "mv_queries": int(mvq.sum().item()),
+        "config": {"workload": STEP_WORKLOADS[args.workload][0], "queries_per_gpu": nq,
+                   "mv_queries": int(mvq.sum().item()),
                    "ffc_queries": int(ffq.sum().item()), "parallelism": f"replicas{world}",
                    "l2": "flushed before every timed step (512 MB write)",
                    "launch": "CUDA graph: reset + prepare + persistent work-stealing kernel instances + results",
@@ -870,6 +898,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mrv", choices=["mrv", "reference"])
     ap.add_argument("--queries", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="ragged_teams", choices=sorted(STEP_WORKLOADS),
+                    help="batch of the timed step (the default is the headline workload)")
     ap.add_argument("--per-query-n", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=2000)
