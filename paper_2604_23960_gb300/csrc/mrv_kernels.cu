@@ -76,8 +76,17 @@ __device__ __forceinline__ long long ck_idx(long long i, long long n, uint32_t s
   return 0;
 }
 #define CK(i, n, site, err) ((decltype(i))::mrv::ck_idx((long long)(i), (long long)(n), ::mrv::kCk_##site, (err)))
+// the half-open range [lo, hi) lies in 0..n-1 (an empty range always does)
+#define CK_RANGE(lo, hi, n, site, err)                  \
+  do {                                                  \
+    if ((hi) > (lo)) {                                  \
+      (void)CK((lo), (n), site, (err));                 \
+      (void)CK((hi) - 1, (n), site, (err));             \
+    }                                                   \
+  } while (0)
 #else
 #define CK(i, n, site, err) (i)
+#define CK_RANGE(lo, hi, n, site, err) ((void)0)
 #endif
 
 constexpr int kFlavorAMaxSpheres = 16;
@@ -999,8 +1008,8 @@ __device__ bool env_mv(const TileCtx &C, const WS &S, const float4 *P, const flo
     if (nr > 0) {
       for (int k = 0; k < nr; ++k) {
         const int4 R = __ldg(&S.rs[r].rects[k]);
-        CK(R.y - 1, S.rs[r].m, RECT, C.err);
-        CK(R.w - 1, S.rs[r].m, RECT, C.err);
+        CK_RANGE(R.x, R.y, S.rs[r].m, RECT, C.err);
+        CK_RANGE(R.z, R.w, S.rs[r].m, RECT, C.err);
         hit |= rect_test(P, o + R.x, o + R.y, P, K, o + R.z, o + R.w, 0.f, 0.f, 0.f, eps, lane);
       }
     } else {
@@ -1333,7 +1342,7 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WS &S, const uint32_t 
                        CAND, C.err);
       const int ge = min(fe, cl.pf[it + 1]);
       const int k = CK((int)(v >> 24), WS::kRobots * kMaxLinks, CAND, C.err);
-      CK(frame_first(S, k) + (ge - cl.pf[it]) - 1, C.M, SPHERE, C.err);
+      CK_RANGE(frame_first(S, k) + (f - cl.pf[it]), frame_first(S, k) + (ge - cl.pf[it]), C.M, SPHERE, C.err);
       const float4 *Pk = P + frame_first(S, k) - cl.pf[it];
       if (KIND == 0) {
         const float4 es = o < kEnvCache ? S.ES[o] : __ldg(&C.env_s[o]);
@@ -1390,9 +1399,9 @@ __device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int 
         const int4 Bk = __ldg(&S.rs[r].md->self_blocks[CK((int)(v & 0xffffu), S.rs[r].n_groups, SELF_BLOCK, C.err)]);
         const int o = S.off[r];
         c = Bk.z & 0xffff;
-        CK(o + Bk.x + c - 1, min(C.M, 1024), SELF_BLOCK, C.err);
-        CK(o + Bk.y + ((Bk.z >> 16) & 0xff) - 1, min(C.M, 1024), SELF_BLOCK, C.err);
-        CK(Bk.w + c - 1, min(S.rs[r].md->n_masks, 65536), SELF_MASK, C.err);
+        CK_RANGE(o + Bk.x, o + Bk.x + c, min(C.M, 1024), SELF_BLOCK, C.err);
+        CK_RANGE(o + Bk.y, o + Bk.y + ((Bk.z >> 16) & 0xff), min(C.M, 1024), SELF_BLOCK, C.err);
+        CK_RANGE(Bk.w, Bk.w + c, min(S.rs[r].md->n_masks, 65536), SELF_MASK, C.err);
         cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 10) | ((uint32_t)r << 20);
         cl.scn[i] = (uint16_t)Bk.w;
         cl.sck[i] = (uint8_t)(r * kMaxLinks + CK((Bk.z >> 24) & 15, S.rs[r].n_links, SELF_BLOCK, C.err));
@@ -1447,7 +1456,8 @@ __device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int 
         const int ge = min(fe, cl.pf[it + 1]);
         const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
         const float4 *Pr = P + S.off[r];
-        CK((int)(v & 0xffffu) + (ge - cl.pf[it]) - 1, (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err);
+        CK_RANGE((int)(v & 0xffffu) + (f - cl.pf[it]), (int)(v & 0xffffu) + (ge - cl.pf[it]),
+                 (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err);
 #pragma unroll 4
         for (; f < ge; ++f) {
           const uint32_t e = __ldg(&pr[f]);
@@ -1518,7 +1528,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           acc.tests += (uint32_t)(i1 - i0);
           acc.boxes += (uint32_t)(ib - is);
           acc.cyls += (uint32_t)(i1 - ib);
-          CK(i1 - 1, E.g_nitems, GRID_ITEM, C.err);
+          CK_RANGE(i0, i1, E.g_nitems, GRID_ITEM, C.err);
           for (int i = i0; i < is; ++i) {
             const int e = CK((int)__ldg(&E.g_items[i]), env_ns, OBST_SPHERE, C.err);
             const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
@@ -1730,9 +1740,9 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
               const int4 Bk = __ldg(&S.rs[r].md->self_blocks[CK((int)(v & 0xffffu), S.rs[r].n_groups, SELF_BLOCK, C.err)]);
               const int o = S.off[r];
               c = Bk.z & 0xffff;
-              CK(o + Bk.x + c - 1, min(C.M, 1024), SELF_BLOCK, C.err);
-              CK(o + Bk.y + ((Bk.z >> 16) & 0xff) - 1, min(C.M, 1024), SELF_BLOCK, C.err);
-              CK(Bk.w + c - 1, min(S.rs[r].md->n_masks, 65536), SELF_MASK, C.err);
+              CK_RANGE(o + Bk.x, o + Bk.x + c, min(C.M, 1024), SELF_BLOCK, C.err);
+              CK_RANGE(o + Bk.y, o + Bk.y + ((Bk.z >> 16) & 0xff), min(C.M, 1024), SELF_BLOCK, C.err);
+              CK_RANGE(Bk.w, Bk.w + c, min(S.rs[r].md->n_masks, 65536), SELF_MASK, C.err);
               cl.sc[i] = (uint32_t)(o + Bk.x) | ((uint32_t)(o + Bk.y) << 10) | ((uint32_t)r << 20);
               cl.scn[i] = (uint16_t)Bk.w;
               cl.sck[i] = (uint8_t)(r * kMaxLinks + CK((Bk.z >> 24) & 15, S.rs[r].n_links, SELF_BLOCK, C.err));
@@ -1787,7 +1797,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
               const int ge = min(fe, cl.pf[it + 1]);
               const uint32_t *pr = S.rs[r].self + (int)(v & 0xffffu) - cl.pf[it];
               const float4 *Pr = P + S.off[r];
-              CK((int)(v & 0xffffu) + (ge - cl.pf[it]) - 1, (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err);
+              CK_RANGE((int)(v & 0xffffu) + (f - cl.pf[it]), (int)(v & 0xffffu) + (ge - cl.pf[it]),
+                 (S.rs[r].n_self + 3) & ~3, SELF_PAIR, C.err);
 #pragma unroll 4
               for (; f < ge; ++f) {
                 const uint32_t e = __ldg(&pr[f]);
@@ -1927,7 +1938,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         const int k = CK((int)(v >> 8), WS::kRobots * kMaxLinks, CAND, C.err);
         const int k2 = CK((int)(v & 0xffu), WS::kRobots * kMaxLinks, CAND, C.err);
         const int ge = min(fe, cl.pf[it + 1]);
-        CK(frame_first(S, k) + (ge - cl.pf[it]) - 1, C.M, SPHERE, C.err);
+        CK_RANGE(frame_first(S, k) + (f - cl.pf[it]), frame_first(S, k) + (ge - cl.pf[it]), C.M, SPHERE, C.err);
         const float4 *Pk = P + frame_first(S, k) - cl.pf[it];
         const int b0 = frame_first(S, k2), b1 = CK(b0 + frame_count(S, k2), C.M + 1, SPHERE, C.err);
         acc.tests += (uint32_t)((ge - f) * (b1 - b0));
