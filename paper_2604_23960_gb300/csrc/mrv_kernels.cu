@@ -75,7 +75,7 @@ __device__ __forceinline__ long long ck_idx(long long i, long long n, uint32_t s
   ck_fail(err, site, i, n);
   return 0;
 }
-#define CK(i, n, site, err) ((decltype(i))::mrv::ck_idx((long long)(i), (long long)(n), ::mrv::kCk_##site, (err)))
+#define CK(i, n, site, err) ((decltype((i) + 0))::mrv::ck_idx((long long)(i), (long long)(n), ::mrv::kCk_##site, (err)))
 // the half-open range [lo, hi) lies in 0..n-1 (an empty range always does)
 #define CK_RANGE(lo, hi, n, site, err)                  \
   do {                                                  \
