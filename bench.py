@@ -846,7 +846,7 @@ def run(args):
                    "tuning": tuning},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic_per_launch(),
-                     "kernel": "k_main (persistent MV/FFC kernel, team layout), early exit, frame-level broadphase",
+                     "kernel": "k_main (persistent MV/FFC kernel, small-team layout), early exit, frame-level broadphase",
                      "work": "the method's dense FP32 work on the states checked, from the kernel's counters: "
                              f"{FLOPS_PER_TEST} flops per sphere-sphere test (robot-robot, obstacle, self), "
                              f"{FLOPS_PER_BOX} per sphere-box test, {FLOPS_PER_JOINT} per joint and "
@@ -869,9 +869,10 @@ def run(args):
         "valid_mv": f"{nvalid}/{int(mvq.sum().item())}",
         "conflicts_ffc": f"{nconf}/{int(ffq.sum().item())}",
         "kernel_ms_mean": kms,
-        # per graph step: k_prep, k_levels, k_scatter, the team k_main, the
-        # large-team k_main (forked beside it; no work item on this batch), k_finish
-        "gpu_launches": 6 * args.steps,
+        # per graph step: k_prep, k_levels, k_scatter, the small-team k_main,
+        # the team and large-team k_main instances (forked beside it; no work
+        # item on this batch), k_finish
+        "gpu_launches": 7 * args.steps,
         "clocks": clocks,
     }
     if strong is not None:

@@ -79,7 +79,7 @@ size_t Scratch::layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char 
   set(&hist, sizeof(int32_t) * kLevelBins);
   set(&level_start, sizeof(int32_t) * kLevelBins);
   set(&cursor, sizeof(int32_t) * kLevelBins);
-  set(&counters, sizeof(int32_t) * 8);
+  set(&counters, sizeof(int32_t) * kNumCounters);
   set(&err, sizeof(uint32_t) * kErrWords);
   set(&stats, sizeof(unsigned long long) * kNumStats);
   set(&counts, sizeof(int32_t) * 4);
@@ -169,28 +169,29 @@ int validate_batch(mrv_ctx *ctx, const mrv_batch *b) {
   return MRV_OK;
 }
 
-// Whether a batch may hold queries of work class 1 (more than kTeamRobots
-// robots or kTeamSpheres spheres), whose kernel instance is then launched too.
-// Host batches are scanned (robots per query first; sphere sums only when the
-// largest model could exceed the bound); device batches may hold any.
-static int maybe_large(const mrv_ctx *ctx, const mrv_batch *b) {
-  if (b->flags & MRV_PTRS_ON_DEVICE) return 1;
+// The work classes a batch may hold (bit c: class c, whose kernel instance
+// is then launched).  Host batches are scanned (robots per query first;
+// sphere sums only when the largest model could exceed a class bound);
+// device batches may hold any.
+static int batch_classes(const mrv_ctx *ctx, const mrv_batch *b) {
+  if (b->flags & MRV_PTRS_ON_DEVICE) return (1 << kNumClasses) - 1;
   int n_max = 0;
   for (int q = 0; q < b->n_queries; ++q) n_max = std::max(n_max, b->q_robot_off[q + 1] - b->q_robot_off[q]);
-  if (n_max > kTeamRobots) return 1;
   int m_max = 0;
   for (const auto &m : ctx->models) m_max = std::max(m_max, m.dev.n_spheres);
-  if (n_max * m_max <= kTeamSpheres) return 0;
+  if (work_class(n_max, n_max * m_max) == 0) return 1;
   const int n_models = (int)ctx->models.size();
+  int mask = 0;
   for (int q = 0; q < b->n_queries; ++q) {
     int M = 0;
+    const int n = b->q_robot_off[q + 1] - b->q_robot_off[q];
     for (int s = b->q_robot_off[q]; s < b->q_robot_off[q + 1]; ++s) {
       const int id = b->slot_robot_id[s];
       if (id >= 0 && id < n_models) M += ctx->models[id].dev.n_spheres;
     }
-    if (M > kTeamSpheres) return 1;
+    mask |= 1 << work_class(n, M);
   }
-  return 0;
+  return mask | 1;
 }
 
 BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int slices_per_item) {
@@ -232,7 +233,7 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
   B.envs = ctx->d_envs;
   B.n_envs = (int32_t)ctx->envs.size();
   B.clock_budget = ctx->clock_budget;
-  B.maybe_large = b->n_queries > 0 ? maybe_large(ctx, b) : 0;
+  B.classes = b->n_queries > 0 ? batch_classes(ctx, b) : 1;
   return B;
 }
 
@@ -266,7 +267,7 @@ cudaError_t Scratch::reset(cudaStream_t st) const {
                           b - a < (1 << 16);
   if (contiguous) return cudaMemsetAsync(hist, 0, (size_t)(b - a), st);
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * kLevelBins, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * kNumCounters, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t) * kErrWords, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kNumStats, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * 4, st);
@@ -275,7 +276,8 @@ cudaError_t Scratch::reset(cudaStream_t st) const {
 
 int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
   // the occupancy of a kernel configuration does not change: queried once
-  int *slot = (warps >= 1 && warps <= 12) ? &ctx->occ[clr ? 1 : 0][cls ? 1 : 0][warps] : nullptr;
+  int *slot = (warps >= 1 && warps <= 12 && cls >= 0 && cls < kNumClasses) ? &ctx->occ[clr ? 1 : 0][cls][warps]
+                                                                         : nullptr;
   int occ = slot ? *slot : 0;
   if (occ < 1) {
     if (max_blocks_per_sm(warps, clr, cls, &occ) != cudaSuccess || occ < 1) {
@@ -310,18 +312,26 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return cuda_fail(e, "capture status");
   const unsigned rec_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev0 && (e = cudaEventRecordWithFlags(ev0, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
-  // queries beyond the team layout: the large-team instance, beside the team
-  // one on the fork's stream (after it on this stream without a fork)
-  const bool side = B.maybe_large && fk && fk->aux;
+  // the small-team instance on this stream; the team and large-team
+  // instances, when the batch may hold their queries, on the fork's stream
+  // beside it (after it on this stream without a fork)
+  const int more = B.classes & ~1;
+  const bool side = more && fk && fk->aux;
   if (side && (e = cudaEventRecord(fk->fork, st)) != cudaSuccess) return cuda_fail(e, "fork event");
   e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm, 0), warps, clr, 0, -1, st);
   if (e != cudaSuccess) return cuda_fail(e, "main launch");
-  if (B.maybe_large) {
-    const int lw = large_warps();
+  if (more) {
     cudaStream_t ls = side ? fk->aux : st;
     if (side && (e = cudaStreamWaitEvent(ls, fk->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
-    e = launch_main(B, grid_for(ctx, lw, clr, 0, 1), lw, clr, 1, -1, ls);
-    if (e != cudaSuccess) return cuda_fail(e, "large-team launch");
+    if (B.classes & 2) {
+      e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm, 1), warps, clr, 1, -1, ls);
+      if (e != cudaSuccess) return cuda_fail(e, "team launch");
+    }
+    if (B.classes & 4) {
+      const int lw = large_warps();
+      e = launch_main(B, grid_for(ctx, lw, clr, 0, 2), lw, clr, 2, -1, ls);
+      if (e != cudaSuccess) return cuda_fail(e, "large-team launch");
+    }
     if (side && ((e = cudaEventRecord(fk->join, ls)) != cudaSuccess || (e = cudaStreamWaitEvent(st, fk->join, 0)) != cudaSuccess))
       return cuda_fail(e, "join");
   }
@@ -445,7 +455,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
     cudaEventRecord(ctx->ev0, st);
     for (int q = 0; q < b->n_queries; ++q) {
       if (hq[q].bits & 4u || hq[q].nchunks == 0) continue;
-      const int cls = (hq[q].bits & 8u) ? 1 : 0;
+      const int cls = (int)((hq[q].bits >> 3) & 3u);
       if ((e = launch_main(B, hq[q].nchunks, 1, clr, cls, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "query synchronize");
     }
@@ -986,7 +996,8 @@ int mrv_graph_create(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_con
   // attributes are set outside the capture
   set_main_attrs(c->tuning.warps_per_block);
   grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm, 0);
-  grid_for(c, large_warps(), false, 0, 1);
+  grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm, 1);
+  grid_for(c, large_warps(), false, 0, 2);
   cudaStream_t cap = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {

@@ -12,6 +12,13 @@
 
 #include "../../include/mrv.h"
 
+// functions used by both the host runtime (g++) and the kernels (nvcc)
+#ifdef __CUDACC__
+#define MRV_HD __host__ __device__
+#else
+#define MRV_HD
+#endif
+
 namespace mrv {
 
 constexpr int kWarp = 32;             // lanes per tile (the GPU's batch width W)
@@ -19,14 +26,30 @@ constexpr int kMaxLinks = MRV_MAX_DOF + 2;  // frames 0..dof+1
 constexpr int kMaxLevels = 256;       // work levels (work items per query)
 constexpr int kEnvIdBase = 1 << 20;   // env ids = kEnvIdBase + env slot
 constexpr int kFkChains = 8;          // (state, robot) chains per FK round
-// Queries of up to kTeamRobots robots and kTeamSpheres spheres form work
-// class 0 (the team kernel layout); larger ones, up to MRV_MAX_ROBOTS and
-// MRV_MAX_QUERY_SPHERES, work class 1 (the large-team layout).  Each class has
-// its own work levels: kLevelBins = 2 x (kMaxLevels + 1) histogram, cursor
-// and level-start bins.
+// Work classes, one persistent-kernel instance (per-warp shared-memory
+// layout) each: class 0 (small teams) up to kTeamRobots robots and
+// kSmallSpheres spheres, 16 warps per SM; class 1 (teams) up to kTeamRobots
+// robots and kTeamSpheres spheres, 12 warps per SM; class 2 (large teams) up
+// to MRV_MAX_ROBOTS robots and MRV_MAX_QUERY_SPHERES spheres.  Each class has
+// its own work levels (kMaxLevels + 1 histogram, cursor and level-start bins)
+// and its own counters (kCtrClaim, kCtrItems, kCtrFirst).
 constexpr int kTeamRobots = 8;
+constexpr int kSmallSpheres = 256;
 constexpr int kTeamSpheres = 512;
-constexpr int kLevelBins = 2 * (kMaxLevels + 1);
+constexpr int kNumClasses = 3;
+constexpr int kLevelBins = kNumClasses * (kMaxLevels + 1);
+// BatchDev::counters: [2] abort flag; per class c the claim counter, the
+// number of work items and the first sorted position of its queries
+constexpr int kCtrAbort = 2;
+constexpr int kNumCounters = 16;
+MRV_HD constexpr int kCtrClaim(int c) { return 4 + 3 * c; }
+MRV_HD constexpr int kCtrItems(int c) { return 5 + 3 * c; }
+MRV_HD constexpr int kCtrFirst(int c) { return 6 + 3 * c; }
+static_assert(kCtrFirst(kNumClasses - 1) < kNumCounters, "counters fit");
+// work class of a query with n robots and M spheres
+MRV_HD constexpr int work_class(int n, int M) {
+  return (n > kTeamRobots || M > kTeamSpheres) ? 2 : (M > kSmallSpheres ? 1 : 0);
+}
 constexpr int kNumStats = 15;         // statistics counters of a call (see mrv_stats)
 
 // device error bits (BatchDev::err)
@@ -163,7 +186,7 @@ struct QueryDev {
   int32_t cte;        // slices per work item
   int32_t env;        // env slot or -1
   uint32_t bits;      // bit 0: FFC, bit 1: flavor A (lane = state), bit 2: invalid,
-                      // bit 3: work class 1 (more than kTeamRobots robots or kTeamSpheres spheres)
+                      // bits 3-4: work class (work_class)
   float rho2;         // largest squared sphere radius of the query's robots
   int32_t nadj;       // pairs-first MV: adjacent robot pairs (0: the order is off)
   int32_t nchain;     // robots that are kinematic chains (one FK chain per state each)
@@ -203,9 +226,8 @@ struct BatchDev {
   int32_t *hist;                     // kLevelBins bins (class 0, then class 1)
   int32_t *level_start;              // kLevelBins
   int32_t *cursor;                   // kLevelBins
-  int32_t *counters;                 // [0] class-0 work counter, [1] class-0 items, [2] abort flag,
-                                     // [3] class-1 items, [4] class-1 work counter,
-                                     // [5] class-0 queries (first sorted position of class 1)
+  int32_t *counters;                 // kNumCounters: the abort flag and per-class claim
+                                     // counter, items and first sorted position (kCtr*)
   uint32_t *err;                     // kErrWords: error bits, check site, index, extent
   unsigned long long *stats;         // [0] states checked, [1] tests executed,
                                      // [2] states available, [3] tests available,
@@ -224,7 +246,7 @@ struct BatchDev {
   const EnvDev *envs;
   int32_t n_envs;
   long long clock_budget;            // persistent kernel: clock64 ticks (0 = none)
-  int32_t maybe_large;               // host: the batch may hold class-1 queries (launch their kernel)
+  int32_t classes;                   // host: bit c = the batch may hold class-c queries (launch its kernel)
   int32_t pad1;
 };
 

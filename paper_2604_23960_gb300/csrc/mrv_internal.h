@@ -103,7 +103,7 @@ struct Fork {
 };
 
 // kernel launch wrappers (mrv_kernels.cu)
-size_t main_smem_bytes(int warps, int cls);   // cls: work class (0 team, 1 large team)
+size_t main_smem_bytes(int warps, int cls);   // cls: work class (0 small team, 1 team, 2 large team)
 int large_warps();                             // warps per block of the large-team instance
 cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st);
 cudaError_t set_main_attrs(int warps);
@@ -132,7 +132,7 @@ struct mrv_ctx {
   long long clock_budget = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   mrv::Fork fork;               // second stream of the large-team instance
-  int occ[2][2][13] = {};       // resident blocks per SM by [clearance][class][warps] (0: not queried yet)
+  int occ[2][mrv::kNumClasses][13] = {};   // resident blocks per SM by [clearance][class][warps] (0: not queried yet)
   void *h_pinned = nullptr;
   uint32_t *h_status = nullptr;
   unsigned long long *h_stats = nullptr;

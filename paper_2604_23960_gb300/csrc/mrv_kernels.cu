@@ -161,17 +161,19 @@ struct Cands {
   int32_t keptf[kCullP + 1];
 };
 
-constexpr int kEnvCache = 64;    // obstacle spheres staged per warp (more: read from L1)
-constexpr int kBoxCache = 32;    // obstacle boxes staged per warp
-
 // Per-warp shared memory of the persistent kernel for queries of up to NR
-// robots and MQ spheres.  Two layouts are instantiated: the team layout (8
-// robots, 512 spheres), sized so that 12 warps share an SM, and the
-// large-team layout (16 robots, 1024 spheres) of a second kernel instance
-// that takes the queries beyond the first (work class 1).
+// robots and MQ spheres.  Three layouts are instantiated, one per work class:
+// small teams (8 robots, 256 spheres; 16 warps share an SM), teams (8 robots,
+// 512 spheres; 12 warps) and large teams (16 robots, 1024 spheres).  Obstacles
+// are read through L1 (a per-warp copy of the first obstacles measured the
+// same and cost 2.3 KB of every warp's shared memory).
 template <int NR, int MQ>
 struct WarpSmemT {
-  static constexpr int kRobots = NR, kSpheres = MQ, kClass = NR > kTeamRobots ? 1 : 0;
+  static constexpr int kRobots = NR, kSpheres = MQ;
+  static constexpr int kClass = work_class(NR, MQ);
+  static constexpr bool kLarge = kClass == 2;   // robot-level cull, self groups in batches
+  // threads per SM the instance is compiled for (the register budget)
+  static constexpr int kMaxThreads = kClass == 0 ? 512 : 384;
   static constexpr int kChains = NR > kFkChains ? NR : kFkChains;   // FK chains held at once
   using Cl = Cands<NR>;
   TileCtx ctx;               // the current work item's query parameters
@@ -181,9 +183,6 @@ struct WarpSmemT {
                              // latest FK round (states grow within a slice)
   float ox, oy, oz;          // origin of the relative frame (world)
   int32_t pad[4];
-  float4 ES[kEnvCache];      // obstacle spheres of the query's env (world)
-  float EK[kEnvCache];       // their |c|^2 - r^2
-  float4 BL[kBoxCache], BH[kBoxCache];   // obstacle boxes
   // robot pairs i < j of the query, i | j << 4 | n_links_j << 8 | m << 16
   // with m = ceil(4096 / n_links_j) (frame pair g of the pair is (g m >> 12,
   // g mod n_links_j), exact for g < 100), and the exclusive prefix of their
@@ -203,15 +202,18 @@ struct WarpSmemT {
     } b;
     float4 PA[kFlavorAMaxSpheres * kWarp];  // flavor A: world centers per lane
   } u;
-  static_assert(sizeof(Cl) <= sizeof(float) * MQ, "candidate lists fit the K array");
   static_assert(NR <= 16 && NR * kMaxLinks < 256, "robot and frame-slot indices fit their fields");
 };
+using WarpSmemSmall = WarpSmemT<kTeamRobots, kSmallSpheres>;
 using WarpSmemTeam = WarpSmemT<kTeamRobots, kTeamSpheres>;
 using WarpSmemLarge = WarpSmemT<MRV_MAX_ROBOTS, MRV_MAX_QUERY_SPHERES>;
+static_assert(WarpSmemSmall::kClass == 0 && WarpSmemTeam::kClass == 1 && WarpSmemLarge::kClass == 2, "classes");
 
 template <class WS>
 __host__ __device__ constexpr size_t warp_smem_bytes() { return (sizeof(WS) + 15) & ~size_t(15); }
-// team layout: 12 warps (3 blocks of 4) must fit the SM's 228 KB with 1 KB reserved per block
+// small-team layout: 16 warps (4 blocks of 4) must fit the SM's 228 KB with 1 KB reserved per block
+static_assert(16 * warp_smem_bytes<WarpSmemSmall>() + 4 * 1024 <= 233472, "shared memory per warp");
+// team layout: 12 warps (3 blocks of 4)
 static_assert(12 * warp_smem_bytes<WarpSmemTeam>() + 3 * 1024 <= 233472, "shared memory per warp");
 // large-team layout: blocks of kLargeWarps warps, one per SM
 constexpr int kLargeWarps = (int)((233472 - 1024) / warp_smem_bytes<WarpSmemLarge>()) > 8
@@ -377,7 +379,7 @@ __global__ void k_prep(BatchDev B) {
     Q.rho2 = rho2;
     const bool flavor_a = all_point && M <= kFlavorAMaxSpheres;
     if (flavor_a) Q.bits |= 2u;
-    if (n > kTeamRobots || M > kTeamSpheres) Q.bits |= 8u;   // large-team kernel
+    Q.bits |= (uint32_t)work_class(n, M) << 3;
     const bool mv = !(Q.bits & 1u);
     const bool check_env = mv && (B.flags & MRV_CHECK_ENV);
     Q.ntiles = (int)((T + 1 + kWarp - 1) / kWarp);
@@ -429,12 +431,13 @@ __global__ void k_prep(BatchDev B) {
   B.q_hit[q] = 0;
   B.q_best[q] = 0x7fffffff;
   B.q_minclr[q] = __int_as_float(f2ord(INFINITY));
-  atomicAdd(&B.hist[CK(((Q.bits & 8u) ? kMaxLevels + 1 : 0) + (Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks),
+  atomicAdd(&B.hist[CK((int)((Q.bits >> 3) & 3u) * (kMaxLevels + 1) + (Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks),
                        kLevelBins, HIST, B.err)], 1);
 }
 
 // level layout, per work class: the class's queries sorted by item count
-// (descending), class 0 first; level c holds the class's queries with more
+// (descending), classes in order (qbase: the queries of the classes before);
+// level c holds the class's queries with more
 // than c items, which are its first cnt_c sorted queries.  With h the class's
 // histogram of item counts (bin kMaxLevels: that many or more) and
 // S[k] = sum_{k' >= k} h[k'], the first sorted position of item count k is
@@ -467,14 +470,16 @@ __global__ void __launch_bounds__(kLevelThreads) k_levels(BatchDev B) {
   if (t < kLevelBins) pre[t] = S1;
   __syncthreads();
   seg_scan(pre, t, L);
-  const int n0 = suf[kMaxLevels];   // S[0] of class 0: its queries
   if (t < kLevelBins) {
-    const int qbase = cls ? n0 : 0;
+    int qbase = 0;   // S[0] of each class before this one: its queries
+    for (int c = 0; c < cls; ++c) qbase += suf[c * L + kMaxLevels];
     B.cursor[t] = qbase + S1;
     if (k < kMaxLevels) B.level_start[CK(cls * L + k + 1, kLevelBins, LEVELS, B.err)] = pre[t];
-    if (k == 0) B.level_start[cls * L] = 0;
-    if (k == kMaxLevels - 1) B.counters[cls ? 3 : 1] = pre[t];   // the class's work items
-    if (t == 0) B.counters[5] = n0;
+    if (k == 0) {
+      B.level_start[cls * L] = 0;
+      B.counters[kCtrFirst(cls)] = qbase;
+    }
+    if (k == kMaxLevels - 1) B.counters[kCtrItems(cls)] = pre[t];   // the class's work items
   }
 }
 
@@ -484,7 +489,7 @@ __global__ void k_scatter(BatchDev B) {
   const QueryDev &Q = B.q[q];
   int c = Q.nchunks;
   if (c > kMaxLevels) c = kMaxLevels;
-  const int pos = atomicAdd(&B.cursor[((Q.bits & 8u) ? kMaxLevels + 1 : 0) + c], 1);
+  const int pos = atomicAdd(&B.cursor[(int)((Q.bits >> 3) & 3u) * (kMaxLevels + 1) + c], 1);
   B.sorted[CK(pos, B.n_queries, SCATTER, B.err)] = q;
 }
 
@@ -988,14 +993,10 @@ __device__ bool env_mv(const TileCtx &C, const WS &S, const float4 *P, const flo
   bool hit = false;
   if (C.env_ns) {
     const float epsw = kEpsU * (fmaxf(cw2, C.env_c2) + fmaxf(C.rho2, C.env_r2));
-    const int ns_c = min(C.env_ns, kEnvCache);
-    hit |= rect_test(P, 0, M, S.ES, S.EK, 0, ns_c, S.ox, S.oy, S.oz, epsw, lane);
-    if (C.env_ns > ns_c) hit |= rect_test(P, 0, M, C.env_s, C.env_k, ns_c, C.env_ns, S.ox, S.oy, S.oz, epsw, lane);
+    hit |= rect_test(P, 0, M, C.env_s, C.env_k, 0, C.env_ns, S.ox, S.oy, S.oz, epsw, lane);
   }
   if (C.env_nb) {
-    const int nb_c = min(C.env_nb, kBoxCache);
-    hit |= box_rows(P, 0, M, S.BL, S.BH, nb_c, S.ox, S.oy, S.oz, lane);
-    if (C.env_nb > nb_c) hit |= box_rows(P, 0, M, C.box_lo + nb_c, C.box_hi + nb_c, C.env_nb - nb_c, S.ox, S.oy, S.oz, lane);
+    hit |= box_rows(P, 0, M, C.box_lo, C.box_hi, C.env_nb, S.ox, S.oy, S.oz, lane);
   }
   for (int a = lane; a < M && C.env_nc; a += kWarp) {   // cylinders: one row per lane
     const float4 p = P[a];
@@ -1110,7 +1111,6 @@ __device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int la
                           unsigned long long &nbox, unsigned long long &ncyl) {
   bool hit = false;
   const int nk = C.self_robots * kMaxLinks;   // frames of the robots with obstacle checks
-  const int ns_c = min(C.env_ns, kEnvCache), nb_c = min(C.env_nb, kBoxCache);
   for (int k0 = 0; k0 < nk; k0 += kWarp) {
     const int k = k0 + lane;
     const float4 bl = k < nk ? S.BS[k] : make_float4(0.f, 0.f, 0.f, -1.f);
@@ -1119,7 +1119,7 @@ __device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int la
     const int a0 = S.off[r] + S.rs[r].ls[l], a1 = CK(S.off[r] + S.rs[r].ls[l + 1], C.M + 1, SPHERE, C.err);
     const float4 bw = make_float4(bl.x + S.ox, bl.y + S.oy, bl.z + S.oz, bl.w);
     for (int e = 0; e < C.env_ns; ++e) {
-      const float4 es = e < ns_c ? S.ES[e] : __ldg(&C.env_s[e]);
+      const float4 es = __ldg(&C.env_s[e]);
       ntests += 1;
       if (!sph_hit(bw, es)) continue;
       for (int a = a0; a < a1; ++a) {
@@ -1130,8 +1130,8 @@ __device__ bool env_broad(const TileCtx &C, const WS &S, const float4 *P, int la
     }
     const float rr = bw.w * bw.w;
     for (int b = 0; b < C.env_nb; ++b) {
-      const float4 lo = b < nb_c ? S.BL[b] : __ldg(&C.box_lo[b]);
-      const float4 hi = b < nb_c ? S.BH[b] : __ldg(&C.box_hi[b]);
+      const float4 lo = __ldg(&C.box_lo[b]);
+      const float4 hi = __ldg(&C.box_hi[b]);
       ntests += 1;
       nbox += 1;
       if (!(box_d2(bw.x, bw.y, bw.z, lo, hi) < rr)) continue;
@@ -1345,7 +1345,7 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WS &S, const uint32_t 
       CK_RANGE(frame_first(S, k) + (f - cl.pf[it]), frame_first(S, k) + (ge - cl.pf[it]), C.M, SPHERE, C.err);
       const float4 *Pk = P + frame_first(S, k) - cl.pf[it];
       if (KIND == 0) {
-        const float4 es = o < kEnvCache ? S.ES[o] : __ldg(&C.env_s[o]);
+        const float4 es = __ldg(&C.env_s[o]);
 #pragma unroll 4
         for (; f < ge; ++f) {
           const float4 p = Pk[f];
@@ -1358,8 +1358,8 @@ __device__ bool resolve_obstacles(const TileCtx &C, const WS &S, const uint32_t 
           hit |= cyl_d2(p.x + ox, p.y + oy, p.z + oz, A, U) < p.w * p.w;
         }
       } else {
-        const float4 lo = o < kBoxCache ? S.BL[o] : __ldg(&C.box_lo[o]);
-        const float4 hi = o < kBoxCache ? S.BH[o] : __ldg(&C.box_hi[o]);
+        const float4 lo = __ldg(&C.box_lo[o]);
+        const float4 hi = __ldg(&C.box_hi[o]);
 #pragma unroll 4
         for (; f < ge; ++f) {
           const float4 p = Pk[f];
@@ -1495,7 +1495,6 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   bool hit = false;
   if (need_env) {
     const int env_ns = C.env_ns, env_nb = C.env_nb;
-    const int ns_c = min(env_ns, kEnvCache), nb_c = min(env_nb, kBoxCache);
     const float4 *env_s = C.env_s, *box_lo = C.box_lo, *box_hi = C.box_hi;
     const float ox = S.ox, oy = S.oy, oz = S.oz;
     const float gR = C.env ? C.env->g_R : -1.f;
@@ -1531,7 +1530,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           CK_RANGE(i0, i1, E.g_nitems, GRID_ITEM, C.err);
           for (int i = i0; i < is; ++i) {
             const int e = CK((int)__ldg(&E.g_items[i]), env_ns, OBST_SPHERE, C.err);
-            const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
+            const float4 es = __ldg(&env_s[e]);
             if (sph_hit(bw, es)) {
               push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
               nd = true;
@@ -1540,8 +1539,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           const float rr = bw.w * bw.w;
           for (int i = is; i < ib; ++i) {
             const int b = CK((int)__ldg(&E.g_items[i]), env_nb, OBST_BOX, C.err);
-            const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
-            const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
+            const float4 lo = __ldg(&box_lo[b]);
+            const float4 hi = __ldg(&box_hi[b]);
             if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
               push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
               nd = true;
@@ -1559,7 +1558,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           acc.boxes += (uint32_t)env_nb;
           acc.cyls += (uint32_t)C.env_nc;
           for (int e = 0; e < env_ns; ++e) {
-            const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
+            const float4 es = __ldg(&env_s[e]);
             if (sph_hit(bw, es)) {
               push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
               nd = true;
@@ -1567,8 +1566,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
           const float rr = bw.w * bw.w;
           for (int b = 0; b < env_nb; ++b) {
-            const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
-            const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
+            const float4 lo = __ldg(&box_lo[b]);
+            const float4 hi = __ldg(&box_hi[b]);
             if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
               push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
               nd = true;
@@ -1591,7 +1590,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
         bool nd = false;
         for (int e = og; e < env_ns; e += 8) {
-          const float4 es = e < ns_c ? S.ES[e] : __ldg(&env_s[e]);
+          const float4 es = __ldg(&env_s[e]);
           if (sph_hit(bw, es)) {
             push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
             nd = true;
@@ -1599,8 +1598,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         }
         const float rr = bw.w * bw.w;
         for (int b = og; b < env_nb; b += 8) {
-          const float4 lo = b < nb_c ? S.BL[b] : __ldg(&box_lo[b]);
-          const float4 hi = b < nb_c ? S.BH[b] : __ldg(&box_hi[b]);
+          const float4 lo = __ldg(&box_lo[b]);
+          const float4 hi = __ldg(&box_hi[b]);
           if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
             push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
             nd = true;
@@ -1653,7 +1652,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         if (__any_sync(0xffffffffu, hit) && !exhaustive) return 1u;
       }
       // self-pair groups by their frames' bounding spheres
-      if constexpr (WS::kClass == 1) {
+      if constexpr (WS::kLarge) {
         // large teams: 32 groups at a time, the overlapping ones appended to
         // the list in order, and the list resolved (with a vote) whenever the
         // next 32 might not fit, so it never overflows (16 arms: about 100 of
@@ -1839,7 +1838,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
       need_frame(cl, k2);
     }
   };
-  if constexpr (WS::kClass == 1) {
+  if constexpr (WS::kLarge) {
     // large teams: frame pairs only for robot pairs whose enclosing spheres
     // overlap.  Robot r's sphere: center at the middle of its frame centers'
     // box, radius the largest distance to a frame sphere's far side, enlarged
@@ -2231,16 +2230,6 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
         }
     S.rpf[CK(p, WS::kRobots * (WS::kRobots - 1) / 2 + 1, PAIRTAB, B.err)] = (int16_t)CK(f, 32768, PAIRTAB_PREFIX, B.err);
   }
-  if (C.check_env && !(Q.bits & 2u)) {
-    for (int o = lane; o < min(C.env_ns, kEnvCache); o += kWarp) {
-      S.ES[o] = C.env_s[o];
-      S.EK[o] = C.env_k[o];
-    }
-    for (int o = lane; o < min(C.env_nb, kBoxCache); o += kWarp) {
-      S.BL[o] = C.box_lo[o];
-      S.BH[o] = C.box_hi[o];
-    }
-  }
   __syncwarp();
   const int total = Q.nslices * Q.nphase;
   const int k0 = c * Q.cte;
@@ -2324,7 +2313,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
 // which is also what the shared memory of 3 blocks of 4 warps of the team
 // layout allows.  The instance of layout WS takes the work items of its class.
 template <bool CLR, class WS>
-__global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
+__global__ void __launch_bounds__(WS::kMaxThreads, 1) k_main(BatchDev B, int q_single) {
   extern __shared__ float4 smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -2339,10 +2328,10 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
       run_chunk<CLR>(B, S, q_single, c, lane);
     return;
   }
-  const int n_items = B.counters[cls ? 3 : 1];
+  const int n_items = B.counters[kCtrItems(cls)];
   if (n_items == 0) return;
   const int *level_start = B.level_start + cls * (kMaxLevels + 1);
-  const int qbase = cls ? B.counters[5] : 0;   // first sorted position of the class
+  const int qbase = B.counters[kCtrFirst(cls)];   // first sorted position of the class
   const bool skip_dead = !(B.flags & MRV_EXHAUSTIVE);
   unsigned long long items = 0;
   // Items are claimed g at a time.  Lane l < g resolves item base + l (level,
@@ -2355,8 +2344,8 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
     // the abort flag is read together with the claim (both round trips at once)
     int base = 0, aborted = 0;
     if (lane == 0) {
-      base = atomicAdd(&B.counters[cls ? 4 : 0], g);
-      aborted = *(volatile int *)&B.counters[2];
+      base = atomicAdd(&B.counters[kCtrClaim(cls)], g);
+      aborted = *(volatile int *)&B.counters[kCtrAbort];
 #ifdef MRV_CHECKED
       aborted |= (*(volatile uint32_t *)B.err & kErrChecked) != 0u;   // stop at a failed index check
 #endif
@@ -2370,7 +2359,7 @@ __global__ void __launch_bounds__(384, 1) k_main(BatchDev B, int q_single) {
       if (aborted) halt = 1;
       else if (B.clock_budget > 0 && clock64() - t_start > B.clock_budget) halt = 2;
       if (halt) atomicOr(B.err, halt == 1 ? kErrAbort : kErrTimeout);
-      if (halt == 2) atomicExch(&B.counters[2], 1);
+      if (halt == 2) atomicExch(&B.counters[kCtrAbort], 1);
     }
     if (__shfl_sync(0xffffffffu, halt, 0)) break;
     const int idx = base + lane;
@@ -2520,7 +2509,9 @@ __global__ void k_clearance(BatchDev B, int q, const int32_t *ts, int nt, int ch
 // ---------------------------------------------------------------------------
 
 size_t main_smem_bytes(int warps, int cls) {
-  return (cls ? warp_smem_bytes<WarpSmemLarge>() : warp_smem_bytes<WarpSmemTeam>()) * (size_t)warps;
+  const size_t per = cls == 2 ? warp_smem_bytes<WarpSmemLarge>()
+                              : (cls == 1 ? warp_smem_bytes<WarpSmemTeam>() : warp_smem_bytes<WarpSmemSmall>());
+  return per * (size_t)warps;
 }
 
 int large_warps() { return kLargeWarps; }
@@ -2539,9 +2530,18 @@ cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st) {
 }
 
 // The dynamic shared memory limit of k_main is a process-wide attribute (per
-// device): it is raised once to what the largest block (12 warps of the team
-// layout, kLargeWarps of the large-team layout) needs, so launches with fewer
-// warps on other threads never see it shrink under them.
+// device): it is raised once to what the largest block (12 warps of the
+// small-team and team layouts, kLargeWarps of the large-team layout) needs,
+// so launches with fewer warps on other threads never see it shrink under
+// them.
+template <class WS>
+static cudaError_t set_attrs_of(int bytes) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_main<false, WS>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true, WS>, a, bytes);
+  return e;
+}
+
 cudaError_t set_main_attrs(int warps) {
   (void)warps;
   constexpr int kMaxDevices = 64;
@@ -2553,35 +2553,38 @@ cudaError_t set_main_attrs(int warps) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return cudaSuccess;
-  const int team = (int)main_smem_bytes(12, 0), large = (int)main_smem_bytes(kLargeWarps, 1);
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  e = cudaFuncSetAttribute(k_main<false, WarpSmemTeam>, a, team);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true, WarpSmemTeam>, a, team);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<false, WarpSmemLarge>, a, large);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_main<true, WarpSmemLarge>, a, large);
+  e = set_attrs_of<WarpSmemSmall>((int)main_smem_bytes(12, 0));
+  if (e == cudaSuccess) e = set_attrs_of<WarpSmemTeam>((int)main_smem_bytes(12, 1));
+  if (e == cudaSuccess) e = set_attrs_of<WarpSmemLarge>((int)main_smem_bytes(kLargeWarps, 2));
   if (e == cudaSuccess) done[dev] = true;
   return e;
 }
 
+template <class WS>
+static cudaError_t occupancy_of(int warps, bool clr, int *out) {
+  const size_t smem = main_smem_bytes(warps, WS::kClass);
+  return clr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WS>, warps * 32, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WS>, warps * 32, smem);
+}
+
 cudaError_t max_blocks_per_sm(int warps, bool clr, int cls, int *out) {
   set_main_attrs(warps);
-  const size_t smem = main_smem_bytes(warps, cls);
-  if (cls)
-    return clr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WarpSmemLarge>, warps * 32, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WarpSmemLarge>, warps * 32, smem);
-  return clr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WarpSmemTeam>, warps * 32, smem)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WarpSmemTeam>, warps * 32, smem);
+  if (cls == 2) return occupancy_of<WarpSmemLarge>(warps, clr, out);
+  if (cls == 1) return occupancy_of<WarpSmemTeam>(warps, clr, out);
+  return occupancy_of<WarpSmemSmall>(warps, clr, out);
+}
+
+template <class WS>
+static void launch_of(const BatchDev &B, int grid, int warps, bool clr, int q_single, cudaStream_t st) {
+  const size_t smem = main_smem_bytes(warps, WS::kClass);
+  if (clr) k_main<true, WS><<<grid, warps * 32, smem, st>>>(B, q_single);
+  else k_main<false, WS><<<grid, warps * 32, smem, st>>>(B, q_single);
 }
 
 cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int cls, int q_single, cudaStream_t st) {
-  const size_t smem = main_smem_bytes(warps, cls);
-  if (cls) {
-    if (clr) k_main<true, WarpSmemLarge><<<grid, warps * 32, smem, st>>>(B, q_single);
-    else k_main<false, WarpSmemLarge><<<grid, warps * 32, smem, st>>>(B, q_single);
-  } else {
-    if (clr) k_main<true, WarpSmemTeam><<<grid, warps * 32, smem, st>>>(B, q_single);
-    else k_main<false, WarpSmemTeam><<<grid, warps * 32, smem, st>>>(B, q_single);
-  }
+  if (cls == 2) launch_of<WarpSmemLarge>(B, grid, warps, clr, q_single, st);
+  else if (cls == 1) launch_of<WarpSmemTeam>(B, grid, warps, clr, q_single, st);
+  else launch_of<WarpSmemSmall>(B, grid, warps, clr, q_single, st);
   return cudaGetLastError();
 }
 
