@@ -181,6 +181,12 @@ struct WarpSmemT {
   int32_t off[NR + 1];
   int32_t seg[NR];           // per robot: waypoint index of the segment of the
                              // latest FK round (states grow within a slice)
+  // slots of a single segment (two waypoints: every start/goal slot): the
+  // segment's end time (-1: several segments, interpolated from global
+  // memory) and its two waypoints, staged once per work item so that an FK
+  // round interpolates without waiting on global loads
+  int32_t itau[NR];
+  float ia[NR][MRV_MAX_DOF], ig[NR][MRV_MAX_DOF];
   float ox, oy, oz;          // origin of the relative frame (world)
   int32_t pad[4];
   // robot pairs i < j of the query, i | j << 4 | n_links_j << 8 | m << 16
@@ -2030,10 +2036,19 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
         if (t <= C.T) {
           const RobotSlot &rs = S.rs[r];
           float q[MRV_MAX_DOF];
-          int lo;
-          interp_from(B, rs.w0, rs.w1, rs.dof, t, S.seg[r], q, &lo);
+          const int T1 = S.itau[r];
+          if (T1 >= 0) {
+            // one segment from time 0 to T1 (the same arithmetic as interp)
+            const float f = t >= T1 ? 0.f : (float)t / (float)T1;
+#pragma unroll
+            for (int j = 0; j < MRV_MAX_DOF; ++j)
+              if (j < rs.dof) q[j] = t >= T1 ? S.ig[r][j] : fmaf(S.ig[r][j] - S.ia[r][j], f, S.ia[r][j]);
+          } else {
+            int lo;
+            interp_from(B, rs.w0, rs.w1, rs.dof, t, S.seg[r], q, &lo);
+            if (row == 0) atomicMax(&S.seg[r], lo);
+          }
           chain_row(B.models[rs.mdl], q, xf + CK(c, WS::kChains, CHAIN, C.err) * (kMaxLinks * 12), row);
-          if (row == 0) atomicMax(&S.seg[r], lo);
         }
       }
     }
@@ -2200,6 +2215,19 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     for (int l = 0; l < kMaxLinks + 2; ++l) rs.ls[l] = (int16_t)(l <= m.n_links ? m.link_start[l] : m.n_spheres);
     S.rs[lane] = rs;
     S.seg[lane] = rs.w0;
+    if (rs.w1 - rs.w0 == 2) {
+      const int w = CK(rs.w0 + 1, B.n_waypoints, WAYPOINT, B.err);
+      const float *a = B.waypoints + (size_t)(w - 1) * B.wp_stride;
+      S.itau[lane] = B.slot_tau[w];
+#pragma unroll
+      for (int j = 0; j < MRV_MAX_DOF; ++j)
+        if (j < rs.dof) {
+          S.ia[lane][j] = a[j];
+          S.ig[lane][j] = a[B.wp_stride + j];
+        }
+    } else {
+      S.itau[lane] = -1;
+    }
     if (lane == 0) { S.ox = m.base[3]; S.oy = m.base[7]; S.oz = m.base[11]; }
   }
   __syncwarp();
