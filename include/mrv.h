@@ -49,10 +49,11 @@ extern "C" {
 #define MRV_ERR_LIMIT (-7)     /* a size beyond a documented maximum        */
 
 /* ---- limits ------------------------------------------------------------ */
-/* Queries of up to 8 robots and 512 spheres run on the team kernel layout;
- * larger ones (the 16-arm Cage team of Sec. V-A) on a second kernel instance
- * with a larger per-warp layout, launched after the first when a batch may
- * hold such queries (always for MRV_PTRS_ON_DEVICE batches). */
+/* Queries of up to 8 robots run on the small-team kernel layout (up to 256
+ * spheres) or the team layout (up to 512); larger ones (the 16-arm Cage team
+ * of Sec. V-A) on a large-team layout; the team and large-team instances are
+ * launched beside the first when a batch may hold such queries (always for
+ * MRV_PTRS_ON_DEVICE batches). */
 #define MRV_MAX_ROBOTS 16          /* robots per query (120 pairs)          */
 #define MRV_MAX_DOF 8              /* joints per robot                      */
 #define MRV_MAX_SPHERES 256        /* spheres per robot model               */
@@ -306,8 +307,11 @@ int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
  * work item is slices_per_item consecutive slices of one query. */
 typedef struct {
   int32_t slices_per_item;   /* slices per work item (>= 1)                  */
-  int32_t warps_per_block;   /* 1..12 (18.7 KB of shared memory per warp; the
-                                large-team instance uses 6 warps of 35.1 KB) */
+  int32_t warps_per_block;   /* 1..12, blocks of the small-team and team
+                                instances (queries of up to 256 / 512
+                                spheres: 13 / 17.3 KB of shared memory per
+                                warp, up to 16 / 12 warps per SM); the
+                                large-team instance uses 6 warps of 34.8 KB */
   int32_t blocks_per_sm;     /* 0 = as many as fit                           */
   int32_t tile_split;        /* 1, 2, 4, 8, 16 or 32 slices per 32-state tile for
                                 kinematic-chain queries (point-robot queries
@@ -325,7 +329,8 @@ int mrv_get_tuning(mrv_ctx *ctx, mrv_tuning *t);
 /* Times candidate tunings on `batch` (MRV_PTRS_ON_DEVICE, run through
  * mrv_run semantics): 1, 2 or 4 slices per item x 2, 4, 8 or 16 slices per
  * tile x 4- or 8-warp blocks, and both MV orders when the batch has obstacle
- * checks and names no order; each scored by the fastest of four timed runs.
+ * checks and names no order; each scored by the fastest of four timed runs
+ * (twelve when a run takes under 2 ms).
  * Keeps the fastest in the context and caches it in the text file
  * `cache_path` (nullable) keyed by device name and a batch class (robot
  * count, sphere count and length buckets, query kinds).  A cached entry is

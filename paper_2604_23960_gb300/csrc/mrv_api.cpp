@@ -665,6 +665,9 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
     spf[p] = (uint32_t)e.first | ((uint32_t)e.second << 16);
   }
   D.n_links = n_links;
+  D.frame_mask = 0;
+  for (int l = 0; l < n_links; ++l)
+    if (PM.link_bs[4 * l + 3] >= 0.f) D.frame_mask |= 1u << l;
   for (int l = 0; l <= n_links; ++l) D.link_start[l] = PM.link_start[l];
   for (int l = 0; l < n_links; ++l)
     for (int k = 0; k < 4; ++k) D.link_bs[l][k] = PM.link_bs[4 * l + k];

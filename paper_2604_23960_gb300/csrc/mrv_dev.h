@@ -140,6 +140,7 @@ struct ModelDev {
   const uint32_t *self_masks;    // per block row: bit c = pair with column c
   int32_t n_groups;
   int32_t n_masks;               // self-pair block rows (entries of self_masks)
+  uint32_t frame_mask;           // bit l: frame l holds spheres
   const int32_t *perm;           // sorted sphere index -> caller's index
 };
 

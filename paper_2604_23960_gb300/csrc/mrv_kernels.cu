@@ -90,7 +90,7 @@ __device__ __forceinline__ long long ck_idx(long long i, long long n, uint32_t s
 #endif
 
 constexpr int kFlavorAMaxSpheres = 16;
-constexpr int kSlotWords = 28;                   // words per RobotSlot in shared memory
+constexpr int kSlotWords = 30;                   // words per RobotSlot in shared memory
 constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
 
 struct RobotSlot {           // per-warp staged view of one robot of the query
@@ -103,6 +103,7 @@ struct RobotSlot {           // per-warp staged view of one robot of the query
   int32_t mdl, m, dof, kind, n_self, w0, w1, n_rects;
   int32_t n_links, n_groups;
   int16_t ls[kMaxLinks + 2]; // frame ranges of the sorted spheres (copy of md->link_start)
+  int16_t nfr;               // frames holding spheres (bits of md->frame_mask)
 };
 static_assert(sizeof(RobotSlot) <= kSlotWords * 4, "slot size");
 
@@ -116,6 +117,7 @@ struct TileCtx {
   int pair_robots;           // robots i whose pairs (i, j > i) are checked
   int self_blk;              // every robot's self pairs come as blocks
   int pr0, pr1;              // robot-pair table entries checked in the current phase
+  int fpt;                   // frame-pair table: 0 not used (too many pairs), 1 not built yet, 2 built
   int first_phase;           // the current phase is the first visit of its states
   long long rangetests;      // sphere tests per state of the entries pr0..pr1-1
   int split, spt, nslices;
@@ -195,6 +197,13 @@ struct WarpSmemT {
   // frame-pair counts n_links_i x n_links_j
   uint32_t rp[NR * (NR - 1) / 2];
   int16_t rpf[NR * (NR - 1) / 2 + 2];
+  // small teams: the query's frame pairs whose two frames hold spheres,
+  // frame slot k | k2 << 8, grouped by robot-pair table entry (fpf: the
+  // exclusive prefix of their counts per entry); built when a work item first
+  // reaches its robot-robot checks
+  static constexpr int kFPCap = (NR <= kTeamRobots && MQ <= kSmallSpheres) ? 512 : 0;
+  uint16_t fp[kFPCap > 0 ? kFPCap : 1];
+  int16_t fpf[NR * (NR - 1) / 2 + 2];
   float4 BS[NR * kMaxLinks];  // per (robot, frame) bounding sphere at the
                               // current state (center relative to o; w < 0: none)
   union {
@@ -1904,6 +1913,40 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
       while (cl.keptf[it + 1] <= f) ++it;
       frame_pair(cl.kept[it], f - cl.keptf[it]);
     }
+  } else if (WS::kFPCap > 0 && C.fpt) {
+    if (C.fpt == 1) {
+      // the frame-pair table, built once per work item: entry e of robot-pair
+      // entry p is its (e - fpf[p])-th pair (u, v) of frames holding spheres
+      const int npr = C.prio ? n - 1 : n * (n - 1) / 2;
+      const int ftot = S.fpf[npr];
+      int p = 0;
+      for (int e = lane; e < ftot; e += kWarp) {
+        while (S.fpf[p + 1] <= e) ++p;
+        const uint32_t r = S.rp[p];
+        const int i = (int)(r & 15u), j = (int)((r >> 4) & 15u);
+        const uint32_t mi = S.rs[i].md->frame_mask, mj = S.rs[j].md->frame_mask;
+        const int nj = __popc(mj), g = e - S.fpf[p];
+        const int ui = g / nj, vi = g - ui * nj;
+        const int u = __fns(mi, 0, ui + 1), v = __fns(mj, 0, vi + 1);
+        S.fp[CK(e, WS::kFPCap > 0 ? WS::kFPCap : 1, PAIRTAB, C.err)] =
+            (uint16_t)((i * kMaxLinks + u) | ((j * kMaxLinks + v) << 8));
+      }
+      __syncwarp();
+      if (lane == 0) C.fpt = 2;
+      __syncwarp();
+    }
+    // the phase's frame pairs whose frames hold spheres, from the table
+    const int ftot = S.fpf[C.pr1];
+    for (int f = S.fpf[C.pr0] + lane; f < ftot; f += kWarp) {
+      const uint32_t e = S.fp[f];
+      const int k = (int)(e & 0xffu), k2 = (int)(e >> 8);
+      acc.tests += 1;
+      if (sph_hit(S.BS[k], S.BS[k2])) {
+        push_cand(cl.pc, &cl.np, &cl.overflow, ((uint32_t)k << 8) | (uint32_t)k2);
+        need_frame(cl, k);
+        need_frame(cl, k2);
+      }
+    }
   } else {
     const int ftot = S.rpf[C.pr1];
     int it = C.pr0;
@@ -2211,6 +2254,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     rs.mdl = id; rs.m = m.n_spheres; rs.dof = m.dof; rs.kind = m.kind; rs.n_self = m.n_self;
     rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.n_rects = m.n_rects;
     rs.n_links = m.n_links; rs.n_groups = m.n_groups;
+    rs.nfr = (int16_t)__popc(m.frame_mask);
 #pragma unroll
     for (int l = 0; l < kMaxLinks + 2; ++l) rs.ls[l] = (int16_t)(l <= m.n_links ? m.link_start[l] : m.n_spheres);
     S.rs[lane] = rs;
@@ -2242,7 +2286,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     for (int r = 0; r < C.n; ++r) blk &= (S.rs[r].n_groups == 0 || S.rs[r].masks != nullptr);
     C.self_blk = blk;
     // pairs in (i, j) order; pairs-first MV lists the adjacent pairs first
-    int p = 0, f = 0;
+    int p = 0, f = 0, ff = 0;
     const bool pf = !C.ffc && Q.nadj > 0;
     const uint32_t *adj = B.q[q].adj;   // read in place (a copy indexed at run time would live in local memory)
     for (int pass = pf ? 0 : 1; pass < 2; ++pass)
@@ -2253,10 +2297,15 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
           const int pc = CK(p, WS::kRobots * (WS::kRobots - 1) / 2, PAIRTAB, B.err);
           S.rp[pc] = (uint32_t)(i | j << 4 | nj << 8) | ((uint32_t)((4096 + nj - 1) / nj) << 16);
           S.rpf[pc] = (int16_t)CK(f, 32768, PAIRTAB_PREFIX, B.err);
+          S.fpf[pc] = (int16_t)ff;
           f += S.rs[i].n_links * S.rs[j].n_links;
+          ff += S.rs[i].nfr * S.rs[j].nfr;
           ++p;
         }
     S.rpf[CK(p, WS::kRobots * (WS::kRobots - 1) / 2 + 1, PAIRTAB, B.err)] = (int16_t)CK(f, 32768, PAIRTAB_PREFIX, B.err);
+    S.fpf[p] = (int16_t)min(ff, 32767);
+    // the table pays for its construction once an item spans 8 states or more
+    C.fpt = (WS::kFPCap > 0 && ff <= WS::kFPCap && Q.cte * Q.spt >= 8) ? 1 : 0;
   }
   __syncwarp();
   const int total = Q.nslices * Q.nphase;
