@@ -124,8 +124,8 @@ MAKERS = None
 # DRAM bytes of one persistent-kernel launch of the headline step, from a
 # one-pass ncu capture of that launch; valid only for the kernel source it was
 # taken on (any other source reports null)
-TRAFFIC = {"kernel_sha256": "47cbb502fe05145a1de78683988fcf25732f9f8b60bd7540e8cfc24c6fea166e",
-           "bytes": 1822132736 + 22372608}
+TRAFFIC = {"kernel_sha256": "37400cdfe34636df955192e17f8fe9a866411c60c9e5fe635ca284dfe2a4e1a9",
+           "bytes": 1290245376 + 20194048}
 
 
 def traffic_per_launch():
