@@ -893,6 +893,17 @@ def run(args):
         dist.destroy_process_group()
 
 
+def run_serving_only(args):
+    """The request server's measurement alone (one GPU): prints its section."""
+    import torch
+    from paper_2604_23960_gb300 import mrv
+    torch.cuda.set_device(0)
+    ctx = mrv.Context(0)
+    out = serving(ctx, args.serve_seconds)
+    ctx.close()
+    print(json.dumps({"serving": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -909,11 +920,15 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--only-serve", action="store_true",
+                    help="run the request server's measurement alone (for profiling its micro-batches)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_serve:
+        run_serving_only(args)
     else:
         run(args)
 

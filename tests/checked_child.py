@@ -3,8 +3,9 @@
 results(ctx) runs a fixed set of seeded inputs through every path of the
 library (MV in each order, flag and layout, FFC, mixed runs, graph replay,
 exhaustive minimum clearance, the per-sphere clearance diagnostic, one
-launch per query, prioritized MV, cylinders, the large-team kernel instance)
-and returns the outputs by name.  The test runs it once in a child process
+launch per query, prioritized MV, cylinders, the large-team kernel instance,
+and benchmark-sized batches of the ragged teams, timed-path FFC, 8- and
+16-arm workloads) and returns the outputs by name.  The test runs it once in a child process
 that loads libmrv_checked.so (MRV_LIBRARY=checked) and once in its own
 process with libmrv.so, and compares.  Run as a script, it writes the
 outputs to an .npz file; any index check failing in the checked build
@@ -98,6 +99,16 @@ def results(ctx) -> dict:
     mrv.mrv_graph_destroy(g)
     out["ragged_gv"], out["ragged_gc"] = _np(vg), _np(cg)
     out["ragged_kind"] = np.asarray(w.batch.q_kind)
+    # benchmark-sized launches (the configurations bench.py times, smaller
+    # counts): ragged teams, timed-path FFC, the 16-arm team
+    wb = W.make_ragged_teams(60000, seed=907)
+    bb = ctx.bind(wb).to("cuda")
+    v, c = ctx.run(bb)
+    out["big_ragged_v"], out["big_ragged_c"] = _np(v), _np(c)
+    out["big_ragged_kind"] = np.asarray(wb.batch.q_kind)
+    out["big_ffc"] = _np(ctx.ffc_find(ctx.bind(W.make_cage_ffc(5000, query_seed=908)).to("cuda")))
+    out["big_c16"] = _np(ctx.mv_validate(ctx.bind(W.make_cage16_mv(2000, query_seed=909)).to("cuda")))
+    out["big_c8"] = _np(ctx.mv_validate(ctx.bind(W.make_cage8_mv(2000, query_seed=910)).to("cuda")))
     return out
 
 

@@ -3,8 +3,9 @@ MRV_CHECKED): every shared- and global-memory index of the kernels is
 checked against its array, and a failure sets the call's error record and
 comes back as MRV_ERR_CUDA naming the check.  A child process runs the
 tiny, edge-case, cylinder, prioritized, 16-arm and ragged inputs of
-tests/checked_child.py through every path with that build: no check may
-fail, and every output must equal this process's run of the normal build."""
+tests/checked_child.py through every path with that build, and
+benchmark-sized ragged, FFC, 8- and 16-arm batches: no check may fail, and
+every output must equal this process's run of the normal build."""
 from __future__ import annotations
 
 import os
@@ -41,6 +42,10 @@ def test_checked_build_clean_and_equal(tmp_path):
             np.testing.assert_array_equal(g[kind == 0], v[kind == 0], err_msg=k)
         elif k in ("ragged_c", "ragged_gc"):
             np.testing.assert_array_equal(g[kind == 1], v[kind == 1], err_msg=k)
+        elif k == "big_ragged_v":
+            np.testing.assert_array_equal(g[ref["big_ragged_kind"] == 0], v[ref["big_ragged_kind"] == 0], err_msg=k)
+        elif k == "big_ragged_c":
+            np.testing.assert_array_equal(g[ref["big_ragged_kind"] == 1], v[ref["big_ragged_kind"] == 1], err_msg=k)
         elif k.endswith("_mc") or k.endswith("_clr"):
             fin = np.isfinite(v)
             np.testing.assert_array_equal(np.isfinite(g), fin, err_msg=k)
