@@ -78,7 +78,7 @@ size_t Scratch::layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char 
   set(&sorted, sizeof(int32_t) * nq);
   set(&hist, sizeof(int32_t) * kLevelBins);
   set(&level_start, sizeof(int32_t) * kLevelBins);
-  set(&cursor, sizeof(int32_t) * kLevelBins);
+  set(&cursor, sizeof(int32_t) * 2 * kLevelBins);
   set(&counters, sizeof(int32_t) * kNumCounters);
   set(&err, sizeof(uint32_t) * kErrWords);
   set(&stats, sizeof(unsigned long long) * kNumStats);

@@ -223,10 +223,10 @@ struct BatchDev {
   int32_t *q_hit;                    // MV: 1 once a collision is found
   int32_t *q_best;                   // FFC: min key t << 7 | pair index
   float *q_minclr;                   // exhaustive MV: min clearance (as ordered int)
-  int32_t *sorted;                   // queries sorted by nchunks (desc)
-  int32_t *hist;                     // kLevelBins bins (class 0, then class 1)
+  int32_t *sorted;                   // queries by class, nchunks (desc), then FFC before MV
+  int32_t *hist;                     // kLevelBins bins (class 0, 1, then 2)
   int32_t *level_start;              // kLevelBins
-  int32_t *cursor;                   // kLevelBins
+  int32_t *cursor;                   // 2 x kLevelBins: each bin's next FFC and next MV position
   int32_t *counters;                 // kNumCounters: the abort flag and per-class claim
                                      // counter, items and first sorted position (kCtr*)
   uint32_t *err;                     // kErrWords: error bits, check site, index, extent

@@ -451,7 +451,8 @@ __global__ void k_prep(BatchDev B) {
 }
 
 // level layout, per work class: the class's queries sorted by item count
-// (descending), classes in order (qbase: the queries of the classes before);
+// (descending; within one item count the FFC queries, then the MV ones),
+// classes in order (qbase: the queries of the classes before);
 // level c holds the class's queries with more
 // than c items, which are its first cnt_c sorted queries.  With h the class's
 // histogram of item counts (bin kMaxLevels: that many or more) and
@@ -488,7 +489,8 @@ __global__ void __launch_bounds__(kLevelThreads) k_levels(BatchDev B) {
   if (t < kLevelBins) {
     int qbase = 0;   // S[0] of each class before this one: its queries
     for (int c = 0; c < cls; ++c) qbase += suf[c * L + kMaxLevels];
-    B.cursor[t] = qbase + S1;
+    B.cursor[t] = qbase + S1;                          // FFC queries fill the bin from its start,
+    B.cursor[kLevelBins + t] = qbase + S1 + B.hist[t];  // MV queries from its end
     if (k < kMaxLevels) B.level_start[CK(cls * L + k + 1, kLevelBins, LEVELS, B.err)] = pre[t];
     if (k == 0) {
       B.level_start[cls * L] = 0;
@@ -504,7 +506,11 @@ __global__ void k_scatter(BatchDev B) {
   const QueryDev &Q = B.q[q];
   int c = Q.nchunks;
   if (c > kMaxLevels) c = kMaxLevels;
-  const int pos = atomicAdd(&B.cursor[(int)((Q.bits >> 3) & 3u) * (kMaxLevels + 1) + c], 1);
+  // each bin holds its FFC queries first and its MV queries after them, so
+  // the warps of a level run long stretches of one kind of item (one code
+  // path in the instruction cache) instead of a mix
+  const int bin = (int)((Q.bits >> 3) & 3u) * (kMaxLevels + 1) + c;
+  const int pos = (Q.bits & 1u) ? atomicAdd(&B.cursor[bin], 1) : atomicSub(&B.cursor[kLevelBins + bin], 1) - 1;
   B.sorted[CK(pos, B.n_queries, SCATTER, B.err)] = q;
 }
 

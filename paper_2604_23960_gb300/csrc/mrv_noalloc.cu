@@ -31,7 +31,7 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 constexpr size_t kBytes =
     align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_WAYPOINTS) + align_up(sizeof(QueryDev) * MRV_NOALLOC_MAX_QUERIES) +
     3 * align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) + align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) +
-    3 * align_up(sizeof(int32_t) * kLevelBins) + align_up(sizeof(int32_t) * kNumCounters) + align_up(sizeof(uint32_t) * kErrWords) +
+    2 * align_up(sizeof(int32_t) * kLevelBins) + align_up(sizeof(int32_t) * 2 * kLevelBins) + align_up(sizeof(int32_t) * kNumCounters) + align_up(sizeof(uint32_t) * kErrWords) +
     align_up(sizeof(unsigned long long) * kNumStats) + align_up(sizeof(int32_t) * 4);
 
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
@@ -66,7 +66,7 @@ void carve(void *base, int64_t nq, int64_t nw, Scratch *S) {
   S->sorted = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
   S->hist = (int32_t *)take(sizeof(int32_t) * kLevelBins);
   S->level_start = (int32_t *)take(sizeof(int32_t) * kLevelBins);
-  S->cursor = (int32_t *)take(sizeof(int32_t) * kLevelBins);
+  S->cursor = (int32_t *)take(sizeof(int32_t) * 2 * kLevelBins);
   S->counters = (int32_t *)take(sizeof(int32_t) * kNumCounters);
   S->err = (uint32_t *)take(sizeof(uint32_t) * kErrWords);
   S->stats = (unsigned long long *)take(sizeof(unsigned long long) * kNumStats);
