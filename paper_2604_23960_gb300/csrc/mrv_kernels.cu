@@ -118,6 +118,7 @@ struct TileCtx {
   int self_blk;              // every robot's self pairs come as blocks
   int pr0, pr1;              // robot-pair table entries checked in the current phase
   int fpt;                   // frame-pair table: 0 not used (too many pairs), 1 not built yet, 2 built
+  int nef, nef_env;          // frame slots holding spheres (ef): all robots', the obstacle-checked robots'
   int first_phase;           // the current phase is the first visit of its states
   long long rangetests;      // sphere tests per state of the entries pr0..pr1-1
   int split, spt, nslices;
@@ -206,6 +207,8 @@ struct WarpSmemT {
   int16_t fpf[NR * (NR - 1) / 2 + 2];
   float4 BS[NR * kMaxLinks];  // per (robot, frame) bounding sphere at the
                               // current state (center relative to o; w < 0: none)
+  uint8_t ef[NR * kMaxLinks]; // the query's frame slots holding spheres, by robot
+                              // (the others' BS entries stay w < 0 for the item)
   union {
     struct {
       float xf[kChains * kMaxLinks * 12];   // link frames of one FK round
@@ -1072,20 +1075,19 @@ __device__ bool env_mv(const TileCtx &C, const WS &S, const float4 *P, const flo
 // FK slot jj of xf
 template <class WS>
 __device__ void link_spheres(const TileCtx &C, WS &S, const float *xf, int jj, int lane) {
-  const int n = C.n;
-  for (int k = lane; k < n * kMaxLinks; k += kWarp) {
+  const int n = C.n, nef = C.nef;
+  for (int i = lane; i < nef; i += kWarp) {
+    const int k = CK((int)S.ef[i], WS::kRobots * kMaxLinks, FRAME_SLOT, C.err);
     const int r = k / kMaxLinks, l = k - r * kMaxLinks;
-    const ModelDev &md = *S.rs[r].md;
-    float4 o = make_float4(0.f, 0.f, 0.f, -1.f);
-    if (l < S.rs[r].n_links && md.link_bs[l][3] >= 0.f) {
-      const float *X = xf + (CK(jj * n + r, WS::kChains, CHAIN, C.err) * kMaxLinks + l) * 12;
-      const float cx = md.link_bs[l][0], cy = md.link_bs[l][1], cz = md.link_bs[l][2];
-      o.x = fmaf(X[0], cx, fmaf(X[1], cy, fmaf(X[2], cz, X[3]))) - S.ox;
-      o.y = fmaf(X[4], cx, fmaf(X[5], cy, fmaf(X[6], cz, X[7]))) - S.oy;
-      o.z = fmaf(X[8], cx, fmaf(X[9], cy, fmaf(X[10], cz, X[11]))) - S.oz;
-      o.w = md.link_bs[l][3];
-    }
-    S.BS[CK(k, WS::kRobots * kMaxLinks, FRAME_SLOT, C.err)] = o;
+    const float *lb = S.rs[r].md->link_bs[l];
+    const float4 bs = make_float4(lb[0], lb[1], lb[2], lb[3]);
+    const float *X = xf + (CK(jj * n + r, WS::kChains, CHAIN, C.err) * kMaxLinks + l) * 12;
+    float4 o;
+    o.x = fmaf(X[0], bs.x, fmaf(X[1], bs.y, fmaf(X[2], bs.z, X[3]))) - S.ox;
+    o.y = fmaf(X[4], bs.x, fmaf(X[5], bs.y, fmaf(X[6], bs.z, X[7]))) - S.oy;
+    o.z = fmaf(X[8], bs.x, fmaf(X[9], bs.y, fmaf(X[10], bs.z, X[11]))) - S.oz;
+    o.w = bs.w;
+    S.BS[k] = o;
   }
 }
 
@@ -1505,7 +1507,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   auto &cl = S.u.b.cl;
   const float4 *P = S.u.b.P;
   const int n = C.n;
-  const int nke = C.self_robots * kMaxLinks;   // frames with obstacle checks
+  const int nke = C.nef_env;   // frames with obstacle checks: entries [0, nke) of ef
   const bool exhaustive = C.exhaustive != 0, ffc = C.ffc != 0;
   if (lane == 0) {
     cl.np = cl.ne = cl.nb = cl.ns = cl.overflow = cl.ny = 0;
@@ -1524,9 +1526,9 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
       const EnvDev &E = *C.env;
       const float glx = E.g_lo[0], gly = E.g_lo[1], glz = E.g_lo[2], gih = E.g_inv_h;
       const int gdx = E.g_dims[0], gdy = E.g_dims[1], gdz = E.g_dims[2];
-      for (int k = lane; k < nke; k += kWarp) {
+      for (int i = lane; i < nke; i += kWarp) {
+        const int k = S.ef[i];
         const float4 bl = S.BS[k];
-        if (bl.w < 0.f) continue;
         const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
         int i0 = 0, is = 0, ib = 0, i1 = 0;   // spheres [i0, is), boxes [is, ib), cylinders [ib, i1)
         bool full = false;
@@ -1605,9 +1607,9 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
     } else {
       // no grid: frames x obstacles, lane = (frame group lane & 3, obstacle group lane >> 2)
       const int fg = lane & 3, og = lane >> 2;
-      for (int k = fg; k < nke; k += 4) {
+      for (int i = fg; i < nke; i += 4) {
+        const int k = S.ef[i];
         const float4 bl = S.BS[k];
-        if (bl.w < 0.f) continue;
         const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
         bool nd = false;
         for (int e = og; e < env_ns; e += 8) {
@@ -1635,8 +1637,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
       }
       const uint32_t ns_l = (uint32_t)max(0, (env_ns - og + 7) >> 3), nb_l = (uint32_t)max(0, (env_nb - og + 7) >> 3);
       const uint32_t nc_l = (uint32_t)max(0, (C.env_nc - og + 7) >> 3);
-      int nf = 0;   // bounding spheres of this lane's frame group
-      for (int k = fg; k < nke; k += 4) nf += S.BS[k].w >= 0.f;
+      const int nf = max(0, (nke - fg + 3) >> 2);   // bounding spheres of this lane's frame group
       acc.tests += (uint32_t)nf * (ns_l + nb_l + nc_l);
       acc.boxes += (uint32_t)nf * nb_l;
       acc.cyls += (uint32_t)nf * nc_l;
@@ -2251,16 +2252,18 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   C.tests = 0; C.btests = 0; C.states = 0; C.chains = 0; C.placed = 0; C.ctests = 0;
   // stage the query's robots; origin of the relative frame = robot 0's base
   const int s0 = B.q_robot_off[q];
+  uint32_t fm = 0;   // this lane's robot: frames holding spheres
   if (lane < C.n) {
     const int id = CK(B.slot_robot_id[CK(s0 + lane, B.n_slots, SLOTS, B.err)], B.n_models, SLOTS, B.err);
     const ModelDev &m = B.models[id];
+    fm = m.frame_mask;
     RobotSlot rs;
     rs.spheres = m.spheres; rs.links = m.sphere_link; rs.self = m.self_pairs; rs.rects = m.self_rects; rs.md = &m;
     rs.masks = m.self_masks;
     rs.mdl = id; rs.m = m.n_spheres; rs.dof = m.dof; rs.kind = m.kind; rs.n_self = m.n_self;
     rs.w0 = B.slot_wp_off[s0 + lane]; rs.w1 = B.slot_wp_off[s0 + lane + 1]; rs.n_rects = m.n_rects;
     rs.n_links = m.n_links; rs.n_groups = m.n_groups;
-    rs.nfr = (int16_t)__popc(m.frame_mask);
+    rs.nfr = (int16_t)__popc(fm);
 #pragma unroll
     for (int l = 0; l < kMaxLinks + 2; ++l) rs.ls[l] = (int16_t)(l <= m.n_links ? m.link_start[l] : m.n_spheres);
     S.rs[lane] = rs;
@@ -2279,6 +2282,30 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
       S.itau[lane] = -1;
     }
     if (lane == 0) { S.ox = m.base[3]; S.oy = m.base[7]; S.oz = m.base[11]; }
+  }
+  {
+    // the frame slots holding spheres, robot by robot (lane r writes robot
+    // r's at the prefix of the counts); every other slot's bounding sphere
+    // is "none" for the whole item
+    const int cnt = __popc(fm);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int pos = incl - cnt;
+    while (fm) {
+      const int l = __ffs(fm) - 1;
+      fm &= fm - 1;
+      S.ef[CK(pos++, WS::kRobots * kMaxLinks, FRAME_SLOT, B.err)] = (uint8_t)(lane * kMaxLinks + l);
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, kWarp - 1), n0 = __shfl_sync(0xffffffffu, incl, 0);
+    for (int k = lane; k < C.n * kMaxLinks; k += kWarp) S.BS[k] = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (lane == 0) {
+      C.nef = tot;
+      C.nef_env = C.prio ? n0 : tot;
+    }
   }
   __syncwarp();
   if (lane == 0) {
