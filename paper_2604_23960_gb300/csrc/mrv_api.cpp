@@ -647,7 +647,7 @@ int robot_model_upload(mrv_ctx *c, const mrv_robot_desc *d, int32_t *id_out) {
       D.dh[k][1] = std::sin(r[1]);
       D.dh[k][2] = r[0];
       D.dh[k][3] = r[2];
-      D.dh[k][4] = r[3];
+      D.th0[k] = r[3];
     }
   for (int s = 0; s < d->n_spheres; ++s) D.r2max = std::max(D.r2max, d->sphere_xyzr[4 * s + 3] * d->sphere_xyzr[4 * s + 3]);
   // spheres grouped by frame with one bounding sphere per frame; self pairs

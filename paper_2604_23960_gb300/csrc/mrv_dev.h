@@ -8,6 +8,7 @@
 //   BatchDev  the ragged CSR batch (caller arrays or staged copies) plus the
 //             per-query / per-slot arrays derived on the device.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/mrv.h"
@@ -114,14 +115,16 @@ enum : uint32_t {
   kCkCount
 };
 
-struct ModelDev {
+struct alignas(16) ModelDev {
+  // the FK parameters first, each row 16-byte aligned (read as float4)
+  float base[12];                // base transform, 3x4 row-major
+  float flange[12];              // flange transform, 3x4 row-major
+  float dh[MRV_MAX_DOF][4];      // cos(alpha), sin(alpha), a, d
+  float th0[MRV_MAX_DOF];        // theta_offset
   int32_t kind, dof, n_spheres, n_self;
   int32_t live;
   float point_z;
   float r2max;                   // largest squared sphere radius
-  float base[12];
-  float flange[12];
-  float dh[MRV_MAX_DOF][5];      // cos(alpha), sin(alpha), a, d, theta_offset
   const float4 *spheres;         // local xyz, radius; sorted by frame
   const int32_t *sphere_link;
   const uint32_t *self_pairs;    // x | y << 16 with x < y, grouped by frame
@@ -143,6 +146,9 @@ struct ModelDev {
   uint32_t frame_mask;           // bit l: frame l holds spheres
   const int32_t *perm;           // sorted sphere index -> caller's index
 };
+static_assert(offsetof(ModelDev, base) % 16 == 0 && offsetof(ModelDev, flange) % 16 == 0 &&
+                  offsetof(ModelDev, dh) % 16 == 0 && sizeof(ModelDev) % 16 == 0,
+              "FK rows of a model are read as float4");
 
 struct EnvDev {
   int32_t n_spheres, n_aabbs;

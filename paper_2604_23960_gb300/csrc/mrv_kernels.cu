@@ -189,7 +189,8 @@ struct WarpSmemT {
   // memory) and its two waypoints, staged once per work item so that an FK
   // round interpolates without waiting on global loads
   int32_t itau[NR];
-  float ia[NR][MRV_MAX_DOF], ig[NR][MRV_MAX_DOF];
+  alignas(16) float ia[NR][MRV_MAX_DOF];
+  alignas(16) float ig[NR][MRV_MAX_DOF];
   float ox, oy, oz;          // origin of the relative frame (world)
   int32_t pad[4];
   // robot pairs i < j of the query, i | j << 4 | n_links_j << 8 | m << 16
@@ -615,7 +616,7 @@ __device__ __noinline__ void chain_frames(const ModelDev &m, const float *q, flo
 #pragma unroll
   for (int k = 0; k < MRV_MAX_DOF; ++k) {
     if (k < m.dof) {
-      const float ca = m.dh[k][0], sa = m.dh[k][1], a = m.dh[k][2], d = m.dh[k][3], th0 = m.dh[k][4];
+      const float ca = m.dh[k][0], sa = m.dh[k][1], a = m.dh[k][2], d = m.dh[k][3], th0 = m.th0[k];
       float s, c;
       sincosf(th0 + q[k], &s, &c);
 #pragma unroll
@@ -666,7 +667,9 @@ __device__ __forceinline__ void joint_sincos(float x, float *s, float *c) {
 }
 
 __device__ __noinline__ void chain_row(const ModelDev &m, const float *q, float *X, int r) {
-  float x = m.base[4 * r + 0], y = m.base[4 * r + 1], z = m.base[4 * r + 2], p = m.base[4 * r + 3];
+  // the model's rows are 16-byte aligned: one vector load per row and joint
+  const float4 b = reinterpret_cast<const float4 *>(m.base)[r];
+  float x = b.x, y = b.y, z = b.z, p = b.w;
   store_row(X, 0, r, x, y, z, p);
   if (m.kind == MRV_ROBOT_POINT) {
     const float zz = m.dof == 2 ? m.point_z : q[2];
@@ -677,9 +680,10 @@ __device__ __noinline__ void chain_row(const ModelDev &m, const float *q, float 
 #pragma unroll
   for (int k = 0; k < MRV_MAX_DOF; ++k) {
     if (k < m.dof) {
-      const float ca = m.dh[k][0], sa = m.dh[k][1], a = m.dh[k][2], d = m.dh[k][3], th0 = m.dh[k][4];
+      const float4 D = reinterpret_cast<const float4 *>(m.dh)[k];
+      const float ca = D.x, sa = D.y, a = D.z, d = D.w;
       float s, c;
-      joint_sincos(th0 + q[k], &s, &c);
+      joint_sincos(m.th0[k] + q[k], &s, &c);
       const float u = ca * y + sa * z;
       const float v = ca * z - sa * y;
       p = fmaf(a, x, fmaf(d, v, p));
@@ -691,9 +695,10 @@ __device__ __noinline__ void chain_row(const ModelDev &m, const float *q, float 
     }
   }
   // flange frame dof+1 = frame dof * F
-  const float *F = m.flange;
-  store_row(X, m.dof + 1, r, x * F[0] + y * F[4] + z * F[8], x * F[1] + y * F[5] + z * F[9],
-            x * F[2] + y * F[6] + z * F[10], p + x * F[3] + y * F[7] + z * F[11]);
+  const float4 *F = reinterpret_cast<const float4 *>(m.flange);
+  const float4 F0 = F[0], F1 = F[1], F2 = F[2];
+  store_row(X, m.dof + 1, r, x * F0.x + y * F1.x + z * F2.x, x * F0.y + y * F1.y + z * F2.y,
+            x * F0.z + y * F1.z + z * F2.z, p + x * F0.w + y * F1.w + z * F2.w);
 }
 
 // direct forms: |a - b|^2 < (ra + rb)^2, clearance |a - b| - ra - rb
@@ -2090,9 +2095,18 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
           if (T1 >= 0) {
             // one segment from time 0 to T1 (the same arithmetic as interp)
             const float f = t >= T1 ? 0.f : (float)t / (float)T1;
+            const float4 *A4 = reinterpret_cast<const float4 *>(S.ia[r]);
+            const float4 *G4 = reinterpret_cast<const float4 *>(S.ig[r]);
+            float av[MRV_MAX_DOF], gv[MRV_MAX_DOF];
+#pragma unroll
+            for (int h = 0; h < MRV_MAX_DOF / 4; ++h) {
+              const float4 a4 = A4[h], g4 = G4[h];
+              av[4 * h] = a4.x; av[4 * h + 1] = a4.y; av[4 * h + 2] = a4.z; av[4 * h + 3] = a4.w;
+              gv[4 * h] = g4.x; gv[4 * h + 1] = g4.y; gv[4 * h + 2] = g4.z; gv[4 * h + 3] = g4.w;
+            }
 #pragma unroll
             for (int j = 0; j < MRV_MAX_DOF; ++j)
-              if (j < rs.dof) q[j] = t >= T1 ? S.ig[r][j] : fmaf(S.ig[r][j] - S.ia[r][j], f, S.ia[r][j]);
+              if (j < rs.dof) q[j] = t >= T1 ? gv[j] : fmaf(gv[j] - av[j], f, av[j]);
           } else {
             int lo;
             interp_from(B, rs.w0, rs.w1, rs.dof, t, S.seg[r], q, &lo);
