@@ -121,6 +121,7 @@ struct alignas(16) ModelDev {
   float flange[12];              // flange transform, 3x4 row-major
   float dh[MRV_MAX_DOF][4];      // cos(alpha), sin(alpha), a, d
   float th0[MRV_MAX_DOF];        // theta_offset
+  float link_bs[kMaxLinks][4];   // frame-local bounding sphere (radius < 0: empty)
   int32_t kind, dof, n_spheres, n_self;
   int32_t live;
   float point_z;
@@ -135,7 +136,6 @@ struct alignas(16) ModelDev {
   int32_t n_rects;               // 0: use the sparse list
   int32_t n_links;               // frames 0..n_links-1 (DH: dof + 2, point: 2)
   int32_t link_start[kMaxLinks + 1];  // spheres (sorted by frame) of frame l
-  float link_bs[kMaxLinks][4];   // frame-local bounding sphere (radius < 0: empty)
   const int4 *self_groups;       // (frame u, frame v, first pair, count)
   const int4 *self_blocks;       // per group: first row sphere, first column
                                  // sphere, rows | columns << 16 (columns <= 32),
@@ -147,7 +147,8 @@ struct alignas(16) ModelDev {
   const int32_t *perm;           // sorted sphere index -> caller's index
 };
 static_assert(offsetof(ModelDev, base) % 16 == 0 && offsetof(ModelDev, flange) % 16 == 0 &&
-                  offsetof(ModelDev, dh) % 16 == 0 && sizeof(ModelDev) % 16 == 0,
+                  offsetof(ModelDev, dh) % 16 == 0 && offsetof(ModelDev, link_bs) % 16 == 0 &&
+                  sizeof(ModelDev) % 16 == 0,
               "FK rows of a model are read as float4");
 
 struct EnvDev {

@@ -648,6 +648,16 @@ __device__ __noinline__ void chain_frames(const ModelDev &m, const float *q, flo
 // columns of each row of the 3x4 transform but never its rows, so the rows
 // evolve independently through the base, the joints and the flange, and three
 // lanes can share a chain (the same arithmetic as chain_frames, row by row).
+// the point (x, y, z) of a link frame's coordinates in the frame of X (3x4
+// row-major, rows 16-byte aligned: three vector loads)
+__device__ __forceinline__ float3 frame_apply(const float *X, float x, float y, float z) {
+  const float4 *R = reinterpret_cast<const float4 *>(X);
+  const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+  return make_float3(fmaf(r0.x, x, fmaf(r0.y, y, fmaf(r0.z, z, r0.w))),
+                     fmaf(r1.x, x, fmaf(r1.y, y, fmaf(r1.z, z, r1.w))),
+                     fmaf(r2.x, x, fmaf(r2.y, y, fmaf(r2.z, z, r2.w))));
+}
+
 __device__ __forceinline__ void store_row(float *X, int link, int r, float x, float y, float z, float p) {
   *reinterpret_cast<float4 *>(X + link * 12 + 4 * r) = make_float4(x, y, z, p);
 }
@@ -1084,15 +1094,10 @@ __device__ void link_spheres(const TileCtx &C, WS &S, const float *xf, int jj, i
   for (int i = lane; i < nef; i += kWarp) {
     const int k = CK((int)S.ef[i], WS::kRobots * kMaxLinks, FRAME_SLOT, C.err);
     const int r = k / kMaxLinks, l = k - r * kMaxLinks;
-    const float *lb = S.rs[r].md->link_bs[l];
-    const float4 bs = make_float4(lb[0], lb[1], lb[2], lb[3]);
+    const float4 bs = reinterpret_cast<const float4 *>(S.rs[r].md->link_bs)[l];
     const float *X = xf + (CK(jj * n + r, WS::kChains, CHAIN, C.err) * kMaxLinks + l) * 12;
-    float4 o;
-    o.x = fmaf(X[0], bs.x, fmaf(X[1], bs.y, fmaf(X[2], bs.z, X[3]))) - S.ox;
-    o.y = fmaf(X[4], bs.x, fmaf(X[5], bs.y, fmaf(X[6], bs.z, X[7]))) - S.oy;
-    o.z = fmaf(X[8], bs.x, fmaf(X[9], bs.y, fmaf(X[10], bs.z, X[11]))) - S.oz;
-    o.w = bs.w;
-    S.BS[k] = o;
+    const float3 w = frame_apply(X, bs.x, bs.y, bs.z);
+    S.BS[k] = make_float4(w.x - S.ox, w.y - S.oy, w.z - S.oz, bs.w);
   }
 }
 
@@ -1309,14 +1314,13 @@ __device__ void place_needed(const TileCtx &C, WS &S, const float *xf, int jj, i
     // spheres are sorted by frame: walk from the first to the last frame to place
     const int s0 = S.rs[r].ls[__ffs(mr) - 1], s1 = S.rs[r].ls[32 - __clz(mr)];
     for (int kk = s0 + lane; kk < s1; kk += kWarp) {
+      // both loads issued together (the sphere is read even where its frame
+      // is not needed)
       const int l = CK(__ldg(&lnk[kk]), S.rs[r].n_links, LINK, C.err);
-      if (!((mr >> l) & 1u)) continue;
       const float4 sp = __ldg(&sph[kk]);
-      const float *X = Xr + l * 12;
-      const float wx = fmaf(X[0], sp.x, fmaf(X[1], sp.y, fmaf(X[2], sp.z, X[3])));
-      const float wy = fmaf(X[4], sp.x, fmaf(X[5], sp.y, fmaf(X[6], sp.z, X[7])));
-      const float wz = fmaf(X[8], sp.x, fmaf(X[9], sp.y, fmaf(X[10], sp.z, X[11])));
-      P[CK(a0 + kk, C.M, SPHERE, C.err)] = make_float4(wx - S.ox, wy - S.oy, wz - S.oz, sp.w);
+      if (!((mr >> l) & 1u)) continue;
+      const float3 w = frame_apply(Xr + l * 12, sp.x, sp.y, sp.z);
+      P[CK(a0 + kk, C.M, SPHERE, C.err)] = make_float4(w.x - S.ox, w.y - S.oy, w.z - S.oz, sp.w);
       acc.placed += 1;
     }
   }
@@ -2157,10 +2161,8 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
 #pragma unroll 4
         for (int kk = lane; kk < m; kk += kWarp) {
           const float4 s = __ldg(&sph[kk]);
-          const float *X = Xr + CK(__ldg(&lnk[kk]), S.rs[r].n_links, LINK, C.err) * 12;
-          const float wx = fmaf(X[0], s.x, fmaf(X[1], s.y, fmaf(X[2], s.z, X[3])));
-          const float wy = fmaf(X[4], s.x, fmaf(X[5], s.y, fmaf(X[6], s.z, X[7])));
-          const float wz = fmaf(X[8], s.x, fmaf(X[9], s.y, fmaf(X[10], s.z, X[11])));
+          const float3 w = frame_apply(Xr + CK(__ldg(&lnk[kk]), S.rs[r].n_links, LINK, C.err) * 12, s.x, s.y, s.z);
+          const float wx = w.x, wy = w.y, wz = w.z;
           const float px = wx - S.ox, py = wy - S.oy, pz = wz - S.oz;
           P[a0 + kk] = make_float4(px, py, pz, s.w);
           const float pp = fmaf(px, px, fmaf(py, py, pz * pz));
