@@ -234,6 +234,8 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
   B.n_envs = (int32_t)ctx->envs.size();
   B.clock_budget = ctx->clock_budget;
   B.classes = b->n_queries > 0 ? batch_classes(ctx, b) : 1;
+  B.full = (b->flags & MRV_NO_BROADPHASE) ? 1 : 0;   // and every run asking for minimum clearances
+  B.clr = 0;
   return B;
 }
 
@@ -274,13 +276,13 @@ cudaError_t Scratch::reset(cudaStream_t st) const {
   return e;
 }
 
-int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
+int grid_for(mrv_ctx *ctx, int warps, bool full, int blocks_per_sm, int cls) {
   // the occupancy of a kernel configuration does not change: queried once
-  int *slot = (warps >= 1 && warps <= 12 && cls >= 0 && cls < kNumClasses) ? &ctx->occ[clr ? 1 : 0][cls][warps]
+  int *slot = (warps >= 1 && warps <= 12 && cls >= 0 && cls < kNumClasses) ? &ctx->occ[full ? 1 : 0][cls][warps]
                                                                          : nullptr;
   int occ = slot ? *slot : 0;
   if (occ < 1) {
-    if (max_blocks_per_sm(warps, clr, cls, &occ) != cudaSuccess || occ < 1) {
+    if (max_blocks_per_sm(warps, full, cls, &occ) != cudaSuccess || occ < 1) {
       cudaGetLastError();
       occ = 1;
     } else if (slot) {
@@ -292,14 +294,15 @@ int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls) {
 }
 
 // Issues the launch sequence on the context's stream (capturable).
-int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, uint8_t *valid, float *minclr,
                 mrv_conflict *conf, bool timed) {
-  return enqueue_run_on(ctx, B, S, clr, valid, minclr, conf, ctx->stream, timed ? ctx->ev0 : nullptr,
+  return enqueue_run_on(ctx, B, S, valid, minclr, conf, ctx->stream, timed ? ctx->ev0 : nullptr,
                         timed ? ctx->ev1 : nullptr, &ctx->fork);
 }
 
-int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, uint8_t *valid, float *minclr,
                    mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, const Fork *fk) {
+  const bool full = B.full != 0;   // the persistent kernel's full instances
   cudaGetLastError();   // the launch checks below report this sequence's errors only
   cudaError_t e = S.reset(st);
   if (e != cudaSuccess) return cuda_fail(e, "scratch reset");
@@ -318,18 +321,18 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_
   const int more = B.classes & ~1;
   const bool side = more && fk && fk->aux;
   if (side && (e = cudaEventRecord(fk->fork, st)) != cudaSuccess) return cuda_fail(e, "fork event");
-  e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm, 0), warps, clr, 0, -1, st);
+  e = launch_main(B, grid_for(ctx, warps, full, ctx->tuning.blocks_per_sm, 0), warps, full, 0, -1, st);
   if (e != cudaSuccess) return cuda_fail(e, "main launch");
   if (more) {
     cudaStream_t ls = side ? fk->aux : st;
     if (side && (e = cudaStreamWaitEvent(ls, fk->fork, 0)) != cudaSuccess) return cuda_fail(e, "fork wait");
     if (B.classes & 2) {
-      e = launch_main(B, grid_for(ctx, warps, clr, ctx->tuning.blocks_per_sm, 1), warps, clr, 1, -1, ls);
+      e = launch_main(B, grid_for(ctx, warps, full, ctx->tuning.blocks_per_sm, 1), warps, full, 1, -1, ls);
       if (e != cudaSuccess) return cuda_fail(e, "team launch");
     }
     if (B.classes & 4) {
       const int lw = large_warps();
-      e = launch_main(B, grid_for(ctx, lw, clr, 0, 2), lw, clr, 2, -1, ls);
+      e = launch_main(B, grid_for(ctx, lw, full, 0, 2), lw, full, 2, -1, ls);
       if (e != cudaSuccess) return cuda_fail(e, "large-team launch");
     }
     if (side && ((e = cudaEventRecord(fk->join, ls)) != cudaSuccess || (e = cudaStreamWaitEvent(st, fk->join, 0)) != cudaSuccess))
@@ -436,12 +439,13 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
   const bool clr = minclr != nullptr;
   const bool per_query = b->flags & MRV_PER_QUERY_LAUNCH;
   BatchDev B = make_batchdev(ctx, b, S, forced_kind, per_query ? 1 : ctx->tuning.slices_per_item);
+  if (clr) B.clr = B.full = 1;
   uint8_t *v_dst = valid ? (dev ? valid : S.out_valid) : nullptr;
   float *m_dst = minclr ? (dev ? minclr : S.out_minclr) : nullptr;
   mrv_conflict *c_dst = conf ? (dev ? conf : S.out_conf) : nullptr;
   cudaStream_t st = ctx->stream;
   if (!per_query) {
-    if ((rc = enqueue_run(ctx, B, S, clr, v_dst, m_dst, c_dst, true))) return rc;
+    if ((rc = enqueue_run(ctx, B, S, v_dst, m_dst, c_dst, true))) return rc;
   } else {
     // baseline: one synchronous launch per query (grid = the query's chunks)
     cudaError_t e = S.reset(st);
@@ -456,7 +460,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
     for (int q = 0; q < b->n_queries; ++q) {
       if (hq[q].bits & 4u || hq[q].nchunks == 0) continue;
       const int cls = (int)((hq[q].bits >> 3) & 3u);
-      if ((e = launch_main(B, hq[q].nchunks, 1, clr, cls, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
+      if ((e = launch_main(B, hq[q].nchunks, 1, B.full != 0, cls, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "query synchronize");
     }
     cudaEventRecord(ctx->ev1, st);
@@ -998,9 +1002,9 @@ int mrv_graph_create(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_con
   BatchDev B = make_batchdev(c, b, g->scratch, -1, c->tuning.slices_per_item);
   // attributes are set outside the capture
   set_main_attrs(c->tuning.warps_per_block);
-  grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm, 0);
-  grid_for(c, c->tuning.warps_per_block, false, c->tuning.blocks_per_sm, 1);
-  grid_for(c, large_warps(), false, 0, 2);
+  grid_for(c, c->tuning.warps_per_block, B.full != 0, c->tuning.blocks_per_sm, 0);
+  grid_for(c, c->tuning.warps_per_block, B.full != 0, c->tuning.blocks_per_sm, 1);
+  grid_for(c, large_warps(), B.full != 0, 0, 2);
   cudaStream_t cap = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -1012,7 +1016,7 @@ int mrv_graph_create(mrv_ctx *c, const mrv_batch *b, uint8_t *valid_out, mrv_con
   c->stream = cap;
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    rc = enqueue_run(c, B, g->scratch, false, valid_out, nullptr, conflict_out, true);
+    rc = enqueue_run(c, B, g->scratch, valid_out, nullptr, conflict_out, true);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
     if (rc == MRV_OK && e2 == cudaSuccess) {

@@ -255,6 +255,9 @@ struct BatchDev {
   int32_t n_envs;
   long long clock_budget;            // persistent kernel: clock64 ticks (0 = none)
   int32_t classes;                   // host: bit c = the batch may hold class-c queries (launch its kernel)
+  int32_t full;                      // the run uses the full instances of the persistent kernel
+                                     // (minimum clearance, MRV_NO_BROADPHASE): dense path, flavor A
+  int32_t clr;                       // exhaustive MV reports each query's minimum clearance
   int32_t pad1;
 };
 

@@ -107,8 +107,8 @@ size_t main_smem_bytes(int warps, int cls);   // cls: work class (0 small team, 
 int large_warps();                             // warps per block of the large-team instance
 cudaError_t launch_prepare(const BatchDev &B, cudaStream_t st);
 cudaError_t set_main_attrs(int warps);
-cudaError_t max_blocks_per_sm(int warps, bool clr, int cls, int *out);
-cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int cls, int q_single, cudaStream_t st);
+cudaError_t max_blocks_per_sm(int warps, bool full, int cls, int *out);
+cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool full, int cls, int q_single, cudaStream_t st);
 cudaError_t launch_finish(const BatchDev &B, uint8_t *valid, float *minclr, mrv_conflict *conf, int *counts,
                           cudaStream_t st);
 cudaError_t launch_clearance(const BatchDev &B, int q, const int32_t *ts, int nt, int check_env, float *out,
@@ -132,7 +132,7 @@ struct mrv_ctx {
   long long clock_budget = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   mrv::Fork fork;               // second stream of the large-team instance
-  int occ[2][mrv::kNumClasses][13] = {};   // resident blocks per SM by [clearance][class][warps] (0: not queried yet)
+  int occ[2][mrv::kNumClasses][13] = {};   // resident blocks per SM by [full instance][class][warps] (0: not queried yet)
   void *h_pinned = nullptr;
   uint32_t *h_status = nullptr;
   unsigned long long *h_stats = nullptr;
@@ -153,13 +153,13 @@ struct mrv_graph {
 namespace mrv {
 int validate_batch(mrv_ctx *ctx, const mrv_batch *b);
 BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_kind, int slices_per_item);
-int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, uint8_t *valid, float *minclr,
                 mrv_conflict *conf, bool timed);
-int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, bool clr, uint8_t *valid, float *minclr,
+int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, uint8_t *valid, float *minclr,
                    mrv_conflict *conf, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, const Fork *fk);
 int stage_inputs(const mrv_batch *b, Scratch &S, cudaStream_t st);
 int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid, float *minclr, mrv_conflict *conf);
-int grid_for(mrv_ctx *ctx, int warps, bool clr, int blocks_per_sm, int cls);
+int grid_for(mrv_ctx *ctx, int warps, bool full, int blocks_per_sm, int cls);
 // maps a device error record (kErrWords words) to a status and message
 int check_device_err(const uint32_t *rec);
 // copies the error word, statistics and counts of the call just enqueued to

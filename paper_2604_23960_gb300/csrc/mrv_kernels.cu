@@ -118,6 +118,7 @@ struct TileCtx {
   int self_blk;              // every robot's self pairs come as blocks
   int pr0, pr1;              // robot-pair table entries checked in the current phase
   int fpt;                   // frame-pair table: 0 not used (too many pairs), 1 not built yet, 2 built
+  int clr;                   // minimum clearance wanted (full instance only)
   int nef, nef_env;          // frame slots holding spheres (ef): all robots', the obstacle-checked robots'
   int first_phase;           // the current phase is the first visit of its states
   long long rangetests;      // sphere tests per state of the entries pr0..pr1-1
@@ -396,7 +397,10 @@ __global__ void k_prep(BatchDev B) {
     Q.M = M;
     Q.env = env;
     Q.rho2 = rho2;
-    const bool flavor_a = all_point && M <= kFlavorAMaxSpheres;
+    // one lane per state (flavor A) only in the full instance: the default
+    // instance keeps just the broadphase path, whose code is then small
+    // enough for its warps to share the instruction cache
+    const bool flavor_a = B.full && all_point && M <= kFlavorAMaxSpheres;
     if (flavor_a) Q.bits |= 2u;
     Q.bits |= (uint32_t)work_class(n, M) << 3;
     const bool mv = !(Q.bits & 1u);
@@ -789,7 +793,7 @@ __device__ __forceinline__ int slice_valid(const TileCtx &C, int k) {
 // ---------------------------------------------------------------------------
 
 // MV -> 1 if a collision was found; FFC -> smallest key (t << kKeyShift | pair) or INT_MAX
-template <bool CLR, class WS>
+template <bool FULL, class WS>
 __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, float &minclr, bool do_env,
                        bool do_pairs) {
   const int t = slice_state(C, k, lane);
@@ -829,17 +833,17 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
       for (int a = 0; a < C.env_rows; ++a) {
         const float4 pa = PA[a * kWarp + lane];
         for (int o = 0; o < C.env_ns; ++o) {
-          if (CLR) minclr = fminf(minclr, sph_clr(pa, C.env_s[o]));
+          if (C.clr) minclr = fminf(minclr, sph_clr(pa, C.env_s[o]));
           else hit |= sph_hit(pa, C.env_s[o]);
         }
         for (int o = 0; o < C.env_nb; ++o) {
           const float d2 = box_d2(pa.x, pa.y, pa.z, C.box_lo[o], C.box_hi[o]);
-          if (CLR) minclr = fminf(minclr, sqrtf(d2) - pa.w);
+          if (C.clr) minclr = fminf(minclr, sqrtf(d2) - pa.w);
           else hit |= d2 < pa.w * pa.w;
         }
         for (int o = 0; o < C.env_nc; ++o) {
           const float d2 = cyl_d2(pa.x, pa.y, pa.z, __ldg(&C.cyl_a[o]), __ldg(&C.cyl_u[o]));
-          if (CLR) minclr = fminf(minclr, sqrtf(d2) - pa.w);
+          if (C.clr) minclr = fminf(minclr, sqrtf(d2) - pa.w);
           else hit |= d2 < pa.w * pa.w;
         }
       }
@@ -848,7 +852,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
           const uint32_t sp = S.rs[r].self[p];
           const float4 x = PA[CK(S.off[r] + (int)(sp & 0xffffu), C.M, FLAVOR_A, C.err) * kWarp + lane];
           const float4 y = PA[CK(S.off[r] + (int)(sp >> 16), C.M, FLAVOR_A, C.err) * kWarp + lane];
-          if (CLR) minclr = fminf(minclr, sph_clr(x, y));
+          if (C.clr) minclr = fminf(minclr, sph_clr(x, y));
           else hit |= sph_hit(x, y);
         }
     }
@@ -858,7 +862,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
           const float4 pa = PA[a * kWarp + lane];
           for (int bb = S.off[i + 1]; bb < C.M; ++bb) {
             const float4 pb = PA[bb * kWarp + lane];
-            if (CLR) minclr = fminf(minclr, sph_clr(pa, pb));
+            if (C.clr) minclr = fminf(minclr, sph_clr(pa, pb));
             else hit |= sph_hit(pa, pb);
           }
         }
@@ -870,7 +874,7 @@ __device__ int slice_a(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
       }
       if (do_pairs) C.tests += (unsigned long long)nvalid * (unsigned long long)C.pairtests;
     }
-    if (CLR) hit = minclr < 0.f;
+    if (C.clr) hit = minclr < 0.f;
     return __any_sync(0xffffffffu, hit) ? 1 : 0;
   }
   // FFC: first colliding pair of this lane's state, in (i, j) order
@@ -2072,7 +2076,7 @@ __device__ void clr_state(const TileCtx &C, const WS &S, const float4 *P, int la
     }
 }
 
-template <bool CLR, class WS>
+template <bool FULL, class WS>
 __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, float &minclr, bool do_env,
                        bool do_pairs) {
   const int n = C.n, M = C.M;
@@ -2125,9 +2129,10 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
     for (int j = j0; j < j0 + CS && j < nv; ++j) {
       const int t = slice_state(C, k, slot_j(C, j, nv));
       if (lane == 0 && C.first_phase) C.states += 1;   // two-phase orders: counted in the first phase
-      if (!CLR && C.broad) {
+      if (!FULL || (C.broad && !C.clr)) {
         // frame-level broadphase; spheres are placed only for the frames whose
-        // bounding spheres overlap something, then resolved exactly
+        // bounding spheres overlap something, then resolved exactly (the
+        // default instance has this path only)
         link_spheres(C, S, xf, j - j0, lane);
         __syncwarp();
         const unsigned res = broad_state(C, S, xf, j - j0, lane, need_env, do_pairs, acc);
@@ -2177,7 +2182,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
       const float eps = kEpsU * (c2 + C.rho2);
       if (!C.ffc) {
         bool hit = false;
-        if (CLR) {
+        if (C.clr) {
           clr_state(C, S, P, lane, do_env, do_pairs, minclr);
           hit = minclr < 0.f;
         } else if (need_env) {
@@ -2198,7 +2203,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
           C.ctests += (unsigned long long)C.cyltests;
         }
         if (do_pairs) {
-          if (!CLR) {
+          if (!C.clr) {
             if (C.pr0 == 0 && C.rangetests == C.pairtests) hit |= pairs_mv(P, K, S.off, n, M, lane, eps, C.pair_robots);
             else hit |= pairs_list_mv(P, K, S, C.pr0, C.pr1, lane, eps);
           }
@@ -2222,7 +2227,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
     }
     __syncwarp();
   }
-  if (!CLR && C.broad) flush_acc(C, acc, lane);
+  if (!FULL || (C.broad && !C.clr)) flush_acc(C, acc, lane);
   return found;
 }
 
@@ -2230,7 +2235,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
 // the persistent work-stealing kernel
 // ---------------------------------------------------------------------------
 
-template <bool CLR, class WS>
+template <bool FULL, class WS>
 __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   const QueryDev Q = B.q[q];
   if (!(B.flags & MRV_EXHAUSTIVE)) {
@@ -2253,6 +2258,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   C.broad = (B.flags & MRV_NO_BROADPHASE) ? 0 : 1;
   C.lin = (C.ffc || (B.flags & MRV_LINEAR)) ? 1 : 0;
   C.prio = (!C.ffc && (B.flags & MRV_PRIORITY)) ? 1 : 0;
+  C.clr = (FULL && B.clr && !C.ffc) ? 1 : 0;
   C.env_ns = 0; C.env_nb = 0; C.env_s = nullptr; C.env_k = nullptr; C.box_lo = nullptr; C.box_hi = nullptr;
   C.env = nullptr;
   C.env_nc = 0; C.cyl_a = nullptr; C.cyl_u = nullptr;
@@ -2388,8 +2394,8 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
                       : *(volatile int *)&B.q_best[q] < (min(slice_state(C, k, 0), C.T) << kKeyShift);
       if (__shfl_sync(0xffffffffu, stop, 0)) break;
     }
-    const int res = (Q.bits & 2u) ? slice_a<CLR>(B, C, S, k, lane, minclr, do_env, do_pairs)
-                                  : slice_b<CLR>(B, C, S, k, lane, minclr, do_env, do_pairs);
+    const int res = (FULL && (Q.bits & 2u)) ? slice_a<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs)
+                                            : slice_b<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs);
     if (!C.ffc) {
       if (res) {
         if (lane == 0) atomicExch(&B.q_hit[q], 1);
@@ -2401,7 +2407,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     }
     __syncwarp();
   }
-  if (CLR) {
+  if (FULL && C.clr) {
     for (int o = 16; o > 0; o >>= 1) minclr = fminf(minclr, __shfl_xor_sync(0xffffffffu, minclr, o));
     if (lane == 0) atomicMin((int *)&B.q_minclr[q], f2ord(minclr));
   }
@@ -2438,7 +2444,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
 // up to 12 warps per block; the register cap (168) lets 12 warps share an SM,
 // which is also what the shared memory of 3 blocks of 4 warps of the team
 // layout allows.  The instance of layout WS takes the work items of its class.
-template <bool CLR, class WS>
+template <bool FULL, class WS>
 __global__ void __launch_bounds__(WS::kMaxThreads, 1) k_main(BatchDev B, int q_single) {
   extern __shared__ float4 smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -2451,7 +2457,7 @@ __global__ void __launch_bounds__(WS::kMaxThreads, 1) k_main(BatchDev B, int q_s
     const QueryDev Q = B.q[q_single];
     if (Q.bits & 4u) return;
     for (int c = blockIdx.x * (blockDim.x >> 5) + warp; c < Q.nchunks; c += gridDim.x * (blockDim.x >> 5))
-      run_chunk<CLR>(B, S, q_single, c, lane);
+      run_chunk<FULL>(B, S, q_single, c, lane);
     return;
   }
   const int n_items = B.counters[kCtrItems(cls)];
@@ -2519,7 +2525,7 @@ __global__ void __launch_bounds__(WS::kMaxThreads, 1) k_main(BatchDev B, int q_s
       const int src = __ffs(live_mask) - 1;
       live_mask &= live_mask - 1;
       const int qq = __shfl_sync(0xffffffffu, q, src), ll = __shfl_sync(0xffffffffu, lvl, src);
-      run_chunk<CLR>(B, S, qq, ll, lane);
+      run_chunk<FULL>(B, S, qq, ll, lane);
       ++items;
     }
   }
@@ -2687,30 +2693,32 @@ cudaError_t set_main_attrs(int warps) {
 }
 
 template <class WS>
-static cudaError_t occupancy_of(int warps, bool clr, int *out) {
+static cudaError_t occupancy_of(int warps, bool full, int *out) {
   const size_t smem = main_smem_bytes(warps, WS::kClass);
-  return clr ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WS>, warps * 32, smem)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WS>, warps * 32, smem);
+  return full ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<true, WS>, warps * 32, smem)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_main<false, WS>, warps * 32, smem);
 }
 
-cudaError_t max_blocks_per_sm(int warps, bool clr, int cls, int *out) {
+cudaError_t max_blocks_per_sm(int warps, bool full, int cls, int *out) {
   set_main_attrs(warps);
-  if (cls == 2) return occupancy_of<WarpSmemLarge>(warps, clr, out);
-  if (cls == 1) return occupancy_of<WarpSmemTeam>(warps, clr, out);
-  return occupancy_of<WarpSmemSmall>(warps, clr, out);
+  if (cls == 2) return occupancy_of<WarpSmemLarge>(warps, full, out);
+  if (cls == 1) return occupancy_of<WarpSmemTeam>(warps, full, out);
+  return occupancy_of<WarpSmemSmall>(warps, full, out);
 }
 
+// full: the instance with every path (the runs that ask for minimum
+// clearances or name MRV_NO_BROADPHASE); otherwise the broadphase-only one
 template <class WS>
-static void launch_of(const BatchDev &B, int grid, int warps, bool clr, int q_single, cudaStream_t st) {
+static void launch_of(const BatchDev &B, int grid, int warps, bool full, int q_single, cudaStream_t st) {
   const size_t smem = main_smem_bytes(warps, WS::kClass);
-  if (clr) k_main<true, WS><<<grid, warps * 32, smem, st>>>(B, q_single);
+  if (full) k_main<true, WS><<<grid, warps * 32, smem, st>>>(B, q_single);
   else k_main<false, WS><<<grid, warps * 32, smem, st>>>(B, q_single);
 }
 
-cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool clr, int cls, int q_single, cudaStream_t st) {
-  if (cls == 2) launch_of<WarpSmemLarge>(B, grid, warps, clr, q_single, st);
-  else if (cls == 1) launch_of<WarpSmemTeam>(B, grid, warps, clr, q_single, st);
-  else launch_of<WarpSmemSmall>(B, grid, warps, clr, q_single, st);
+cudaError_t launch_main(const BatchDev &B, int grid, int warps, bool full, int cls, int q_single, cudaStream_t st) {
+  if (cls == 2) launch_of<WarpSmemLarge>(B, grid, warps, full, q_single, st);
+  else if (cls == 1) launch_of<WarpSmemTeam>(B, grid, warps, full, q_single, st);
+  else launch_of<WarpSmemSmall>(B, grid, warps, full, q_single, st);
   return cudaGetLastError();
 }
 

@@ -109,7 +109,7 @@ extern "C" int mv_validate_noalloc(mrv_ctx *ctx, const mrv_batch *b, uint8_t *va
   Scratch S;   // a view only: it owns nothing (base stays null)
   carve(base, b->n_queries, b->n_waypoints, &S);
   const BatchDev B = make_batchdev(ctx, b, S, MRV_KIND_MV, ctx->tuning.slices_per_item);
-  if ((rc = enqueue_run_on(ctx, B, S, false, valid_out, nullptr, nullptr, ctx->stream, ctx->ev0, ctx->ev1,
+  if ((rc = enqueue_run_on(ctx, B, S, valid_out, nullptr, nullptr, ctx->stream, ctx->ev0, ctx->ev1,
                            &ctx->fork)))
     return rc;
   // error word, statistics and counts come back through the context's pinned

@@ -198,7 +198,7 @@ void mrv_server::launch(Slot &s) {
   uint32_t *err_h = (uint32_t *)((char *)conf_h + sizeof(mrv_conflict) * (size_t)nq);
   if (!rc) {
     BatchDev B = make_batchdev(ctx, &b, s.scratch, -1, ctx->tuning.slices_per_item);
-    rc = enqueue_run_on(ctx, B, s.scratch, false, s.scratch.out_valid, nullptr, s.scratch.out_conf, s.stream, s.ev0,
+    rc = enqueue_run_on(ctx, B, s.scratch, s.scratch.out_valid, nullptr, s.scratch.out_conf, s.stream, s.ev0,
                         s.ev1, &s.fork);
   }
   if (!rc) {
