@@ -1509,6 +1509,8 @@ __device__ bool resolve_self_list(const TileCtx &C, WS &S, const float *xf, int 
   return hit;
 }
 
+__device__ EnvDev g_no_env;   // zero: no obstacles, an empty grid
+
 // One state of the broadphase path: MV -> 1 on a collision, FFC -> the
 // code of the first colliding robot pair (0: none).  MV checks the obstacles, then the self
 // pairs, then the other robots, with a warp vote after each (all three
@@ -1533,12 +1535,15 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
     const int env_ns = C.env_ns, env_nb = C.env_nb;
     const float4 *env_s = C.env_s, *box_lo = C.box_lo, *box_hi = C.box_hi;
     const float ox = S.ox, oy = S.oy, oz = S.oz;
-    const float gR = C.env ? C.env->g_R : -1.f;
-    if (gR >= 0.f) {
-      // lane per frame: the obstacles listed in the grid cell of its center
-      const EnvDev &E = *C.env;
-      const float glx = E.g_lo[0], gly = E.g_lo[1], glz = E.g_lo[2], gih = E.g_inv_h;
-      const int gdx = E.g_dims[0], gdy = E.g_dims[1], gdz = E.g_dims[2];
+    // lane per frame: the obstacles listed in the grid cell of its center;
+    // a frame larger than the grid's radius, or any frame when the
+    // environment has no grid, scans every obstacle
+    // (no environment: an empty one, whose frames find no grid cell)
+    const EnvDev *Ep = C.env ? C.env : &g_no_env;
+    const float gR = Ep->g_R;
+    const float glx = Ep->g_lo[0], gly = Ep->g_lo[1], glz = Ep->g_lo[2], gih = Ep->g_inv_h;
+    const int gdx = Ep->g_dims[0], gdy = Ep->g_dims[1], gdz = Ep->g_dims[2];
+    {
       for (int i = lane; i < nke; i += kWarp) {
         const int k = S.ef[i];
         const float4 bl = S.BS[k];
@@ -1549,9 +1554,9 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           const float fx = (bw.x - glx) * gih, fy = (bw.y - gly) * gih, fz = (bw.z - glz) * gih;
           if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)gdx && fy < (float)gdy && fz < (float)gdz) {
             const int c = CK(((int)fz * gdy + (int)fy) * gdx + (int)fx, gdx * gdy * gdz, GRID_CELL, C.err);
-            i0 = __ldg(&E.g_off[c]);
-            i1 = __ldg(&E.g_off[c + 1]);
-            const uint32_t cnt = __ldg(&E.g_cnt[c]);
+            i0 = __ldg(&Ep->g_off[c]);
+            i1 = __ldg(&Ep->g_off[c + 1]);
+            const uint32_t cnt = __ldg(&Ep->g_cnt[c]);
             is = i0 + (int)(cnt & 0xffffu);
             ib = is + (int)(cnt >> 16);
           }
@@ -1563,9 +1568,9 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           acc.tests += (uint32_t)(i1 - i0);
           acc.boxes += (uint32_t)(ib - is);
           acc.cyls += (uint32_t)(i1 - ib);
-          CK_RANGE(i0, i1, E.g_nitems, GRID_ITEM, C.err);
+          CK_RANGE(i0, i1, Ep->g_nitems, GRID_ITEM, C.err);
           for (int i = i0; i < is; ++i) {
-            const int e = CK((int)__ldg(&E.g_items[i]), env_ns, OBST_SPHERE, C.err);
+            const int e = CK((int)__ldg(&Ep->g_items[i]), env_ns, OBST_SPHERE, C.err);
             const float4 es = __ldg(&env_s[e]);
             if (sph_hit(bw, es)) {
               push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
@@ -1574,7 +1579,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
           const float rr = bw.w * bw.w;
           for (int i = is; i < ib; ++i) {
-            const int b = CK((int)__ldg(&E.g_items[i]), env_nb, OBST_BOX, C.err);
+            const int b = CK((int)__ldg(&Ep->g_items[i]), env_nb, OBST_BOX, C.err);
             const float4 lo = __ldg(&box_lo[b]);
             const float4 hi = __ldg(&box_hi[b]);
             if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
@@ -1583,7 +1588,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
             }
           }
           for (int i = ib; i < i1; ++i) {
-            const int y = CK((int)__ldg(&E.g_items[i]), C.env_nc, OBST_CYL, C.err);
+            const int y = CK((int)__ldg(&Ep->g_items[i]), C.env_nc, OBST_CYL, C.err);
             if (cyl_d2(bw.x, bw.y, bw.z, __ldg(&C.cyl_a[y]), __ldg(&C.cyl_u[y])) < rr) {
               push_obst(cl.yc, &cl.ny, &cl.overflow, k, y);
               nd = true;
@@ -1617,43 +1622,6 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         }
         if (nd) need_frame(cl, k);
       }
-    } else {
-      // no grid: frames x obstacles, lane = (frame group lane & 3, obstacle group lane >> 2)
-      const int fg = lane & 3, og = lane >> 2;
-      for (int i = fg; i < nke; i += 4) {
-        const int k = S.ef[i];
-        const float4 bl = S.BS[k];
-        const float4 bw = make_float4(bl.x + ox, bl.y + oy, bl.z + oz, bl.w);
-        bool nd = false;
-        for (int e = og; e < env_ns; e += 8) {
-          const float4 es = __ldg(&env_s[e]);
-          if (sph_hit(bw, es)) {
-            push_obst(cl.ec, &cl.ne, &cl.overflow, k, e);
-            nd = true;
-          }
-        }
-        const float rr = bw.w * bw.w;
-        for (int b = og; b < env_nb; b += 8) {
-          const float4 lo = __ldg(&box_lo[b]);
-          const float4 hi = __ldg(&box_hi[b]);
-          if (box_d2(bw.x, bw.y, bw.z, lo, hi) < rr) {
-            push_obst(cl.bc, &cl.nb, &cl.overflow, k, b);
-            nd = true;
-          }
-        }
-        for (int y = og; y < C.env_nc; y += 8)
-          if (cyl_d2(bw.x, bw.y, bw.z, __ldg(&C.cyl_a[y]), __ldg(&C.cyl_u[y])) < rr) {
-            push_obst(cl.yc, &cl.ny, &cl.overflow, k, y);
-            nd = true;
-          }
-        if (nd) need_frame(cl, k);
-      }
-      const uint32_t ns_l = (uint32_t)max(0, (env_ns - og + 7) >> 3), nb_l = (uint32_t)max(0, (env_nb - og + 7) >> 3);
-      const uint32_t nc_l = (uint32_t)max(0, (C.env_nc - og + 7) >> 3);
-      const int nf = max(0, (nke - fg + 3) >> 2);   // bounding spheres of this lane's frame group
-      acc.tests += (uint32_t)nf * (ns_l + nb_l + nc_l);
-      acc.boxes += (uint32_t)nf * nb_l;
-      acc.cyls += (uint32_t)nf * nc_l;
     }
     __syncwarp();
     if (cl.overflow) {   // too many candidates: resolve env and self in the lanes

@@ -441,3 +441,47 @@ def test_ffc_repeatable_under_concurrent_claims(ctx):
         v, c = (_np(x) for x in ctx.run(br, flags=fl))
         np.testing.assert_array_equal(v[kind == 0], v0[kind == 0])
         np.testing.assert_array_equal(c[kind == 1], c0[kind == 1])
+
+
+@pytest.mark.parametrize("gridless", [False, True])
+def test_obstacle_lists_without_a_grid_cell(gridless):
+    """Frames that no grid cell covers scan every obstacle of the
+    environment: frames larger than the grid's radius (the environment is
+    uploaded before the models, so its grid is built for 0.3 m frames and the
+    discs' frames are 0.45 and 0.6 m), and an environment with more obstacle
+    spheres than a grid indexes (70,000, most of them above the discs' plane:
+    no grid at all).  MV verdicts (a mix of valid and colliding motions) and
+    FFC conflicts equal the oracle's, with and without the frame broadphase."""
+    rng = np.random.default_rng(1400 + int(gridless))
+    env = W.world_boxes(7, n=8)
+    if gridless:
+        n = 70000   # above the 65,535 obstacles of one kind a grid indexes
+        z = np.where(np.arange(n) < 10, 0.0, rng.uniform(0.7, 3.0, n))
+        sph = np.column_stack([rng.uniform(0.0, 10.0, n), rng.uniform(0.0, 10.0, n), z,
+                               np.full(n, 0.03)]).astype(np.float32)
+        env = W.Env(sph, env.aabbs, name="many")
+    discs = [W.disc_robot(0.6), W.disc_robot(0.45)]
+    bb = W.BatchBuilder(2, False)
+    for _ in range(60):
+        robots = [int(rng.integers(0, 2)) for _ in range(int(rng.integers(1, 4)))]
+        paths = []
+        for _r in robots:
+            a = rng.uniform(0.5, 9.5, 2)
+            paths.append(np.array([a, np.clip(a + rng.uniform(-1.0, 1.0, 2), 0.5, 9.5)]))
+        bb.add(robots, paths, None, int(rng.integers(0, 2)), 0)
+    w = W.Workload("beyond_grid", discs, [env], bb.build(0.1), env=0, check_env=True)
+    c = mrv.Context(0)
+    try:
+        eid = c.upload_env(env)
+        rids = [c.upload_model(m) for m in discs]
+        ba = c.bind(w, rids, [eid])
+        o = O.Oracle(w)
+        v = c.mv_validate(ba)
+        PA.check_mv(o, v, check_env=True)
+        assert 0 < int(np.sum(v)) < len(v)
+        np.testing.assert_array_equal(c.mv_validate(ba, flags=mrv.MRV_NO_BROADPHASE), v)
+        f = c.ffc_find(ba)
+        PA.check_ffc(o, f)
+        np.testing.assert_array_equal(c.ffc_find(ba, flags=mrv.MRV_NO_BROADPHASE), f)
+    finally:
+        c.close()
