@@ -874,8 +874,10 @@ def run(args):
         "kernel_ms_mean": kms,
         # per graph step: k_prep, k_levels, k_scatter, the small-team k_main,
         # the team and large-team k_main instances (forked beside it; no work
-        # item on this batch), k_finish
-        "gpu_launches": 7 * args.steps,
+        # item on this batch), the full instance's pass over the queries
+        # handed over (queries_redone; usually none), k_finish
+        "gpu_launches": 8 * args.steps,
+        "queries_redone": st_step.get("queries_redone", 0),
         "clocks": clocks,
     }
     if strong is not None:

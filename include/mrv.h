@@ -298,6 +298,13 @@ typedef struct {
   uint64_t method_joints;         /* joints of the kinematic-chain robots     */
   uint64_t method_chains;         /* kinematic chains (one per robot, state)  */
   uint64_t method_spheres;        /* sphere placements                        */
+  /* Queries the default kernel instance handed to the full one: a state
+   * whose broadphase candidate lists overflowed, or self pairs of a model
+   * without row blocks.  The full instance reruns every work item of such a
+   * query; states_checked and the method_* counters count each state once,
+   * the executed-work counters (sphere_tests, fk_chains, spheres_placed, ...)
+   * both runs. */
+  uint64_t queries_redone;
 } mrv_stats;
 int mrv_get_stats(mrv_ctx *ctx, mrv_stats *out);
 

@@ -76,6 +76,9 @@ size_t Scratch::layout(int64_t nq, int64_t ns, int64_t nw, int64_t stride, char 
   set(&q_best, sizeof(int32_t) * nq);
   set(&q_minclr, sizeof(float) * nq);
   set(&sorted, sizeof(int32_t) * nq);
+  set(&redo_flag, sizeof(int32_t) * nq);
+  set(&redo, sizeof(int32_t) * nq);
+  set(&q_states, sizeof(int32_t) * nq);
   set(&hist, sizeof(int32_t) * kLevelBins);
   set(&level_start, sizeof(int32_t) * kLevelBins);
   set(&cursor, sizeof(int32_t) * 2 * kLevelBins);
@@ -222,6 +225,9 @@ BatchDev make_batchdev(mrv_ctx *ctx, const mrv_batch *b, Scratch &S, int forced_
   B.q_best = S.q_best;
   B.q_minclr = S.q_minclr;
   B.sorted = S.sorted;
+  B.redo_flag = S.redo_flag;
+  B.redo = S.redo;
+  B.q_states = S.q_states;
   B.hist = S.hist;
   B.level_start = S.level_start;
   B.cursor = S.cursor;
@@ -294,6 +300,13 @@ int grid_for(mrv_ctx *ctx, int warps, bool full, int blocks_per_sm, int cls) {
 }
 
 // Issues the launch sequence on the context's stream (capturable).
+// the full large-team instance over the queries the default instances
+// handed over (usually none: its warps find the list empty and return)
+cudaError_t launch_redo(mrv_ctx *ctx, const BatchDev &B, cudaStream_t st) {
+  const int lw = large_warps();
+  return launch_main(B, grid_for(ctx, lw, true, 1, 2), lw, true, 2, kRedoPass, st);
+}
+
 int enqueue_run(mrv_ctx *ctx, const BatchDev &B, Scratch &S, uint8_t *valid, float *minclr,
                 mrv_conflict *conf, bool timed) {
   return enqueue_run_on(ctx, B, S, valid, minclr, conf, ctx->stream, timed ? ctx->ev0 : nullptr,
@@ -338,6 +351,7 @@ int enqueue_run_on(mrv_ctx *ctx, const BatchDev &B, Scratch &S, uint8_t *valid, 
     if (side && ((e = cudaEventRecord(fk->join, ls)) != cudaSuccess || (e = cudaStreamWaitEvent(st, fk->join, 0)) != cudaSuccess))
       return cuda_fail(e, "join");
   }
+  if (!full && (e = launch_redo(ctx, B, st)) != cudaSuccess) return cuda_fail(e, "full-instance pass launch");
   if (ev1 && (e = cudaEventRecordWithFlags(ev1, st, rec_flags)) != cudaSuccess) return cuda_fail(e, "timing event");
   if ((e = launch_finish(B, valid, minclr, conf, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish launch");
   return MRV_OK;
@@ -409,6 +423,7 @@ int mrv_ctx::sync() {
   stats.method_joints = h_stats[12];
   stats.method_chains = h_stats[13];
   stats.method_spheres = h_stats[14];
+  stats.queries_redone = h_stats[15];
   stats.n_valid = h_counts[0];
   stats.n_conflicts = h_counts[1];
   float ms = 0.f;
@@ -463,6 +478,7 @@ int run_batch(mrv_ctx *ctx, const mrv_batch *b, int forced_kind, uint8_t *valid,
       if ((e = launch_main(B, hq[q].nchunks, 1, B.full != 0, cls, q, st)) != cudaSuccess) return cuda_fail(e, "query launch");
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "query synchronize");
     }
+    if (!B.full && (e = launch_redo(ctx, B, st)) != cudaSuccess) return cuda_fail(e, "full-instance pass launch");
     cudaEventRecord(ctx->ev1, st);
     if ((e = launch_finish(B, v_dst, m_dst, c_dst, S.counts, st)) != cudaSuccess) return cuda_fail(e, "finish");
   }

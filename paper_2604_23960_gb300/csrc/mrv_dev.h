@@ -39,8 +39,12 @@ constexpr int kSmallSpheres = 256;
 constexpr int kTeamSpheres = 512;
 constexpr int kNumClasses = 3;
 constexpr int kLevelBins = kNumClasses * (kMaxLevels + 1);
-// BatchDev::counters: [2] abort flag; per class c the claim counter, the
-// number of work items and the first sorted position of its queries
+// BatchDev::counters: [0] queries handed to the full instance (entries of
+// BatchDev::redo), [1] its claim counter, [2] abort flag; per class c the
+// claim counter, the number of work items and the first sorted position of
+// its queries
+constexpr int kCtrRedo = 0;
+constexpr int kCtrRedoClaim = 1;
 constexpr int kCtrAbort = 2;
 constexpr int kNumCounters = 16;
 MRV_HD constexpr int kCtrClaim(int c) { return 4 + 3 * c; }
@@ -51,7 +55,10 @@ static_assert(kCtrFirst(kNumClasses - 1) < kNumCounters, "counters fit");
 MRV_HD constexpr int work_class(int n, int M) {
   return (n > kTeamRobots || M > kTeamSpheres) ? 2 : (M > kSmallSpheres ? 1 : 0);
 }
-constexpr int kNumStats = 15;         // statistics counters of a call (see mrv_stats)
+constexpr int kNumStats = 16;         // statistics counters of a call (see mrv_stats)
+// k_main's q_single for the pass of the full large-team instance over the
+// queries the default instances handed over (BatchDev::redo)
+constexpr int kRedoPass = -2;
 
 // device error bits (BatchDev::err)
 enum : uint32_t {
@@ -234,6 +241,12 @@ struct BatchDev {
   int32_t *hist;                     // kLevelBins bins (class 0, 1, then 2)
   int32_t *level_start;              // kLevelBins
   int32_t *cursor;                   // 2 x kLevelBins: each bin's next FFC and next MV position
+  int32_t *redo_flag;                // n_queries: 1 once the query is listed in redo
+  int32_t *q_states;                 // n_queries: states the default instances counted
+  int32_t *redo;                     // n_queries: queries whose checks need a path the
+                                     // default instances do not have (candidate lists
+                                     // overflowing, self pairs without blocks), rerun
+                                     // whole by the full large-team instance
   int32_t *counters;                 // kNumCounters: the abort flag and per-class claim
                                      // counter, items and first sorted position (kCtr*)
   uint32_t *err;                     // kErrWords: error bits, check site, index, extent
@@ -247,7 +260,8 @@ struct BatchDev {
                                      // (robot-robot, obstacle spheres, self
                                      // pairs), [10] box tests, [11] cylinder
                                      // tests, [12] joints, [13] chains,
-                                     // [14] sphere placements
+                                     // [14] sphere placements, [15] queries
+                                     // rerun by the full instance
   // tables
   const ModelDev *models;
   int32_t n_models;

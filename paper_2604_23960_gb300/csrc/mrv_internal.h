@@ -26,6 +26,7 @@ struct Scratch {
   int32_t *q_hit = nullptr, *q_best = nullptr;
   float *q_minclr = nullptr;
   int32_t *sorted = nullptr, *hist = nullptr, *level_start = nullptr, *cursor = nullptr;
+  int32_t *redo_flag = nullptr, *redo = nullptr, *q_states = nullptr;
   int32_t *counters = nullptr;
   uint32_t *err = nullptr;
   unsigned long long *stats = nullptr;

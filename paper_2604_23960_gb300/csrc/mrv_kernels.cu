@@ -453,6 +453,8 @@ __global__ void k_prep(BatchDev B) {
   B.q[q] = Q;
   B.q_hit[q] = 0;
   B.q_best[q] = 0x7fffffff;
+  B.redo_flag[q] = 0;
+  B.q_states[q] = 0;
   B.q_minclr[q] = __int_as_float(f2ord(INFINITY));
   atomicAdd(&B.hist[CK((int)((Q.bits >> 3) & 3u) * (kMaxLevels + 1) + (Q.nchunks > kMaxLevels ? kMaxLevels : Q.nchunks),
                        kLevelBins, HIST, B.err)], 1);
@@ -1516,7 +1518,13 @@ __device__ EnvDev g_no_env;   // zero: no obstacles, an empty grid
 // pairs, then the other robots, with a warp vote after each (all three
 // belong to one state, so the verdict is the same in any order; the env and
 // self checks still come before the robot-robot ones, as in Alg. 1).
-template <class WS>
+// kRedoState: the state needs a path only the full instance has (a
+// candidate list overflowed, or self pairs without blocks); the default
+// instance then hands the whole query over (FULL = false only)
+constexpr unsigned kRedoState = 0xffffffffu;
+constexpr int kSliceRedo = -2;   // slice result: hand the query over
+
+template <bool FULL, class WS>
 __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int lane, bool need_env,
                                 bool do_pairs, BroadAcc &acc) {
   auto &cl = S.u.b.cl;
@@ -1624,7 +1632,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
       }
     }
     __syncwarp();
-    if (cl.overflow) {   // too many candidates: resolve env and self in the lanes
+    if (!FULL && cl.overflow) return kRedoState;
+    if (FULL && cl.overflow) {   // too many candidates: resolve env and self in the lanes
       need_all(cl, lane);
       place_needed(C, S, xf, jj, lane, acc);
       unsigned long long t = 0, bx = 0, cy = 0;
@@ -1718,7 +1727,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
         }
         __syncwarp();
-        if (cl.overflow) {
+        if (!FULL && (cl.overflow || (cl.ns && !C.self_blk))) return kRedoState;
+        if (FULL && cl.overflow) {
           need_all(cl, lane);
           place_needed(C, S, xf, jj, lane, acc);
           unsigned long long t = 0, bx = 0, cy = 0;
@@ -1775,7 +1785,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
           acc.tests += nt;
           __syncwarp();
-        } else if (cl.ns) {
+        } else if (FULL && cl.ns) {
           // self pairs from the pair list, one contiguous run per lane
           place_needed(C, S, xf, jj, lane, acc);
           const int ns = cl.ns;
@@ -1946,7 +1956,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   __syncwarp();
   unsigned pm = 0;
   const int np = cl.np;
-  if (cl.overflow) {
+  if (!FULL && cl.overflow) return kRedoState;
+  if (FULL && cl.overflow) {
     // every pair of the query's checked robots (a superset of the phase's
     // entries in the pairs-first order: an MV collision found there is one)
     need_all(cl, lane);
@@ -2103,8 +2114,12 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
         // default instance has this path only)
         link_spheres(C, S, xf, j - j0, lane);
         __syncwarp();
-        const unsigned res = broad_state(C, S, xf, j - j0, lane, need_env, do_pairs, acc);
+        const unsigned res = broad_state<FULL>(C, S, xf, j - j0, lane, need_env, do_pairs, acc);
         __syncwarp();
+        if (!FULL && res == kRedoState) {
+          flush_acc(C, acc, lane);
+          return kSliceRedo;
+        }
         if (res) {
           if (!C.ffc) {
             if (!C.exhaustive) {
@@ -2202,6 +2217,26 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
 // ---------------------------------------------------------------------------
 // the persistent work-stealing kernel
 // ---------------------------------------------------------------------------
+
+// s states of query q (s in two's complement: negative to take them back)
+// and the method's dense work of those states, added to the statistics:
+// every test and placement of the query's flavor, whatever the broadphase
+// skipped
+__device__ __forceinline__ void add_state_stats(const BatchDev &B, int q, unsigned long long s) {
+  const QueryDev *Qd = B.q + q;   // read here: not held in registers over the item
+  const unsigned long long bt = (unsigned long long)__ldg(&Qd->boxtests);
+  const unsigned long long ct = (unsigned long long)__ldg(&Qd->cyltests);
+  const int nch = __ldg(&Qd->nchain);
+  atomicAdd(&B.stats[9], s * (unsigned long long)(__ldg(&Qd->pairtests) + __ldg(&Qd->envtests)));
+  if (bt) atomicAdd(&B.stats[10], s * bt);
+  if (ct) atomicAdd(&B.stats[11], s * ct);
+  if (nch) {
+    atomicAdd(&B.stats[12], s * (unsigned long long)__ldg(&Qd->njoint));
+    atomicAdd(&B.stats[13], s * (unsigned long long)nch);
+  }
+  atomicAdd(&B.stats[14], s * (unsigned long long)__ldg(&Qd->M));
+  atomicAdd(&B.stats[0], s);
+}
 
 template <bool FULL, class WS>
 __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
@@ -2364,6 +2399,13 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     }
     const int res = (FULL && (Q.bits & 2u)) ? slice_a<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs)
                                             : slice_b<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs);
+    if (!FULL && res == kSliceRedo) {
+      // the query goes to the full instance's pass, listed once; that pass
+      // reruns every item of it (the checks of a state are idempotent)
+      if (lane == 0 && atomicExch(&B.redo_flag[q], 1) == 0)
+        B.redo[CK(atomicAdd(&B.counters[kCtrRedo], 1), B.n_queries, QUERY, B.err)] = q;
+      break;
+    }
     if (!C.ffc) {
       if (res) {
         if (lane == 0) atomicExch(&B.q_hit[q], 1);
@@ -2381,25 +2423,14 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   }
   __syncwarp();
   if (lane == 0) {
-    // the method's dense work of the states this item checked (each state
-    // counts once, in its first phase): every test and placement of the
-    // query's flavor, whatever the broadphase skipped
-    const unsigned long long s = C.states;
-    if (s) {
-      const QueryDev *Qd = B.q + q;   // read again here: not held in registers over the item
-      const unsigned long long bt = (unsigned long long)__ldg(&Qd->boxtests);
-      const unsigned long long ct = (unsigned long long)__ldg(&Qd->cyltests);
-      const int nch = __ldg(&Qd->nchain);
-      atomicAdd(&B.stats[9], s * (unsigned long long)(__ldg(&Qd->pairtests) + __ldg(&Qd->envtests)));
-      if (bt) atomicAdd(&B.stats[10], s * bt);
-      if (ct) atomicAdd(&B.stats[11], s * ct);
-      if (nch) {
-        atomicAdd(&B.stats[12], s * (unsigned long long)__ldg(&Qd->njoint));
-        atomicAdd(&B.stats[13], s * (unsigned long long)nch);
-      }
-      atomicAdd(&B.stats[14], s * (unsigned long long)__ldg(&Qd->M));
+    // the states this item checked (each state counts once, in its first
+    // phase) and the method's dense work of them; the default instances
+    // also keep each query's count, which the full instance's pass takes
+    // back before it reruns a query handed over
+    if (C.states) {
+      add_state_stats(B, q, C.states);
+      if (!FULL) atomicAdd(&B.q_states[q], (int)C.states);
     }
-    atomicAdd(&B.stats[0], C.states);
     atomicAdd(&B.stats[1], C.tests);
     atomicAdd(&B.stats[5], C.btests);
     atomicAdd(&B.stats[8], C.ctests);
@@ -2420,6 +2451,31 @@ __global__ void __launch_bounds__(WS::kMaxThreads, 1) k_main(BatchDev B, int q_s
   WS &S = *reinterpret_cast<WS *>(reinterpret_cast<char *>(smem_raw) + warp * warp_smem_bytes<WS>());
   constexpr int cls = WS::kClass;
   const long long t_start = clock64();
+  if (q_single == kRedoPass) {
+    // the full instance (large-team layout, which holds any query) reruns
+    // every item of the queries the default instances handed over, one
+    // query per warp at a time
+    if constexpr (FULL) {
+      const int n = *(volatile int *)&B.counters[kCtrRedo];
+      for (;;) {
+        int e = 0;
+        if (lane == 0) e = atomicAdd(&B.counters[kCtrRedoClaim], 1);
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if (e >= n) break;
+        const int q = CK(B.redo[CK(e, B.n_queries, QUERY, B.err)], B.n_queries, QUERY, B.err);
+        if (lane == 0) {
+          // the states the default instance counted for q are checked again here
+          const int sp = atomicExch(&B.q_states[q], 0);
+          if (sp) add_state_stats(B, q, (unsigned long long)(-(long long)sp));
+        }
+        __syncwarp();
+        const int nch = B.q[q].nchunks;
+        for (int c = 0; c < nch; ++c) run_chunk<FULL>(B, S, q, c, lane);
+        if (lane == 0) atomicAdd(&B.stats[15], 1ull);
+      }
+    }
+    return;
+  }
   if (q_single >= 0) {
     // one launch per query: warp w of block x takes items x*warps + w, ...
     const QueryDev Q = B.q[q_single];

@@ -25,12 +25,13 @@ namespace mrv {
 namespace {
 
 // per-call scratch: waypoint times, per-query records and verdict words,
-// the sorted query list, level tables, counters, error word and statistics
+// the sorted query list, the handed-over query list and its flags, level
+// tables, counters, error word and statistics
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 constexpr size_t kBytes =
     align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_WAYPOINTS) + align_up(sizeof(QueryDev) * MRV_NOALLOC_MAX_QUERIES) +
-    3 * align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) + align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) +
+    6 * align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) + align_up(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES) +
     2 * align_up(sizeof(int32_t) * kLevelBins) + align_up(sizeof(int32_t) * 2 * kLevelBins) + align_up(sizeof(int32_t) * kNumCounters) + align_up(sizeof(uint32_t) * kErrWords) +
     align_up(sizeof(unsigned long long) * kNumStats) + align_up(sizeof(int32_t) * 4);
 
@@ -64,6 +65,9 @@ void carve(void *base, int64_t nq, int64_t nw, Scratch *S) {
   S->q_best = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
   S->q_minclr = (float *)take(sizeof(float) * MRV_NOALLOC_MAX_QUERIES);
   S->sorted = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
+  S->redo_flag = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
+  S->redo = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
+  S->q_states = (int32_t *)take(sizeof(int32_t) * MRV_NOALLOC_MAX_QUERIES);
   S->hist = (int32_t *)take(sizeof(int32_t) * kLevelBins);
   S->level_start = (int32_t *)take(sizeof(int32_t) * kLevelBins);
   S->cursor = (int32_t *)take(sizeof(int32_t) * 2 * kLevelBins);

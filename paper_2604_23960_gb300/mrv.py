@@ -83,7 +83,7 @@ class Stats(C.Structure):
                 ("fk_chains", C.c_uint64), ("spheres_placed", C.c_uint64), ("cylinder_tests", C.c_uint64),
                 ("method_sphere_tests", C.c_uint64), ("method_box_tests", C.c_uint64),
                 ("method_cylinder_tests", C.c_uint64), ("method_joints", C.c_uint64),
-                ("method_chains", C.c_uint64), ("method_spheres", C.c_uint64)]
+                ("method_chains", C.c_uint64), ("method_spheres", C.c_uint64), ("queries_redone", C.c_uint64)]
 
 
 class Tuning(C.Structure):

@@ -485,3 +485,60 @@ def test_obstacle_lists_without_a_grid_cell(gridless):
         np.testing.assert_array_equal(c.ffc_find(ba, flags=mrv.MRV_NO_BROADPHASE), f)
     finally:
         c.close()
+
+
+def test_overflowing_candidate_lists_go_to_the_full_instance(ctx):
+    """States whose broadphase candidate lists overflow (more than 64
+    frame-obstacle or frame-frame candidates at one state) are handed from
+    the default kernel instance to the full one, which reruns every item of
+    the query with its in-lane fallbacks: a Panda-like arm inside a dense
+    cloud of obstacle spheres (MV), and eight arms on a 0.5 m circle, every
+    frame near its neighbours' (FFC and MV).  Results equal the oracle's and
+    the broadphase-free run's, and the statistics count the queries handed
+    over."""
+    fx = W.load_cage_fixtures()
+    rng = np.random.default_rng(1500)
+    arm = W.panda_like(W._pose(0.0, 0.0, 0.0), fx["self_pairs"])
+    n = 1500
+    cloud = np.column_stack([rng.uniform(-0.9, 0.9, n), rng.uniform(-0.9, 0.9, n), rng.uniform(0.0, 1.3, n),
+                             np.full(n, 0.02)]).astype(np.float32)
+    env = W.Env(cloud, np.zeros((0, 6), np.float32), name="cloud")
+    bb = W.BatchBuilder(7, False)
+    for _ in range(24):
+        bb.add([0], [rng.uniform(W.PANDA_LO, W.PANDA_HI, (2, 7))], None, 0, 0)
+    w = W.Workload("cloud", [arm], [env], bb.build(1.0 / 16), env=0, check_env=True)
+    ba = ctx.bind(w)
+    v = ctx.mv_validate(ba)
+    assert ctx.stats()["queries_redone"] > 0
+    PA.check_mv(O.Oracle(w), v, check_env=True)
+    np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_NO_BROADPHASE), v)
+    arms = [W.panda_like(W._pose(0.5 * np.cos(a), 0.5 * np.sin(a), 0.0, a + np.pi), fx["self_pairs"])
+            for a in np.linspace(0, 2 * np.pi, 8, endpoint=False)]
+    bb = W.BatchBuilder(7, True)
+    for _ in range(12):
+        paths = [rng.uniform(W.PANDA_LO, W.PANDA_HI, (3, 7)) for _ in arms]
+        bb.add(list(range(8)), paths, [rng.integers(10, 40, 2) for _ in arms], 1, -1)
+    w8 = W.Workload("eight_packed", arms, [], bb.build(), -1, True)
+    o8 = O.Oracle(w8)
+    b8 = ctx.bind(w8)
+    c = ctx.ffc_find(b8)
+    assert ctx.stats()["queries_redone"] > 0
+    PA.check_ffc(o8, c)
+    np.testing.assert_array_equal(ctx.ffc_find(b8, flags=mrv.MRV_NO_BROADPHASE), c)
+    v8 = ctx.mv_validate(b8, check_env=False)
+    PA.check_mv(o8, v8, check_env=False)
+    np.testing.assert_array_equal(ctx.mv_validate(b8, check_env=False, flags=mrv.MRV_NO_BROADPHASE), v8)
+    # a looser circle (1 m): conflicts at varied times, lists that may or
+    # may not overflow; the same results either way
+    rng = np.random.default_rng(1501)
+    arms = [W.panda_like(W._pose(np.cos(a), np.sin(a), 0.0, a + np.pi), fx["self_pairs"])
+            for a in np.linspace(0, 2 * np.pi, 8, endpoint=False)]
+    bb = W.BatchBuilder(7, True)
+    for _ in range(12):
+        paths = [rng.uniform(W.PANDA_LO, W.PANDA_HI, (3, 7)) for _ in arms]
+        bb.add(list(range(8)), paths, [rng.integers(10, 40, 2) for _ in arms], 1, -1)
+    w1 = W.Workload("eight_1m", arms, [], bb.build(), -1, True)
+    b1 = ctx.bind(w1)
+    c1 = ctx.ffc_find(b1)
+    PA.check_ffc(O.Oracle(w1), c1)
+    np.testing.assert_array_equal(ctx.ffc_find(b1, flags=mrv.MRV_NO_BROADPHASE), c1)
