@@ -181,18 +181,27 @@ static int batch_classes(const mrv_ctx *ctx, const mrv_batch *b) {
   int n_max = 0;
   for (int q = 0; q < b->n_queries; ++q) n_max = std::max(n_max, b->q_robot_off[q + 1] - b->q_robot_off[q]);
   int m_max = 0;
-  for (const auto &m : ctx->models) m_max = std::max(m_max, m.dev.n_spheres);
-  if (work_class(n_max, n_max * m_max) == 0) return 1;
+  bool points = false;   // one-lane-per-state queries (point robots only) take the team class
+  for (const auto &m : ctx->models) {
+    m_max = std::max(m_max, m.dev.n_spheres);
+    points |= m.dev.kind == MRV_ROBOT_POINT;
+  }
+  if (!points && work_class(n_max, n_max * m_max) == 0) return 1;
   const int n_models = (int)ctx->models.size();
   int mask = 0;
   for (int q = 0; q < b->n_queries; ++q) {
     int M = 0;
+    bool all_point = true;
     const int n = b->q_robot_off[q + 1] - b->q_robot_off[q];
     for (int s = b->q_robot_off[q]; s < b->q_robot_off[q + 1]; ++s) {
       const int id = b->slot_robot_id[s];
-      if (id >= 0 && id < n_models) M += ctx->models[id].dev.n_spheres;
+      if (id >= 0 && id < n_models) {
+        M += ctx->models[id].dev.n_spheres;
+        all_point &= ctx->models[id].dev.kind == MRV_ROBOT_POINT;
+      }
     }
-    mask |= 1 << work_class(n, M);
+    const int c = work_class(n, M);
+    mask |= 1 << ((all_point && M <= kFlavorAMaxSpheres && c == 0) ? 1 : c);
   }
   return mask | 1;
 }

@@ -51,6 +51,9 @@ MRV_HD constexpr int kCtrClaim(int c) { return 4 + 3 * c; }
 MRV_HD constexpr int kCtrItems(int c) { return 5 + 3 * c; }
 MRV_HD constexpr int kCtrFirst(int c) { return 6 + 3 * c; }
 static_assert(kCtrFirst(kNumClasses - 1) < kNumCounters, "counters fit");
+// queries of point robots only with at most this many spheres check one
+// state per lane (flavor A), in the team or large-team class
+constexpr int kFlavorAMaxSpheres = 16;
 // work class of a query with n robots and M spheres
 MRV_HD constexpr int work_class(int n, int M) {
   return (n > kTeamRobots || M > kTeamSpheres) ? 2 : (M > kSmallSpheres ? 1 : 0);

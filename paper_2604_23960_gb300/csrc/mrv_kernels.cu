@@ -89,7 +89,6 @@ __device__ __forceinline__ long long ck_idx(long long i, long long n, uint32_t s
 #define CK_RANGE(lo, hi, n, site, err) ((void)0)
 #endif
 
-constexpr int kFlavorAMaxSpheres = 16;
 constexpr int kSlotWords = 30;                   // words per RobotSlot in shared memory
 constexpr float kEpsU = 48.0f / 16777216.0f;     // 2 x 24 unit roundoffs
 
@@ -397,12 +396,13 @@ __global__ void k_prep(BatchDev B) {
     Q.M = M;
     Q.env = env;
     Q.rho2 = rho2;
-    // one lane per state (flavor A) only in the full instance: the default
-    // instance keeps just the broadphase path, whose code is then small
-    // enough for its warps to share the instruction cache
-    const bool flavor_a = B.full && all_point && M <= kFlavorAMaxSpheres;
+    // one lane per state (flavor A): never in the small-team default
+    // instance, which keeps just the broadphase path (its code then small
+    // enough for its warps to share the instruction cache); such queries
+    // take the team class (the large-team one beyond 8 robots)
+    const bool flavor_a = all_point && M <= kFlavorAMaxSpheres;
     if (flavor_a) Q.bits |= 2u;
-    Q.bits |= (uint32_t)work_class(n, M) << 3;
+    Q.bits |= (uint32_t)(flavor_a ? max(1, work_class(n, M)) : work_class(n, M)) << 3;
     const bool mv = !(Q.bits & 1u);
     const bool check_env = mv && (B.flags & MRV_CHECK_ENV);
     Q.ntiles = (int)((T + 1 + kWarp - 1) / kWarp);
@@ -1523,6 +1523,12 @@ __device__ EnvDev g_no_env;   // zero: no obstacles, an empty grid
 // instance then hands the whole query over (FULL = false only)
 constexpr unsigned kRedoState = 0xffffffffu;
 constexpr int kSliceRedo = -2;   // slice result: hand the query over
+// only the small-team default instance hands queries over (the one whose
+// code must stay small: it runs the bulk of mixed batches); the team and
+// large-team instances keep the in-lane fallbacks, since their 8- and
+// 16-arm queries overflow the lists often
+template <bool FULL, class WS>
+__host__ __device__ constexpr bool hands_over() { return !FULL && WS::kClass == 0; }
 
 template <bool FULL, class WS>
 __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int lane, bool need_env,
@@ -1632,8 +1638,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
       }
     }
     __syncwarp();
-    if (!FULL && cl.overflow) return kRedoState;
-    if (FULL && cl.overflow) {   // too many candidates: resolve env and self in the lanes
+    if (hands_over<FULL, WS>() && cl.overflow) return kRedoState;
+    if (!hands_over<FULL, WS>() && cl.overflow) {   // too many candidates: resolve env and self in the lanes
       need_all(cl, lane);
       place_needed(C, S, xf, jj, lane, acc);
       unsigned long long t = 0, bx = 0, cy = 0;
@@ -1727,8 +1733,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
         }
         __syncwarp();
-        if (!FULL && (cl.overflow || (cl.ns && !C.self_blk))) return kRedoState;
-        if (FULL && cl.overflow) {
+        if (hands_over<FULL, WS>() && (cl.overflow || (cl.ns && !C.self_blk))) return kRedoState;
+        if (!hands_over<FULL, WS>() && cl.overflow) {
           need_all(cl, lane);
           place_needed(C, S, xf, jj, lane, acc);
           unsigned long long t = 0, bx = 0, cy = 0;
@@ -1785,7 +1791,7 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
           }
           acc.tests += nt;
           __syncwarp();
-        } else if (FULL && cl.ns) {
+        } else if (!hands_over<FULL, WS>() && cl.ns) {
           // self pairs from the pair list, one contiguous run per lane
           place_needed(C, S, xf, jj, lane, acc);
           const int ns = cl.ns;
@@ -1956,8 +1962,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
   __syncwarp();
   unsigned pm = 0;
   const int np = cl.np;
-  if (!FULL && cl.overflow) return kRedoState;
-  if (FULL && cl.overflow) {
+  if (hands_over<FULL, WS>() && cl.overflow) return kRedoState;
+  if (!hands_over<FULL, WS>() && cl.overflow) {
     // every pair of the query's checked robots (a superset of the phase's
     // entries in the pairs-first order: an MV collision found there is one)
     need_all(cl, lane);
@@ -2116,7 +2122,7 @@ __device__ int slice_b(const BatchDev &B, TileCtx &C, WS &S, int k, int lane, fl
         __syncwarp();
         const unsigned res = broad_state<FULL>(C, S, xf, j - j0, lane, need_env, do_pairs, acc);
         __syncwarp();
-        if (!FULL && res == kRedoState) {
+        if (hands_over<FULL, WS>() && res == kRedoState) {
           flush_acc(C, acc, lane);
           return kSliceRedo;
         }
@@ -2397,9 +2403,9 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
                       : *(volatile int *)&B.q_best[q] < (min(slice_state(C, k, 0), C.T) << kKeyShift);
       if (__shfl_sync(0xffffffffu, stop, 0)) break;
     }
-    const int res = (FULL && (Q.bits & 2u)) ? slice_a<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs)
+    const int res = ((FULL || WS::kClass != 0) && (Q.bits & 2u)) ? slice_a<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs)
                                             : slice_b<FULL>(B, C, S, k, lane, minclr, do_env, do_pairs);
-    if (!FULL && res == kSliceRedo) {
+    if (hands_over<FULL, WS>() && res == kSliceRedo) {
       // the query goes to the full instance's pass, listed once; that pass
       // reruns every item of it (the checks of a state are idempotent)
       if (lane == 0 && atomicExch(&B.redo_flag[q], 1) == 0)
@@ -2429,7 +2435,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     // back before it reruns a query handed over
     if (C.states) {
       add_state_stats(B, q, C.states);
-      if (!FULL) atomicAdd(&B.q_states[q], (int)C.states);
+      if (hands_over<FULL, WS>()) atomicAdd(&B.q_states[q], (int)C.states);
     }
     atomicAdd(&B.stats[1], C.tests);
     atomicAdd(&B.stats[5], C.btests);
