@@ -492,10 +492,11 @@ def test_overflowing_candidate_lists_go_to_the_full_instance(ctx):
     frame-obstacle or frame-frame candidates at one state) are handed from
     the default kernel instance to the full one, which reruns every item of
     the query with its in-lane fallbacks: a Panda-like arm inside a dense
-    cloud of obstacle spheres (MV), and eight arms on a 0.5 m circle, every
-    frame near its neighbours' (FFC and MV).  Results equal the oracle's and
-    the broadphase-free run's, and the statistics count the queries handed
-    over."""
+    cloud of obstacle spheres (MV), and three arms on one base with five
+    discs around it (FFC and MV).  Results equal the oracle's and the
+    broadphase-free run's, and the statistics count the queries handed over.
+    Eight arms on a 1 m circle (the team class, which keeps the in-lane
+    fallbacks) give the oracle's conflicts too."""
     fx = W.load_cage_fixtures()
     rng = np.random.default_rng(1500)
     arm = W.panda_like(W._pose(0.0, 0.0, 0.0), fx["self_pairs"])
@@ -512,13 +513,16 @@ def test_overflowing_candidate_lists_go_to_the_full_instance(ctx):
     assert ctx.stats()["queries_redone"] > 0
     PA.check_mv(O.Oracle(w), v, check_env=True)
     np.testing.assert_array_equal(ctx.mv_validate(ba, flags=mrv.MRV_NO_BROADPHASE), v)
-    arms = [W.panda_like(W._pose(0.5 * np.cos(a), 0.5 * np.sin(a), 0.0, a + np.pi), fx["self_pairs"])
-            for a in np.linspace(0, 2 * np.pi, 8, endpoint=False)]
+    # three arms on one base and five discs around it (197 spheres: the
+    # small-team class): far more than 64 overlapping frame pairs per state
+    team = [W.panda_like(W._pose(0.0, 0.0, 0.0, yaw), fx["self_pairs"]) for yaw in (0.0, 2.1, 4.2)]
+    team += [W.disc_robot(0.3, z0=0.5, lo=(-0.2, -0.2), hi=(0.2, 0.2)) for _ in range(5)]
     bb = W.BatchBuilder(7, True)
     for _ in range(12):
-        paths = [rng.uniform(W.PANDA_LO, W.PANDA_HI, (3, 7)) for _ in arms]
-        bb.add(list(range(8)), paths, [rng.integers(10, 40, 2) for _ in arms], 1, -1)
-    w8 = W.Workload("eight_packed", arms, [], bb.build(), -1, True)
+        paths = [rng.uniform(W.PANDA_LO, W.PANDA_HI, (3, 7)) for _ in range(3)]
+        paths += [rng.uniform(-0.2, 0.2, (3, 2)) for _ in range(5)]
+        bb.add(list(range(8)), paths, [rng.integers(10, 40, 2) for _ in range(8)], 1, -1)
+    w8 = W.Workload("packed_team", team, [], bb.build(), -1, True)
     o8 = O.Oracle(w8)
     b8 = ctx.bind(w8)
     c = ctx.ffc_find(b8)
