@@ -232,7 +232,7 @@ int mrv_run(mrv_ctx *ctx, const mrv_batch *batch, uint8_t *valid_out, mrv_confli
  * cudaFree synchronizes the device) or an application whose device memory is
  * already fully budgeted by its own allocator.  It computes exactly what
  * mv_validate computes (early termination, MRV_CHECK_ENV honoured), but its
- * per-call scratch is one static device array of about 0.66 MB that every GPU
+ * per-call scratch is one static device array of about 0.84 MB that every GPU
  * loading the library holds until the process exits, so the call performs no
  * allocation.  The caller passes device pointers (MRV_PTRS_ON_DEVICE) for the
  * batch and valid_out; at most MRV_NOALLOC_MAX_QUERIES queries and
