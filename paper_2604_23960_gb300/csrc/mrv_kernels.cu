@@ -1951,6 +1951,8 @@ __device__ unsigned broad_state(TileCtx &C, WS &S, const float *xf, int jj, int 
         need_frame(cl, k2);
       }
     }
+  } else if (hands_over<FULL, WS>()) {
+    return kRedoState;   // more frame pairs than the table holds
   } else {
     const int ftot = S.rpf[C.pr1];
     int it = C.pr0;
@@ -2369,7 +2371,7 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
     S.rpf[CK(p, WS::kRobots * (WS::kRobots - 1) / 2 + 1, PAIRTAB, B.err)] = (int16_t)CK(f, 32768, PAIRTAB_PREFIX, B.err);
     S.fpf[p] = (int16_t)min(ff, 32767);
     // the table pays for its construction once an item spans 8 states or more
-    C.fpt = (WS::kFPCap > 0 && ff <= WS::kFPCap && Q.cte * Q.spt >= 8) ? 1 : 0;
+    C.fpt = (WS::kFPCap > 0 && ff <= WS::kFPCap && (WS::kClass == 0 || Q.cte * Q.spt >= 8)) ? 1 : 0;
   }
   __syncwarp();
   const int total = Q.nslices * Q.nphase;
