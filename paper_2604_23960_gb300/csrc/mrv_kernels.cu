@@ -2448,9 +2448,13 @@ __device__ void run_chunk(const BatchDev &B, WS &S, int q, int c, int lane) {
   __syncwarp();
 }
 
-// up to 12 warps per block; the register cap (168) lets 12 warps share an SM,
-// which is also what the shared memory of 3 blocks of 4 warps of the team
-// layout allows.  The instance of layout WS takes the work items of its class.
+// The persistent kernel.  Launch bounds: 512 threads per SM for the
+// small-team layout (at most 128 registers, 16 warps sharing an SM) and 384
+// for the others (168 registers; 12 warps of the team layout).  The instance
+// of layout WS takes the work items of its class; FULL selects the instance
+// with every path (see hands_over), and q_single one query per launch
+// (>= 0) or the full instance's pass over the handed-over queries
+// (kRedoPass).
 template <bool FULL, class WS>
 __global__ void __launch_bounds__(WS::kMaxThreads, 1) k_main(BatchDev B, int q_single) {
   extern __shared__ float4 smem_raw[];
